@@ -1,0 +1,135 @@
+"""Pins for the oracle's model quantities: eq. 26 scores, the collapsed cluster
+marginal, the CRP partition probability and the split / merge Hastings ratios."""
+
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy import stats
+from scipy.special import gammaln
+
+from oracle.model import (log_crp_partition, log_hastings_merge, log_hastings_split,
+                          log_marginal_cluster, multinomial_scores)
+
+
+def set_partitions(items):
+    """All set partitions of a list (restricted-growth enumeration)."""
+    if not items:
+        yield []
+        return
+    first, rest = items[0], items[1:]
+    for part in set_partitions(rest):
+        for i in range(len(part)):
+            yield part[:i] + [[first] + part[i]] + part[i + 1:]
+        yield [[first]] + part
+
+
+def test_scores_match_multinomial_pmf_differences():
+    """s_ik - s_ik' equals log pi_k - log pi_k' + logpmf(x|theta_k) - logpmf(x|theta_k')."""
+    rng = np.random.default_rng(0)
+    D, K = 6, 3
+    theta = rng.dirichlet(np.ones(D), size=K)
+    logpi = np.log(rng.dirichlet(np.ones(K)))
+    x = rng.integers(0, 5, size=(4, D))
+    s = multinomial_scores(sp.csr_matrix(x.astype(float)), logpi, np.log(theta))
+    for i in range(x.shape[0]):
+        lp = np.array([stats.multinomial.logpmf(x[i], x[i].sum(), theta[k]) for k in range(K)])
+        np.testing.assert_allclose(s[i] - s[i, 0], (logpi + lp) - (logpi[0] + lp[0]), atol=1e-10)
+
+
+def polya_urn_log_marginal(S, beta):
+    """Sequential Polya-urn product: draw the T counts one by one in gene order."""
+    D = len(S)
+    seen = [0] * D
+    total = 0.0
+    t = 0
+    for u in range(D):
+        for _ in range(int(S[u])):
+            total += math.log((beta + seen[u]) / (D * beta + t))
+            seen[u] += 1
+            t += 1
+    return total
+
+
+@pytest.mark.parametrize("beta", [0.05, 0.5, 1.0, 3.0])
+def test_cluster_marginal_equals_polya_urn(beta):
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        S = rng.integers(0, 12, size=7) * (rng.random(7) < 0.7)
+        assert abs(log_marginal_cluster(S, beta) - polya_urn_log_marginal(S, beta)) < 1e-10
+
+
+def test_cluster_marginal_matches_dirichlet_multinomial_pmf():
+    """scipy's Dirichlet-multinomial pmf = f(S) * multinomial coefficient."""
+    rng = np.random.default_rng(2)
+    beta = 0.3
+    S = rng.integers(0, 40, size=9)
+    T = S.sum()
+    coef = gammaln(T + 1) - gammaln(S + 1).sum()
+    ref = stats.dirichlet_multinomial.logpmf(S, np.full(9, beta), T) - coef
+    assert abs(log_marginal_cluster(S, beta) - ref) < 1e-9
+
+
+def test_cluster_marginal_two_genes_uniform_prior_is_beta_integral():
+    """D = 2, lambda = 1: f = S0! S1! / (T + 1)! exactly."""
+    for s0, s1 in [(0, 0), (3, 0), (2, 5), (17, 11)]:
+        exact = Fraction(math.factorial(s0) * math.factorial(s1), math.factorial(s0 + s1 + 1))
+        assert abs(log_marginal_cluster(np.array([s0, s1]), 1.0) - math.log(exact)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+@pytest.mark.parametrize("alpha", [0.3, 1.0, 2.5])
+def test_crp_partition_probabilities_sum_to_one(n, alpha):
+    total = sum(math.exp(log_crp_partition([len(b) for b in p], alpha))
+                for p in set_partitions(list(range(n))))
+    assert abs(total - 1.0) < 1e-12
+
+
+def crp_sequential(blocks, alpha):
+    """CRP seating probability of a labelled partition, customer by customer."""
+    owner = {}
+    for b, block in enumerate(blocks):
+        for i in block:
+            owner[i] = b
+    n = len(owner)
+    sizes = {}
+    p = 0.0
+    for i in range(n):
+        b = owner[i]
+        p += math.log((sizes[b] if b in sizes else alpha) / (alpha + i))
+        sizes[b] = sizes.get(b, 0) + 1
+    return p
+
+
+def test_split_and_merge_ratios_against_exact_integrals():
+    """Two genes, lambda = 1: posterior ratios from CRP seating and Beta integrals."""
+    x = np.array([[3, 0], [2, 1], [0, 4], [1, 3], [4, 1]])
+    A, B = [0, 1, 4], [2, 3]
+    alpha = 0.7
+
+    def log_joint(blocks):
+        lp = crp_sequential(blocks, alpha)
+        for blk in blocks:
+            s0, s1 = x[blk].sum(axis=0)
+            lp += math.log(Fraction(math.factorial(s0) * math.factorial(s1),
+                                    math.factorial(s0 + s1 + 1)))
+        return lp
+
+    ratio = log_joint([A, B]) - log_joint([A + B])
+    sum_logq = -1.25
+    got = log_hastings_split(len(A), len(B), x[A].sum(0), x[B].sum(0), alpha, 1.0, sum_logq)
+    assert abs(got - (ratio - sum_logq)) < 1e-10
+    got_m = log_hastings_merge(len(A), len(B), x[A].sum(0), x[B].sum(0), alpha, 1.0)
+    assert abs(got_m - (-ratio + (len(A) + len(B) - 2) * math.log(0.5))) < 1e-10
+
+
+def test_merge_is_reverse_of_split_without_q():
+    rng = np.random.default_rng(3)
+    Sa, Sb = rng.integers(0, 50, 20), rng.integers(0, 50, 20)
+    na, nb = 13, 8
+    s = log_hastings_split(na, nb, Sa, Sb, 1.3, 0.1, 0.0)
+    m = log_hastings_merge(na, nb, Sa, Sb, 1.3, 0.1)
+    assert abs(m + s - (na + nb - 2) * math.log(0.5)) < 1e-9

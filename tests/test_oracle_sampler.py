@@ -1,0 +1,232 @@
+"""Pins for the oracle sampler: the eq. 4 label draw, the eq. 8 sub-label draw,
+the bookkeeping invariants, and the chain's stationary law on tiny data."""
+
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.special import logsumexp
+
+from oracle import philox
+from oracle.model import log_crp_partition, log_marginal_cluster
+from oracle.sampler import Sampler, assign, csr_matrix, sufficient_stats
+
+from .test_oracle_model import set_partitions
+
+
+def replicated_rows(row, n):
+    row = np.asarray(row)
+    nz = np.nonzero(row)[0]
+    indptr = np.arange(n + 1) * nz.size
+    return indptr, np.tile(nz, n), np.tile(row[nz], n)
+
+
+def test_label_draw_is_categorical_softmax():
+    """Gumbel-max over s_ik + g_ik draws k with probability softmax(s_i)."""
+    rng = np.random.default_rng(4)
+    D, K, n = 5, 6, 30000
+    row = np.array([3, 0, 1, 4, 2])
+    logtheta = np.log(rng.dirichlet(np.ones(D), size=3 * K))
+    logpi = np.log(rng.dirichlet(np.ones(K + 1)))
+    X = csr_matrix(*replicated_rows(row, n), n, D)
+    nsub = np.full((K, 2), 10)
+    labels, _, _, scores = assign(X, logpi, logtheta, np.zeros(n, np.int64), np.zeros(n, np.int64),
+                                  nsub, 42, 0, 9)
+    p = np.exp(scores[0] - logsumexp(scores[0]))
+    counts = np.bincount(labels, minlength=K)
+    ok = p * n > 5
+    assert ok.sum() >= 2
+    obs = np.append(counts[ok], counts[~ok].sum())
+    exp = np.append(p[ok] * n, p[~ok].sum() * n)
+    if exp[-1] == 0:
+        obs, exp = obs[:-1], exp[:-1]
+    assert stats.chisquare(obs, exp).pvalue > 1e-4
+
+
+def test_sublabel_draw_follows_eq8_and_logq_is_its_log_probability():
+    rng = np.random.default_rng(5)
+    D, K, n = 4, 2, 40000
+    row = np.array([2, 1, 0, 3])
+    logtheta = np.log(rng.dirichlet(np.ones(D) * 2, size=3 * K))
+    logpi = np.log(np.array([0.5, 0.49, 0.01]))
+    X = csr_matrix(*replicated_rows(row, n), n, D)
+    nsub = np.array([[7, 3], [2, 9]])
+    labels_old = np.zeros(n, np.int64)
+    sub_old = (np.arange(n) % 2).astype(np.int64)
+    labels, sub, logq, _ = assign(X, logpi, logtheta, labels_old, sub_old, nsub, 42, 0, 2)
+    lik = np.array([[row @ logtheta[3 * k + 1], row @ logtheta[3 * k + 2]] for k in range(K)])
+    for k in range(K):
+        for so in (0, 1):
+            sel = (labels == k) & (sub_old == so)
+            if sel.sum() < 500:
+                continue
+            w = nsub[k].astype(float) - (np.array([0, 1]) == so) * (k == 0)
+            p1 = w[1] * math.exp(lik[k, 1]) / (w[0] * math.exp(lik[k, 0]) + w[1] * math.exp(lik[k, 1]))
+            m = sel.sum()
+            got = sub[sel].mean()
+            assert abs(got - p1) < 5 * math.sqrt(p1 * (1 - p1) / m) + 1e-9
+            expect_logq = np.where(sub[sel] == 1, math.log(p1), math.log(1 - p1))
+            np.testing.assert_allclose(logq[sel], expect_logq, atol=1e-9)
+
+
+def test_sweep_and_moves_keep_invariants(tiny_dataset):
+    ds = tiny_dataset
+    s = Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, seed=3)
+    colsum = np.bincount(ds.indices, weights=ds.data, minlength=ds.D)
+    for it in range(12):
+        s.sweep()
+        s.split_merge(0)
+        nsub, Ssub = s.stats()
+        assert s.labels.min() >= 0 and s.labels.max() < s.K
+        assert set(np.unique(s.sub)) <= {0, 1}
+        assert nsub.sum() == ds.N and np.all(nsub.sum(axis=1) > 0)
+        np.testing.assert_array_equal(Ssub.sum(axis=(0, 1)), colsum)
+        assert s.sumlogq.shape == (s.K,) and np.all(s.sumlogq <= 0)
+    assert s.t == 12 and s.m == 12
+
+
+def test_forced_split_and_merge_moves():
+    """Huge alpha accepts every split; tiny alpha accepts every identical-data merge."""
+    rng = np.random.default_rng(6)
+    n, D = 40, 3
+    x = rng.integers(0, 4, size=(n, D))
+    indptr = np.arange(n + 1) * D
+    s = Sampler(indptr, np.tile(np.arange(D), n), x.ravel(), n, D, alpha=1e300, beta=1.0, seed=1)
+    sub0 = s.sub.copy()
+    assert s.split_merge(1) == 1
+    assert s.K == 2
+    np.testing.assert_array_equal(s.labels, sub0)        # sub-cluster 1 became cluster 1
+    s.alpha = 1e-300
+    assert s.split_merge(2) == 1
+    assert s.K == 1 and np.all(s.labels == 0)
+    np.testing.assert_array_equal(s.sub, sub0)           # a -> sub 0, b -> sub 1
+
+
+def test_capacity_limit_counts_rejected_splits():
+    rng = np.random.default_rng(7)
+    n, D = 30, 2
+    x = rng.integers(0, 4, size=(n, D))
+    s = Sampler(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D,
+                alpha=1e300, beta=1.0, seed=1, kmax=1)
+    assert s.split_merge(1) == 0 and s.K == 1 and s.capacity_rejects == 1
+
+
+def exact_partition_posterior(x, alpha, beta):
+    n = x.shape[0]
+    parts = list(set_partitions(list(range(n))))
+    logp = np.array([log_crp_partition([len(b) for b in p], alpha)
+                     + sum(log_marginal_cluster(x[b].sum(axis=0), beta) for b in p) for p in parts])
+    return parts, np.exp(logp - logsumexp(logp))
+
+
+def canonical(labels):
+    seen, out = {}, []
+    for l in labels:
+        out.append(seen.setdefault(int(l), len(seen)))
+    return tuple(out)
+
+
+def partition_key(p, n):
+    lab = np.empty(n, dtype=int)
+    for b, blk in enumerate(p):
+        lab[blk] = b
+    return canonical(lab)
+
+
+TINY_X = np.array([[4, 0, 1], [3, 1, 0], [0, 3, 2], [1, 4, 1], [2, 2, 2]])
+
+
+def collapsed_gibbs_frequencies(x, alpha, beta, iters, seed):
+    """Neal (2000) Algorithm 3: textbook collapsed Gibbs; validates the enumerator."""
+    rng = np.random.default_rng(seed)
+    n = x.shape[0]
+    lab = np.zeros(n, dtype=int)
+    counts = {}
+    for _ in range(iters):
+        for i in range(n):
+            lab[i] = -1
+            blocks = sorted(set(lab[lab >= 0]))
+            lp = []
+            for b in blocks:
+                S = x[lab == b].sum(axis=0)
+                lp.append(math.log((lab == b).sum())
+                          + log_marginal_cluster(S + x[i], beta) - log_marginal_cluster(S, beta))
+            lp.append(math.log(alpha) + log_marginal_cluster(x[i], beta)
+                      - log_marginal_cluster(np.zeros_like(x[i]), beta))
+            lp = np.array(lp)
+            c = rng.choice(len(lp), p=np.exp(lp - logsumexp(lp)))
+            lab[i] = blocks[c] if c < len(blocks) else (max(blocks) + 1 if blocks else 0)
+        key = canonical(lab)
+        counts[key] = counts.get(key, 0) + 1
+    return counts
+
+
+def total_variation(counts, parts, post, n):
+    tot = sum(counts.values())
+    emp = np.array([counts.get(partition_key(p, n), 0) / tot for p in parts])
+    return 0.5 * np.abs(emp - post).sum()
+
+
+def test_enumerated_posterior_matches_collapsed_gibbs():
+    parts, post = exact_partition_posterior(TINY_X, 1.0, 0.5)
+    counts = collapsed_gibbs_frequencies(TINY_X, 1.0, 0.5, 6000, seed=0)
+    assert total_variation(counts, parts, post, TINY_X.shape[0]) < 0.04
+
+
+def k_restricted_posterior(x, K, alpha, beta):
+    parts, post = exact_partition_posterior(x, alpha, beta)
+    keep = np.array([len(p) == K for p in parts])
+    parts = [p for p, k in zip(parts, keep) if k]
+    post = post[keep] / post[keep].sum()
+    return parts, post
+
+
+def test_sweep_is_exact_gibbs_for_fixed_K_posterior():
+    """With K held fixed, the eq. 4 sweep (pi | c, theta | c, then all c_i | pi, theta
+    in parallel) is a Gibbs sampler for p(c | x, K non-empty clusters).  Label draws
+    that empty a cluster are redrawn with fresh counters (rejection sampling of the
+    restricted conditional), so the chain's partition frequencies must match the
+    enumerated posterior over partitions into exactly K blocks."""
+    from oracle.sampler import draw_pi, draw_theta
+    x = TINY_X
+    n, D = x.shape
+    K, alpha, beta = 2, 1.0, 0.5
+    X = csr_matrix(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D)
+    parts, post = k_restricted_posterior(x, K, alpha, beta)
+    labels = np.array([0, 0, 1, 1, 1])
+    sub = np.zeros(n, dtype=np.int64)
+    counts, s, iters = {}, 0, 5000
+    for t in range(iters):
+        nsub, Ssub = sufficient_stats(X, labels, sub, K)
+        logpi = draw_pi(nsub.sum(axis=1), alpha, 0, 0, t)
+        logtheta = draw_theta(Ssub, beta, 0, 0, t)
+        while True:                      # redraw c only, pi and theta held fixed
+            new, _, _, _ = assign(X, logpi, logtheta, labels, sub, nsub, 0, 0, s)
+            s += 1
+            if np.bincount(new, minlength=K).min() > 0:
+                break
+        labels = new
+        key = canonical(labels)
+        counts[key] = counts.get(key, 0) + 1
+    # 5000 correlated steps leave TV ~0.02 of sampling noise; redrawing pi and theta
+    # together with rejected labels (a biased restricted conditional) gives ~0.1.
+    assert total_variation(counts, parts, post, n) < 0.05
+
+
+@pytest.mark.xfail(strict=True, reason=(
+    "finding: the paper's chain (parallel restricted Gibbs that may empty clusters, "
+    "plus separate split-only and merge-only MH chains) is not invariant for the "
+    "DPMM posterior on 5-cell data; it over-weights coarse partitions"))
+def test_full_chain_matches_exact_partition_posterior():
+    x = TINY_X
+    n, D = x.shape
+    parts, post = exact_partition_posterior(x, 1.0, 0.5)
+    s = Sampler(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D, 1.0, 0.5, seed=11)
+    counts = {}
+    for _ in range(3000):
+        s.sweep()
+        s.split_merge(0)
+        key = canonical(s.labels)
+        counts[key] = counts.get(key, 0) + 1
+    assert total_variation(counts, parts, post, n) < 0.05
