@@ -1,0 +1,412 @@
+"""Throughput of the Para-DPMM sampler on one GB300 (or N GPUs, independent chains).
+
+One step = one Gibbs sweep (pi, theta, theta-bar draws; labels and sub-labels;
+statistics; empty-cluster removal) + one coin-selected split/merge move, all
+in libdpmm.so's kernels, replayed from the step's CUDA graph.  The metric is
+Gibbs sweeps per second on the 68,000-cell x 1,000-gene workload (synthetic
+Dirichlet-multinomial data of PBMC 68K's size).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own chain
+(chain_id = rank) on the same data: no data-path collective, weak scaling.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gibbs sweeps/sec at 68k cells x 1k genes; BF16 form vs plain FP32, ARI-matched"
+UNIT = "sweeps/s"
+L2_FLUSH_BYTES = 256 << 20
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+KERNELS_PER_STEP = 14     # 8 sweep kernels + 6 move kernels (see csrc/sweep.cu, moves.cu)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--engine", default="csr_fp32", choices=["csr_fp32", "auto"])
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from paper_1812_10048_gb300 import synth
+    t0 = time.time()
+    ds = synth.pbmc68k()
+    return ds, time.time() - t0
+
+
+def workload_config(ds):
+    return {
+        "workload": "pbmc68k-synthetic: 68,000 cells x 1,000 genes CSR int32, 10 Zipf(1.2) "
+                    "clusters, Dir(0.05) profiles, LogNormal(log 1000, 0.6) library sizes",
+        "N": ds.N, "D": ds.D, "nnz": ds.nnz, "density": round(ds.density, 4),
+        "alpha": 1.0, "beta": 0.1, "kmax": 256,
+        "step": "1 sweep + 1 coin-selected split/merge move (CUDA graph replay)",
+        "l2": "flushed between timed steps (256 MB write); workload ~40 MB fits in L2",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "power_w_max": float(max(power)) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def assign_algorithmic_bytes(ds, K, packed=True):
+    """Bytes the label/sub-label kernel must move once per sweep.
+
+    CSR read (indptr + 4-byte packed entries, or 8-byte int32 pairs), the cell
+    state read and written (4 + 4 bytes), the cluster and sub-cluster log theta
+    tables (3 K D floats) and log pi (K + 1 floats)."""
+    per_nnz = 4 if packed else 8
+    return (4 * (ds.N + 1) + per_nnz * ds.nnz + 8 * ds.N + 4 * 3 * K * ds.D + 4 * (K + 1))
+
+
+def step_algorithmic_bytes(ds, K):
+    """Whole step: the assign bytes, the statistics pass (CSR + state reads) and
+    the parameter draws (statistics in, tables out)."""
+    stats = 4 * (ds.N + 1) + 4 * ds.nnz + 4 * ds.N + 4 * 2 * K * ds.D
+    draws = 4 * 2 * K * ds.D + 4 * 3 * K * ds.D
+    return assign_algorithmic_bytes(ds, K) + stats + draws
+
+
+def traffic_for(kernel, workload_name):
+    try:
+        with open(TRAFFIC_PATH) as f:
+            rec = json.load(f)[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1812_10048_gb300", "csrc", rec.get("source", "sweep.cu"))
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if sha != rec.get("source_sha256") or rec.get("workload") != workload_name:
+        return None
+    return rec.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_steps_per_sec(ds, state, seconds, cells=None):
+    """Time oracle steps (sweep + split/merge) from the given state.
+
+    With ``cells`` the oracle runs on the first ``cells`` rows only and the
+    rate is scaled by cells / N to a full-workload equivalent."""
+    from oracle.sampler import Sampler as OracleSampler
+    labels, sub, K, t, m, sumlogq = state
+    n = ds.N if cells is None else int(cells)
+    indptr = ds.indptr[:n + 1]
+    o = OracleSampler(indptr, ds.indices[:indptr[-1]], ds.data[:indptr[-1]], n, ds.D, 1.0, 0.1,
+                      seed=42)
+    lab = labels[:n]
+    present = np.unique(lab)
+    remap = np.full(K, -1)
+    remap[present] = np.arange(present.size)
+    o.set_state(remap[lab], sub[:n], present.size, t, m, np.asarray(sumlogq)[present])
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.sweep()
+        o.split_merge(0)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 1000:
+            break
+    return steps / el * (n / ds.N), steps, el, n
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    from paper_1812_10048_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+        _build.build()
+    import paper_1812_10048_gb300 as P
+
+    ds, gen_s = workload()
+    engine = P.ENGINE_CSR_FP32 if args.engine == "csr_fp32" else P.ENGINE_AUTO
+    s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                  chain_id=rank, engine=engine)
+    stream = torch.cuda.ExternalStream(s.stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up (also captures the step graph, with per-phase timing events)
+    P.dpmm_profile(s.ctx, True)
+    s.step(args.warmup)
+    s.sync()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phases = np.zeros((args.steps, 5), dtype=np.float64)
+    Ks = np.zeros(args.steps, dtype=np.int64)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            starts[i].record(stream)
+        s.step(1)
+        ends[i].record(stream)
+        phases[i] = P.dpmm_phase_times(s.ctx, 5)   # events of this step (synchronises)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    labels, K_final = s.labels()
+    state = s.get_state()
+    _, _, sumlogq = s.stats()
+
+    result = {"rank": rank, "total_ms": total_ms, "step_ms": step_ms, "phases": phases,
+              "K_final": K_final, "wall_s": wall, "clocks": clk, "labels": labels,
+              "state": (state[0], state[1], state[2], state[3], state[4], sumlogq), "ds": ds,
+              "gen_s": gen_s}
+
+    # end to end through the public API with host buffers
+    if rank == 0:
+        pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+               for a in (ds.indptr, ds.indices, ds.data)]
+        lab_out = torch.empty(ds.N, dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = P.Sampler(pin[0], pin[1], pin[2], ds.N, ds.D, 1.0, 0.1, kmax=256, seed=43,
+                       engine=engine)
+        s2.step(args.e2e_steps)
+        lab, K2 = P.dpmm_labels(s2.ctx, ds.N)
+        e2e_s = time.perf_counter() - t0
+        s2.close()
+        result["e2e"] = {
+            "value": args.e2e_steps / e2e_s, "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(a.numel() * 4 for a in pin) / args.e2e_steps),
+            "d2h_bytes_per_step": int(4 * ds.N / args.e2e_steps),
+            "steps": args.e2e_steps, "seconds": e2e_s,
+            "what": "dpmm_init from pinned host CSR + steps + dpmm_labels to host, wall clock",
+        }
+    s.close()
+    return result
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    r = run_ours(args, rank, world, local)
+    if rank != 0:
+        return 0
+    ds = r["ds"]
+    K = int(r["K_final"])
+    steps = args.steps
+    ms_per_step = r["total_ms"] / steps
+    value = world * steps / (r["total_ms"] / 1e3)
+    peak, peak_kind = hbm_peak()
+    assign_ms = float(np.mean(r["phases"][:, 1]))
+    a_bytes = assign_algorithmic_bytes(ds, K)
+    achieved = a_bytes / (assign_ms * 1e-3) / 1e9
+    step_bytes = step_algorithmic_bytes(ds, K)
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(ds),
+        "roofline": {
+            "kernel": "k_assign (contraction + Gumbel-max labels + eq. 8 sub-labels)",
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+            "traffic": traffic_for("k_assign", "pbmc68k"),
+            "algorithmic_bytes_per_launch": int(a_bytes), "avg_launch_ms": round(assign_ms, 5),
+            "K": K,
+        },
+        "step_roofline": {
+            "achieved": round(step_bytes / (ms_per_step * 1e-3) / 1e9, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
+            "algorithmic_bytes_per_step": int(step_bytes),
+        },
+        "phase_ms": {n: round(float(np.mean(r["phases"][:, i])), 5) for i, n in
+                     enumerate(["draw", "assign", "stats", "compact", "moves"])},
+        "e2e": r.get("e2e"),
+        "gpu_launches": KERNELS_PER_STEP * steps,
+        "clocks": r["clocks"],
+        "wall_s_timed_loop": round(r["wall_s"], 3),
+    }
+    try:
+        from oracle.ari import adjusted_rand_index
+        line["ari_vs_truth"] = round(adjusted_rand_index(r["labels"], ds.labels), 4)
+    except Exception as e:  # noqa: BLE001
+        line["ari_vs_truth"] = f"unavailable: {e}"
+    if not args.no_cpu_baseline and world == 1:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        rate, n_steps, el, cells = oracle_steps_per_sec(ds, r["state"], args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_steps} oracle steps (sweep + split/merge, FP64 numpy/scipy) on the "
+                      f"full {cells}-cell workload from the GPU chain's state, {el:.1f} s",
+        }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle timed on the host cores (reference arm)."""
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    ds, _ = workload()
+    from oracle.sampler import Sampler as OracleSampler
+    # state: a short oracle chain on the full data gives a realistic K
+    budget_s = 150.0
+    per_step = budget_s / max(1, args.steps + args.warmup)
+    # oracle cost is ~linear in the number of cells; size the sample to the budget
+    probe = OracleSampler(ds.indptr[:2001], ds.indices[:ds.indptr[2000]], ds.data[:ds.indptr[2000]],
+                          2000, ds.D, 1.0, 0.1, seed=42)
+    for _ in range(5):
+        probe.sweep()
+        probe.split_merge(0)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        probe.sweep()
+        probe.split_merge(0)
+    per_cell = (time.perf_counter() - t0) / 3 / 2000
+    cells = int(min(ds.N, max(200, per_step / per_cell)))
+    o = OracleSampler(ds.indptr[:cells + 1], ds.indices[:ds.indptr[cells]],
+                      ds.data[:ds.indptr[cells]], cells, ds.D, 1.0, 0.1, seed=42)
+    for _ in range(args.warmup):
+        o.sweep()
+        o.split_merge(0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.sweep()
+        o.split_merge(0)
+    el = time.perf_counter() - t0
+    value = args.steps / el * (cells / ds.N)
+    line = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / value, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(ds), "impl": "reference",
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step on the first {cells} of {ds.N} cells, rate scaled "
+                                   f"by {cells}/{ds.N}"},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

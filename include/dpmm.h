@@ -1,0 +1,239 @@
+/*
+ * dpmm.h -- C ABI of the GB300 Para-DPMM sampler (Duan, Pinto & Xie,
+ * "Parallel Clustering of Single Cell Transcriptomic Data with Split-Merge
+ * Sampling on Dirichlet Process Mixtures", arXiv 1812.10048).
+ *
+ * One context holds one chain of the sampler for one cells x genes UMI count
+ * matrix on one GPU.  All device memory is owned by the library.  Calls that
+ * launch work are asynchronous on the context's stream unless stated; calls
+ * that return data to the host synchronise that stream.
+ *
+ * Pointers: every array argument may be a host pointer (pageable or pinned)
+ * or a device pointer of the current device; the library copies with
+ * cudaMemcpyDefault and keeps no reference to caller memory after the call
+ * returns (and, for device pointers, after the stream work it enqueued).
+ *
+ * Errors: every int-returning call returns DPMM_OK (0) or a negative code;
+ * dpmm_last_error() then gives a thread-local message.  No C++ exception
+ * crosses this boundary.  After DPMM_ECUDA the context should be freed.
+ *
+ * Notation follows the paper: x_i^u is the count of gene u in cell i, V (here
+ * D) genes, N cells, K clusters, DP concentration alpha, symmetric Dirichlet
+ * hyper-parameter lambda (here beta), sub-cluster quantities with a bar.
+ */
+#ifndef DPMM_H
+#define DPMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DPMM_OK 0
+#define DPMM_EINVAL -1      /* bad argument or malformed CSR */
+#define DPMM_ENOMEM -2      /* device or host allocation failed */
+#define DPMM_ECUDA -3       /* a CUDA call failed */
+#define DPMM_ECAPACITY -4   /* K would exceed kmax (splits are rejected instead) */
+#define DPMM_EOVERFLOW -5   /* a 32-bit gene-count statistic would wrap */
+#define DPMM_ETIMEOUT -6    /* a bounded device-side wait gave up */
+#define DPMM_ESTATE -7      /* call not valid in the context's current state */
+
+#define DPMM_ENGINE_AUTO 0      /* pick per sweep from K and the row lengths */
+#define DPMM_ENGINE_CSR_FP32 1  /* warp-per-cell CSR contraction, FP32 */
+#define DPMM_ENGINE_TILE_BF16 2 /* dense 128-cell tiles on tcgen05, BF16 hi/lo */
+
+typedef struct dpmm_ctx dpmm_ctx;
+
+typedef struct dpmm_opts {
+    int32_t kmax;      /* cluster capacity, 1..1024 (default 256) */
+    int32_t engine;    /* DPMM_ENGINE_* (default AUTO) */
+    int32_t split_q;   /* 1 (default): split ratio includes -sum_i log q_i */
+    int32_t chain_id;  /* 0 .. 2^24-1, enters every Philox counter */
+    uint64_t seed;     /* Philox key (default 42) */
+    int32_t reserved[8];
+} dpmm_opts;
+
+/* Fill *opts with the defaults above. */
+void dpmm_default_opts(dpmm_opts* opts);
+
+/*
+ * Create a chain for the N x D count matrix given in CSR form (rows = cells,
+ * columns = genes; Section 2.1 stores the same UMI matrix as V x N).
+ *   indptr  int32[N+1], non-decreasing, indptr[0] = 0, indptr[N] = nnz
+ *   indices int32[nnz], 0 <= indices < D (any order within a row)
+ *   data    int32[nnz], counts >= 0
+ * alpha > 0 (DP concentration), beta > 0 (eq. 28 lambda).  opts may be NULL.
+ * stream: a cudaStream_t to run on, or NULL for a stream owned by the context.
+ * The chain starts with K = 1 (all cells in cluster 0) and fair-coin
+ * sub-labels.  Errors: DPMM_EINVAL (malformed CSR, D < 1, N < 1, alpha or
+ * beta not positive, kmax out of range), DPMM_ENOMEM, DPMM_ECUDA.
+ * Synchronises the stream before returning.
+ */
+int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices,
+              const int32_t* data, int64_t N, int32_t D, double alpha, double beta,
+              const dpmm_opts* opts, void* stream);
+
+/* Release every resource of the context (NULL is ignored). */
+void dpmm_free(dpmm_ctx* ctx);
+
+/*
+ * n_sweeps blocked sweeps of eq. 4 (pi, theta, theta-bar from their Dirichlet
+ * posteriors, eq. 19; every label from pi_k p(x_i | theta_k) and every
+ * sub-label from eq. 8; Sections 2.1-2.3), each followed by removal of empty
+ * clusters.  Asynchronous.
+ */
+int dpmm_sweep(dpmm_ctx* ctx, int32_t n_sweeps);
+
+/*
+ * One move of the split/merge MCMC (Sections 2.3-2.4): mode 1 runs the split
+ * chain (every cluster proposes the split given by its sub-labels, accepted
+ * by eq. 7 with the lgamma-sum likelihood ratio and q(S*|S) from eq. 8),
+ * mode 2 the merge chain (random disjoint pairs, eq. 7 with the eq. 23
+ * proposal ratio), mode 0 picks one of the two by a fair coin.  If
+ * n_accepted is not NULL the call synchronises and stores the number of
+ * accepted moves; otherwise it is asynchronous.
+ */
+int dpmm_split_merge(dpmm_ctx* ctx, int32_t mode, int32_t* n_accepted);
+
+/*
+ * n_steps iterations of (one sweep + one coin-selected split/merge move),
+ * replayed from a CUDA graph captured on first use.  Asynchronous.
+ */
+int dpmm_step(dpmm_ctx* ctx, int32_t n_steps);
+
+/* Copy the current labels (int32[N], in [0, K)) to out and K to *K_out
+ * (either may be NULL).  Synchronises. */
+int dpmm_labels(dpmm_ctx* ctx, int32_t* out, int32_t* K_out);
+
+/*
+ * Per-phase CUDA-event timing.  With enable = 1, every sweep and move records
+ * events on the context stream (also inside the dpmm_step graph, which is
+ * re-captured when the setting changes).  dpmm_phase_times() returns the
+ * device time of each phase of the last step in ms (n <= 5 entries):
+ * [0] pi/theta draws, [1] label + sub-label draw (the contraction, eq. 4
+ * third line and eq. 8), [2] statistics, [3] empty-cluster removal,
+ * [4] split/merge move.  dpmm_phase_times synchronises.
+ */
+int dpmm_profile(dpmm_ctx* ctx, int32_t enable);
+int dpmm_phase_times(dpmm_ctx* ctx, float* ms, int32_t n);
+
+/* Block until all work enqueued on the context's stream is done. */
+int dpmm_sync(dpmm_ctx* ctx);
+
+/* The context's cudaStream_t. */
+void* dpmm_stream(dpmm_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dpmm_last_error(void);
+
+/* ---- state hooks (checkpoint / resume, parity tests) -------------------- */
+
+/*
+ * Read the chain state: labels int32[N], sub-labels uint8[N] (0/1), K, the
+ * sweep counter t and the split/merge call counter m (any output may be
+ * NULL).  Synchronises.
+ */
+int dpmm_get_state(dpmm_ctx* ctx, int32_t* labels, uint8_t* sub, int32_t* K,
+                   int64_t* t, int64_t* m);
+
+/*
+ * Replace the chain state.  labels in [0, K) with every cluster non-empty,
+ * sub-labels 0/1, 1 <= K <= kmax; t, m the counters.  sumlogq (double[K],
+ * per-cluster sum of log q_i used by the next split proposal) may be NULL, in
+ * which case n_k log(1/2) is used.  Statistics are recomputed on the device.
+ * A resumed chain with the same seed continues bit-identically.
+ */
+int dpmm_set_state(dpmm_ctx* ctx, const int32_t* labels, const uint8_t* sub, int32_t K,
+                   int64_t t, int64_t m, const double* sumlogq);
+
+/*
+ * Sufficient statistics of the current state: nsub uint32[K][2] (n-bar),
+ * Ssub uint32[K][2][D] (gene sums per sub-cluster), sumlogq double[K]
+ * (any may be NULL).  Synchronises.
+ */
+int dpmm_get_stats(dpmm_ctx* ctx, uint32_t* nsub, uint32_t* Ssub, double* sumlogq);
+
+/* ---- phase hooks (the two halves of one sweep) --------------------------- */
+
+/* First half of a sweep: draw log pi (K+1 entries) and log theta for the K
+ * clusters and their 2K sub-clusters (eq. 4 first two lines, eq. 19). */
+int dpmm_draw_params(dpmm_ctx* ctx);
+
+/* Second half: labels and sub-labels from the current parameters (eq. 4 third
+ * line, eq. 8), statistics, empty-cluster removal; advances t. */
+int dpmm_assign(dpmm_ctx* ctx);
+
+/*
+ * Current parameters: logpi float[K+1]; logtheta float[3K][D] with row 3k
+ * for cluster k and rows 3k+1, 3k+2 for its sub-clusters 0 and 1.
+ * Synchronises.
+ */
+int dpmm_get_params(dpmm_ctx* ctx, float* logpi, float* logtheta);
+int dpmm_set_params(dpmm_ctx* ctx, const float* logpi, const float* logtheta);
+
+/*
+ * FP32 log-likelihood scores of selected cells under the current parameters,
+ * computed by the same device code as the sweep's contraction:
+ * out float[n][3K]: columns 0..K-1 hold log pi_k + sum_u x_i^u log theta_k^u
+ * (eq. 4 third line with eq. 26), column K + 2k + r holds
+ * sum_u x_i^u log theta-bar_{k,r}^u (the likelihood factor of eq. 8).
+ * Synchronises.
+ */
+int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out);
+
+/* Split/merge diagnostics of the last dpmm_split_merge call: chain (1 split,
+ * 2 merge), and log H per cluster (split; NaN where no proposal) or per pair
+ * (merge, with the pair's cluster indices a < b in pair_ab int32[2][n]).
+ * Arrays hold kmax entries.  Synchronises. */
+int dpmm_debug_moves(dpmm_ctx* ctx, int32_t* chain, double* log_h, int32_t* pair_ab,
+                     int32_t* n_entries);
+
+/* ---- collapsed log marginal likelihood (empirical Bayes) ---------------- */
+
+typedef struct dpmm_logml dpmm_logml;
+
+/*
+ * Statistics n_k, S_ku, T_k of fixed labels for the collapsed log marginal
+ * likelihood (theta integrated out of eq. 12 against eq. 28 with a gene-wise
+ * beta_u, pi out of eq. 10).  CSR as in dpmm_init, labels int32[N] in
+ * [0, K); empty clusters are ignored.  stream as in dpmm_init.
+ */
+int dpmm_logml_create(dpmm_logml** out, const int32_t* indptr, const int32_t* indices,
+                      const int32_t* data, int64_t N, int32_t D, const int32_t* labels,
+                      int32_t K, void* stream);
+void dpmm_logml_free(dpmm_logml* h);
+
+/*
+ * LML = K log alpha + lgamma(alpha) - lgamma(alpha+N) + sum_k lgamma(n_k)
+ *     + sum_k [lgamma(B) - lgamma(B+T_k) + sum_u (lgamma(beta_u+S_ku) - lgamma(beta_u))]
+ * with alpha = exp(log_alpha), beta = exp(log_beta) (float[D]), B = sum beta.
+ * Summed in FP64 on the device.  *logml is a host double.  Synchronises.
+ */
+int dpmm_logml_forward(dpmm_logml* h, double log_alpha, const float* log_beta, double* logml);
+
+/*
+ * Gradient of LML: *grad_log_alpha = K + alpha (psi(alpha) - psi(alpha+N)),
+ * grad_log_beta[u] = beta_u sum_k [psi(B) - psi(B+T_k) + psi(beta_u+S_ku) - psi(beta_u)]
+ * (float[D], FP32 digamma sums).  grad_log_beta may be a device pointer, in
+ * which case the call is asynchronous apart from *grad_log_alpha (host).
+ */
+int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
+                        double* grad_log_alpha, float* grad_log_beta);
+
+/* ---- test hooks ---------------------------------------------------------- */
+
+/* Philox4x32-10 words of the device generator: ctr uint32[n][4] -> out
+ * uint32[n][4] with key (seed lo, seed hi).  Synchronises. */
+int dpmm_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n);
+
+/* The first n 4-word outputs of cuRAND's Philox4_32_10 generator after
+ * curand_init(seed, 0, 0) (consecutive curand4 calls), out uint32[n][4]:
+ * a library reference for the device generator.  Synchronises. */
+int dpmm_debug_curand_philox(uint64_t seed, int64_t n, uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPMM_H */

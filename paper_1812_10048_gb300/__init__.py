@@ -1,0 +1,255 @@
+"""GB300 Para-DPMM: split/merge sampler for Dirichlet-process mixtures of
+multinomials over a cells x genes UMI count matrix (arXiv 1812.10048).
+
+The functions below carry the names of the C ABI in ``include/dpmm.h`` and
+only marshal arguments; every step of the sampler runs in libdpmm.so's CUDA
+kernels.  ``Sampler`` wraps one context for convenience; ``LogMLFunction``
+exposes the collapsed log marginal likelihood to torch.autograd.
+"""
+
+import ctypes
+
+import numpy as np
+
+from ._lib import (DpmmError, ENGINE_AUTO, ENGINE_CSR_FP32, ENGINE_TILE_BF16, check, dpmm_opts,
+                   lib, ptr)
+
+__all__ = [
+    "DpmmError", "Sampler", "LogML", "dpmm_default_opts", "dpmm_init", "dpmm_free", "dpmm_sweep",
+    "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
+    "dpmm_phase_times", "dpmm_get_state",
+    "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
+    "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_moves", "dpmm_logml_create",
+    "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_debug_philox",
+    "dpmm_debug_curand_philox", "ENGINE_AUTO", "ENGINE_CSR_FP32", "ENGINE_TILE_BF16",
+]
+
+
+def _i32(a):
+    if hasattr(a, "data_ptr"):
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def dpmm_default_opts(**overrides):
+    o = dpmm_opts()
+    lib().dpmm_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def dpmm_init(indptr, indices, data, N, D, alpha, beta, opts=None, stream=None):
+    """Create a chain; arrays may be numpy (host) or torch tensors (host or device)."""
+    indptr, indices, data = _i32(indptr), _i32(indices), _i32(data)
+    h = ctypes.c_void_p()
+    o = opts if opts is not None else dpmm_default_opts()
+    check(lib().dpmm_init(ctypes.byref(h), ptr(indptr), ptr(indices), ptr(data), int(N), int(D),
+                          float(alpha), float(beta), ctypes.byref(o),
+                          ctypes.c_void_p(stream) if stream else None))
+    return h
+
+
+def dpmm_free(ctx):
+    lib().dpmm_free(ctx)
+
+
+def dpmm_sweep(ctx, n_sweeps=1):
+    check(lib().dpmm_sweep(ctx, int(n_sweeps)))
+
+
+def dpmm_split_merge(ctx, mode=0, want_count=True):
+    n = ctypes.c_int32(0)
+    check(lib().dpmm_split_merge(ctx, int(mode), ctypes.byref(n) if want_count else None))
+    return n.value if want_count else None
+
+
+def dpmm_step(ctx, n_steps=1):
+    check(lib().dpmm_step(ctx, int(n_steps)))
+
+
+def dpmm_labels(ctx, N):
+    out = np.empty(int(N), dtype=np.int32)
+    K = ctypes.c_int32(0)
+    check(lib().dpmm_labels(ctx, ptr(out), ctypes.byref(K)))
+    return out, K.value
+
+
+def dpmm_sync(ctx):
+    check(lib().dpmm_sync(ctx))
+
+
+def dpmm_profile(ctx, enable=True):
+    check(lib().dpmm_profile(ctx, int(bool(enable))))
+
+
+def dpmm_phase_times(ctx, n=5):
+    out = np.zeros(int(n), dtype=np.float32)
+    check(lib().dpmm_phase_times(ctx, ptr(out), int(n)))
+    return out
+
+
+def dpmm_stream(ctx):
+    return lib().dpmm_stream(ctx)
+
+
+def dpmm_get_state(ctx, N):
+    labels = np.empty(int(N), dtype=np.int32)
+    sub = np.empty(int(N), dtype=np.uint8)
+    K, t, m = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    check(lib().dpmm_get_state(ctx, ptr(labels), ptr(sub), ctypes.byref(K), ctypes.byref(t),
+                               ctypes.byref(m)))
+    return labels, sub, K.value, t.value, m.value
+
+
+def dpmm_set_state(ctx, labels, sub, K, t=0, m=0, sumlogq=None):
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    sub = np.ascontiguousarray(sub, dtype=np.uint8)
+    sq = None if sumlogq is None else np.ascontiguousarray(sumlogq, dtype=np.float64)
+    check(lib().dpmm_set_state(ctx, ptr(labels), ptr(sub), int(K), int(t), int(m), ptr(sq)))
+
+
+def dpmm_get_stats(ctx, K, D):
+    nsub = np.empty((K, 2), dtype=np.uint32)
+    Ssub = np.empty((K, 2, D), dtype=np.uint32)
+    sumlogq = np.empty(K, dtype=np.float64)
+    check(lib().dpmm_get_stats(ctx, ptr(nsub), ptr(Ssub), ptr(sumlogq)))
+    return nsub, Ssub, sumlogq
+
+
+def dpmm_draw_params(ctx):
+    check(lib().dpmm_draw_params(ctx))
+
+
+def dpmm_assign(ctx):
+    check(lib().dpmm_assign(ctx))
+
+
+def dpmm_get_params(ctx, K, D):
+    logpi = np.empty(K + 1, dtype=np.float32)
+    logtheta = np.empty((3 * K, D), dtype=np.float32)
+    check(lib().dpmm_get_params(ctx, ptr(logpi), ptr(logtheta)))
+    return logpi, logtheta
+
+
+def dpmm_set_params(ctx, logpi, logtheta):
+    logpi = np.ascontiguousarray(logpi, dtype=np.float32)
+    logtheta = np.ascontiguousarray(logtheta, dtype=np.float32)
+    check(lib().dpmm_set_params(ctx, ptr(logpi), ptr(logtheta)))
+
+
+def dpmm_debug_scores(ctx, cells, K):
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    out = np.empty((cells.size, 3 * K), dtype=np.float32)
+    check(lib().dpmm_debug_scores(ctx, ptr(cells), int(cells.size), ptr(out)))
+    return out
+
+
+def dpmm_debug_moves(ctx, kmax):
+    chain, n = ctypes.c_int32(0), ctypes.c_int32(0)
+    log_h = np.empty(kmax, dtype=np.float64)
+    pair_ab = np.empty((kmax, 2), dtype=np.int32)
+    check(lib().dpmm_debug_moves(ctx, ctypes.byref(chain), ptr(log_h), ptr(pair_ab),
+                                 ctypes.byref(n)))
+    return chain.value, log_h[:n.value], pair_ab[:n.value]
+
+
+def dpmm_logml_create(indptr, indices, data, N, D, labels, K, stream=None):
+    indptr, indices, data, labels = _i32(indptr), _i32(indices), _i32(data), _i32(labels)
+    h = ctypes.c_void_p()
+    check(lib().dpmm_logml_create(ctypes.byref(h), ptr(indptr), ptr(indices), ptr(data), int(N),
+                                  int(D), ptr(labels), int(K),
+                                  ctypes.c_void_p(stream) if stream else None))
+    return h
+
+
+def dpmm_logml_free(h):
+    lib().dpmm_logml_free(h)
+
+
+def dpmm_logml_forward(h, log_alpha, log_beta):
+    out = ctypes.c_double(0.0)
+    check(lib().dpmm_logml_forward(h, float(log_alpha), ptr(log_beta), ctypes.byref(out)))
+    return out.value
+
+
+def dpmm_logml_backward(h, log_alpha, log_beta, grad_log_beta):
+    ga = ctypes.c_double(0.0)
+    check(lib().dpmm_logml_backward(h, float(log_alpha), ptr(log_beta), ctypes.byref(ga),
+                                    ptr(grad_log_beta)))
+    return ga.value
+
+
+def dpmm_debug_philox(ctr, seed):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    check(lib().dpmm_debug_philox(ptr(ctr), int(seed), ptr(out), int(ctr.shape[0])))
+    return out
+
+
+def dpmm_debug_curand_philox(seed, n):
+    out = np.empty((int(n), 4), dtype=np.uint32)
+    check(lib().dpmm_debug_curand_philox(int(seed), int(n), ptr(out)))
+    return out
+
+
+class Sampler:
+    """One chain of the sampler on the current CUDA device."""
+
+    def __init__(self, indptr, indices, data, N, D, alpha, beta, *, kmax=256, seed=42,
+                 chain_id=0, engine=ENGINE_AUTO, split_q=True, stream=None):
+        self.N, self.D, self.kmax = int(N), int(D), int(kmax)
+        opts = dpmm_default_opts(kmax=kmax, seed=seed, chain_id=chain_id, engine=engine,
+                                 split_q=int(bool(split_q)))
+        self.ctx = dpmm_init(indptr, indices, data, N, D, alpha, beta, opts, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            dpmm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        dpmm_sweep(self.ctx, n)
+
+    def split_merge(self, mode=0):
+        return dpmm_split_merge(self.ctx, mode)
+
+    def step(self, n=1):
+        dpmm_step(self.ctx, n)
+
+    def labels(self):
+        return dpmm_labels(self.ctx, self.N)
+
+    @property
+    def K(self):
+        return self.labels_K()
+
+    def labels_K(self):
+        K = ctypes.c_int32(0)
+        check(lib().dpmm_labels(self.ctx, None, ctypes.byref(K)))
+        return K.value
+
+    def get_state(self):
+        return dpmm_get_state(self.ctx, self.N)
+
+    def set_state(self, labels, sub, K, t=0, m=0, sumlogq=None):
+        dpmm_set_state(self.ctx, labels, sub, K, t, m, sumlogq)
+
+    def stats(self):
+        return dpmm_get_stats(self.ctx, self.labels_K(), self.D)
+
+    def sync(self):
+        dpmm_sync(self.ctx)
+
+    @property
+    def stream(self):
+        return dpmm_stream(self.ctx)
+
+
+from .autograd import LogML, LogMLFunction  # noqa: E402

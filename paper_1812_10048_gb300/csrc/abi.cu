@@ -1,0 +1,749 @@
+// C ABI of the library (include/dpmm.h): argument checking, device memory,
+// the sweep / move pipelines and the CUDA graph of dpmm_step.
+#include <curand_kernel.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "logml.cuh"
+
+using namespace dpmm;
+
+struct dpmm_ctx {
+    Ctx c;
+};
+struct dpmm_logml {
+    LmlPlan p;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(expr)                                                                         \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return fail(DPMM_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e),     \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, std::max<size_t>(1, count) * sizeof(T));
+}
+
+// Copy n elements from a host or device pointer into a host vector.
+template <typename T>
+int fetch(std::vector<T>& dst, const T* src, size_t n) {
+    dst.resize(n);
+    if (n == 0) return DPMM_OK;
+    CK(cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDefault));
+    return DPMM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Host-side CSR checks (shared by dpmm_init and dpmm_logml_create).
+int check_csr(const std::vector<int32_t>& indptr, const std::vector<int32_t>& idx,
+              const std::vector<int32_t>& val, int64_t N, int32_t D, int32_t* max_count) {
+    if (indptr[0] != 0) return fail(DPMM_EINVAL, "indptr[0] = %d, expected 0", indptr[0]);
+    for (int64_t i = 0; i < N; ++i)
+        if (indptr[i + 1] < indptr[i])
+            return fail(DPMM_EINVAL, "indptr decreases at row %lld", (long long)i);
+    int32_t mx = 0;
+    std::vector<unsigned long long> colsum(D, 0ull);
+    for (size_t e = 0; e < idx.size(); ++e) {
+        if (idx[e] < 0 || idx[e] >= D)
+            return fail(DPMM_EINVAL, "column index %d out of [0, %d) at entry %zu", idx[e], D, e);
+        if (val[e] < 0) return fail(DPMM_EINVAL, "negative count %d at entry %zu", val[e], e);
+        mx = std::max(mx, val[e]);
+        colsum[idx[e]] += (unsigned long long)val[e];
+    }
+    for (int32_t u = 0; u < D; ++u)
+        if (colsum[u] >= (1ull << 32))
+            return fail(DPMM_EOVERFLOW, "gene %d sums to %llu >= 2^32 (32-bit statistics)", u,
+                        colsum[u]);
+    *max_count = mx;
+    return DPMM_OK;
+}
+
+int sync_scalars(Ctx& c) {
+    CK(cudaMemcpyAsync(c.sc_host, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return DPMM_OK;
+}
+
+void free_ctx(Ctx& c) {
+    if (c.step_exec) cudaGraphExecDestroy(c.step_exec);
+    for (cudaEvent_t& e : c.ev)
+        if (e) cudaEventDestroy(e);
+    void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
+                    c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
+                    c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c.sc_host) cudaFreeHost(c.sc_host);
+    if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+}
+
+#define MARK(i)                                                    \
+    do {                                                           \
+        if (c.profile) CK(cudaEventRecord(c.ev[i], c.stream));     \
+    } while (0)
+
+int enqueue_sweep(Ctx& c) {
+    MARK(0);
+    CK(launch_draw_params(c));
+    MARK(1);
+    CK(launch_assign(c));
+    MARK(2);
+    CK(launch_stats(c, nullptr, c.acc_nsub, c.acc_Ssub, nullptr));
+    MARK(3);
+    CK(launch_plan(c, PLAN_COMPACT));
+    CK(launch_apply_plan(c, PLAN_COMPACT));
+    MARK(4);
+    return DPMM_OK;
+}
+
+int enqueue_assign_half(Ctx& c) {
+    CK(launch_assign(c));
+    CK(launch_stats(c, nullptr, c.acc_nsub, c.acc_Ssub, nullptr));
+    CK(launch_plan(c, PLAN_COMPACT));
+    CK(launch_apply_plan(c, PLAN_COMPACT));
+    return DPMM_OK;
+}
+
+int enqueue_moves(Ctx& c, int32_t mode) {
+    MARK(4);
+    CK(launch_move_score(c, mode));
+    CK(launch_plan(c, PLAN_SPLIT));
+    CK(launch_apply_plan(c, PLAN_SPLIT));
+    MARK(5);
+    return DPMM_OK;
+}
+
+// Recompute the main statistics from the current cell states.
+int recount_all(Ctx& c) {
+    CK(cudaMemsetAsync(c.nsub, 0, sizeof(uint32_t) * 2 * c.kmax, c.stream));
+    CK(cudaMemsetAsync(c.Ssub, 0, sizeof(uint32_t) * 2 * (size_t)c.kmax * c.D, c.stream));
+    CK(launch_stats(c, nullptr, c.nsub, c.Ssub, nullptr));
+    return DPMM_OK;
+}
+
+#define CHECK_CTX(ctx)                                                  \
+    do {                                                                \
+        if (!(ctx)) return fail(DPMM_EINVAL, "null context");           \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+const char* dpmm_last_error(void) { return g_err.c_str(); }
+
+void dpmm_default_opts(dpmm_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->kmax = 256;
+    o->engine = DPMM_ENGINE_AUTO;
+    o->split_q = 1;
+    o->chain_id = 0;
+    o->seed = 42;
+}
+
+int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, const int32_t* data,
+              int64_t N, int32_t D, double alpha, double beta, const dpmm_opts* opts,
+              void* stream) {
+    if (!out) return fail(DPMM_EINVAL, "out is null");
+    *out = nullptr;
+    if (N < 1) return fail(DPMM_EINVAL, "N = %lld, need N >= 1", (long long)N);
+    if (N >= (1ll << 31)) return fail(DPMM_EINVAL, "N = %lld exceeds 2^31 - 1", (long long)N);
+    if (D < 1) return fail(DPMM_EINVAL, "D = %d, need D >= 1", D);
+    if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(DPMM_EINVAL, "alpha must be > 0");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(DPMM_EINVAL, "beta must be > 0");
+    if (!indptr) return fail(DPMM_EINVAL, "indptr is null");
+    dpmm_opts o;
+    dpmm_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.kmax < 1 || o.kmax > kMaxKmax)
+        return fail(DPMM_EINVAL, "kmax = %d outside [1, %d]", o.kmax, kMaxKmax);
+    if (o.chain_id < 0 || o.chain_id >= (1 << 24))
+        return fail(DPMM_EINVAL, "chain_id = %d outside [0, 2^24)", o.chain_id);
+
+    std::vector<int32_t> hptr, hidx, hval;
+    int rc;
+    if ((rc = fetch(hptr, indptr, (size_t)N + 1))) return rc;
+    const int64_t nnz = hptr[N];
+    if (nnz < 0) return fail(DPMM_EINVAL, "indptr[N] = %lld", (long long)nnz);
+    if (nnz > 0 && (!indices || !data)) return fail(DPMM_EINVAL, "indices/data are null");
+    if ((rc = fetch(hidx, indices, (size_t)nnz))) return rc;
+    if ((rc = fetch(hval, data, (size_t)nnz))) return rc;
+    int32_t max_count = 0;
+    if ((rc = check_csr(hptr, hidx, hval, N, D, &max_count))) return rc;
+
+    dpmm_ctx* h = new (std::nothrow) dpmm_ctx();
+    if (!h) return fail(DPMM_ENOMEM, "host allocation failed");
+    Ctx& c = h->c;
+    c.N = N;
+    c.D = D;
+    c.nnz = nnz;
+    c.alpha = alpha;
+    c.beta = beta;
+    c.opts = o;
+    c.kmax = o.kmax;
+    c.packed = D <= 65536 && max_count <= 65535;
+
+    auto bail = [&](int code) {
+        free_ctx(c);
+        delete h;
+        return code;
+    };
+#define CKI(expr)                                                                            \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return bail(fail(_e == cudaErrorMemoryAllocation ? DPMM_ENOMEM : DPMM_ECUDA,     \
+                             "%s: %s", #expr, cudaGetErrorString(_e)));                      \
+    } while (0)
+
+    CKI(cudaGetDevice(&c.device));
+    CKI(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+    if (stream) {
+        c.stream = (cudaStream_t)stream;
+    } else {
+        CKI(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        c.own_stream = true;
+    }
+    const size_t K2 = 2 * (size_t)c.kmax;
+    CKI(dalloc(&c.indptr, (size_t)N + 1));
+    if (c.packed) {
+        CKI(dalloc(&c.entries, (size_t)nnz));
+    } else {
+        CKI(dalloc(&c.cols, (size_t)nnz));
+        CKI(dalloc(&c.counts, (size_t)nnz));
+    }
+    CKI(dalloc(&c.state, (size_t)N));
+    CKI(dalloc(&c.sc, 1));
+    CKI(cudaMallocHost((void**)&c.sc_host, sizeof(DevScalars)));
+    CKI(dalloc(&c.nsub, K2));
+    CKI(dalloc(&c.Ssub, K2 * D));
+    CKI(dalloc(&c.sumlogq, (size_t)c.kmax));
+    CKI(dalloc(&c.acc_nsub, K2));
+    CKI(dalloc(&c.acc_Ssub, K2 * D));
+    CKI(dalloc(&c.acc_sumlogq, (size_t)c.kmax));
+    CKI(dalloc(&c.logpi, (size_t)c.kmax + 1));
+    CKI(dalloc(&c.Lc, (size_t)c.kmax * D));
+    CKI(dalloc(&c.Ls, K2 * D));
+    CKI(dalloc(&c.lmap, K2));
+    CKI(dalloc(&c.desc, K2));
+    CKI(dalloc(&c.reinit, (size_t)c.kmax));
+    CKI(dalloc(&c.decide, (size_t)c.kmax));
+    CKI(dalloc(&c.log_h, (size_t)c.kmax));
+    CKI(dalloc(&c.pair_ab, K2));
+
+    CKI(cudaMemcpyAsync(c.indptr, hptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice,
+                        c.stream));
+    if (c.packed) {
+        std::vector<uint32_t> packed((size_t)nnz);
+        for (int64_t e = 0; e < nnz; ++e)
+            packed[e] = ((uint32_t)hidx[e] << 16) | (uint32_t)hval[e];
+        CKI(cudaMemcpyAsync(c.entries, packed.data(), sizeof(uint32_t) * nnz,
+                            cudaMemcpyHostToDevice, c.stream));
+        CKI(cudaStreamSynchronize(c.stream));
+    } else if (nnz > 0) {
+        CKI(cudaMemcpyAsync(c.cols, hidx.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice,
+                            c.stream));
+        CKI(cudaMemcpyAsync(c.counts, hval.data(), sizeof(int32_t) * nnz,
+                            cudaMemcpyHostToDevice, c.stream));
+    }
+    CKI(cudaMemsetAsync(c.acc_nsub, 0, sizeof(uint32_t) * K2, c.stream));
+    CKI(cudaMemsetAsync(c.acc_Ssub, 0, sizeof(uint32_t) * K2 * D, c.stream));
+    CKI(cudaMemsetAsync(c.acc_sumlogq, 0, sizeof(double) * c.kmax, c.stream));
+    CKI(cudaMemsetAsync(c.sumlogq, 0, sizeof(double) * c.kmax, c.stream));
+    CKI(cudaMemsetAsync(c.reinit, 0, c.kmax, c.stream));
+    std::memset(c.sc_host, 0, sizeof(DevScalars));
+    c.sc_host->K = 1;
+    c.sc_host->K_new = 1;
+    CKI(cudaMemcpyAsync(c.sc, c.sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c.stream));
+    CKI(configure_launches(c));
+    CKI(launch_init_state(c));
+    if (recount_all(c) != DPMM_OK) return bail(DPMM_ECUDA);
+    const double s0 = (double)N * std::log(0.5);
+    CKI(cudaMemcpyAsync(c.sumlogq, &s0, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    CKI(cudaStreamSynchronize(c.stream));
+#undef CKI
+    *out = h;
+    return DPMM_OK;
+}
+
+void dpmm_free(dpmm_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->c.stream);
+    free_ctx(ctx->c);
+    delete ctx;
+}
+
+int dpmm_sweep(dpmm_ctx* ctx, int32_t n) {
+    CHECK_CTX(ctx);
+    if (n < 0) return fail(DPMM_EINVAL, "n_sweeps < 0");
+    for (int32_t i = 0; i < n; ++i) {
+        int rc = enqueue_sweep(ctx->c);
+        if (rc) return rc;
+    }
+    return DPMM_OK;
+}
+
+int dpmm_split_merge(dpmm_ctx* ctx, int32_t mode, int32_t* n_accepted) {
+    CHECK_CTX(ctx);
+    if (mode < 0 || mode > 2) return fail(DPMM_EINVAL, "mode %d not in {0, 1, 2}", mode);
+    int rc = enqueue_moves(ctx->c, mode);
+    if (rc) return rc;
+    if (n_accepted) {
+        if ((rc = sync_scalars(ctx->c))) return rc;
+        *n_accepted = ctx->c.sc_host->n_accepted;
+    }
+    return DPMM_OK;
+}
+
+int dpmm_step(dpmm_ctx* ctx, int32_t n) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (n < 0) return fail(DPMM_EINVAL, "n_steps < 0");
+    if (c.step_exec && c.graph_profiled != c.profile) {
+        cudaGraphExecDestroy(c.step_exec);
+        c.step_exec = nullptr;
+    }
+    if (!c.step_exec) {
+        c.graph_profiled = c.profile;
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_sweep(c);
+        if (!rc) rc = enqueue_moves(c, 0);
+        cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+        if (rc) return rc;
+        CK(e);
+        e = cudaGraphInstantiate(&c.step_exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    for (int32_t i = 0; i < n; ++i) CK(cudaGraphLaunch(c.step_exec, c.stream));
+    return DPMM_OK;
+}
+
+int dpmm_labels(dpmm_ctx* ctx, int32_t* out, int32_t* K_out) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    int rc;
+    if (out) {
+        std::vector<uint32_t> st((size_t)c.N);
+        CK(cudaMemcpyAsync(st.data(), c.state, sizeof(uint32_t) * c.N, cudaMemcpyDeviceToHost,
+                           c.stream));
+        if ((rc = sync_scalars(c))) return rc;
+        for (int64_t i = 0; i < c.N; ++i) out[i] = (int32_t)state_label(st[i]);
+    } else if ((rc = sync_scalars(c))) {
+        return rc;
+    }
+    if (K_out) *K_out = c.sc_host->K;
+    return DPMM_OK;
+}
+
+int dpmm_profile(dpmm_ctx* ctx, int32_t enable) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (enable && !c.ev[0])
+        for (cudaEvent_t& e : c.ev) CK(cudaEventCreate(&e));
+    c.profile = enable != 0;
+    return DPMM_OK;
+}
+
+int dpmm_phase_times(dpmm_ctx* ctx, float* ms, int32_t n) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (!c.ev[0]) return fail(DPMM_ESTATE, "profiling was never enabled");
+    if (!ms || n < 0 || n > 5) return fail(DPMM_EINVAL, "need ms and 0 <= n <= 5");
+    CK(cudaStreamSynchronize(c.stream));
+    for (int i = 0; i < n; ++i) CK(cudaEventElapsedTime(&ms[i], c.ev[i], c.ev[i + 1]));
+    return DPMM_OK;
+}
+
+int dpmm_sync(dpmm_ctx* ctx) {
+    CHECK_CTX(ctx);
+    CK(cudaStreamSynchronize(ctx->c.stream));
+    return DPMM_OK;
+}
+
+void* dpmm_stream(dpmm_ctx* ctx) { return ctx ? (void*)ctx->c.stream : nullptr; }
+
+int dpmm_get_state(dpmm_ctx* ctx, int32_t* labels, uint8_t* sub, int32_t* K, int64_t* t,
+                   int64_t* m) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    std::vector<uint32_t> st;
+    if (labels || sub) {
+        st.resize((size_t)c.N);
+        CK(cudaMemcpyAsync(st.data(), c.state, sizeof(uint32_t) * c.N, cudaMemcpyDeviceToHost,
+                           c.stream));
+    }
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    for (int64_t i = 0; i < (int64_t)st.size(); ++i) {
+        if (labels) labels[i] = (int32_t)state_label(st[i]);
+        if (sub) sub[i] = (uint8_t)state_sub(st[i]);
+    }
+    if (K) *K = c.sc_host->K;
+    if (t) *t = c.sc_host->t;
+    if (m) *m = c.sc_host->m;
+    return DPMM_OK;
+}
+
+int dpmm_set_state(dpmm_ctx* ctx, const int32_t* labels, const uint8_t* sub, int32_t K,
+                   int64_t t, int64_t m, const double* sumlogq) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (K < 1 || K > c.kmax) return fail(DPMM_EINVAL, "K = %d outside [1, %d]", K, c.kmax);
+    if (!labels || !sub) return fail(DPMM_EINVAL, "labels/sub are null");
+    if (t < 0 || t > 0xFFFFFFFFll || m < 0 || m > 0xFFFFFFFFll)
+        return fail(DPMM_EINVAL, "counters out of range");
+    std::vector<int32_t> lab;
+    std::vector<uint8_t> sb;
+    int rc;
+    if ((rc = fetch(lab, labels, (size_t)c.N))) return rc;
+    if ((rc = fetch(sb, sub, (size_t)c.N))) return rc;
+    std::vector<uint32_t> st((size_t)c.N);
+    std::vector<int64_t> nk(K, 0);
+    for (int64_t i = 0; i < c.N; ++i) {
+        if (lab[i] < 0 || lab[i] >= K)
+            return fail(DPMM_EINVAL, "label %d of cell %lld outside [0, %d)", lab[i],
+                        (long long)i, K);
+        if (sb[i] > 1) return fail(DPMM_EINVAL, "sub-label of cell %lld not 0/1", (long long)i);
+        st[i] = pack_state((uint32_t)lab[i], sb[i]);
+        nk[lab[i]]++;
+    }
+    for (int32_t k = 0; k < K; ++k)
+        if (!nk[k]) return fail(DPMM_EINVAL, "cluster %d is empty", k);
+    std::vector<double> sq(K);
+    if (sumlogq) {
+        if ((rc = fetch(sq, sumlogq, (size_t)K))) return rc;
+    } else {
+        for (int32_t k = 0; k < K; ++k) sq[k] = (double)nk[k] * std::log(0.5);
+    }
+    CK(cudaStreamSynchronize(c.stream));
+    CK(cudaMemcpy(c.state, st.data(), sizeof(uint32_t) * c.N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.sumlogq, sq.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
+    if ((rc = sync_scalars(c))) return rc;
+    c.sc_host->K = K;
+    c.sc_host->K_new = K;
+    c.sc_host->t = (uint32_t)t;
+    c.sc_host->m = (uint32_t)m;
+    CK(cudaMemcpy(c.sc, c.sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice));
+    if ((rc = recount_all(c))) return rc;
+    CK(cudaStreamSynchronize(c.stream));
+    return DPMM_OK;
+}
+
+int dpmm_get_stats(dpmm_ctx* ctx, uint32_t* nsub, uint32_t* Ssub, double* sumlogq) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    const int K = c.sc_host->K;
+    if (nsub) CK(cudaMemcpy(nsub, c.nsub, sizeof(uint32_t) * 2 * K, cudaMemcpyDefault));
+    if (Ssub) CK(cudaMemcpy(Ssub, c.Ssub, sizeof(uint32_t) * 2 * (size_t)K * c.D, cudaMemcpyDefault));
+    if (sumlogq) CK(cudaMemcpy(sumlogq, c.sumlogq, sizeof(double) * K, cudaMemcpyDefault));
+    return DPMM_OK;
+}
+
+int dpmm_draw_params(dpmm_ctx* ctx) {
+    CHECK_CTX(ctx);
+    CK(launch_draw_params(ctx->c));
+    return DPMM_OK;
+}
+
+int dpmm_assign(dpmm_ctx* ctx) {
+    CHECK_CTX(ctx);
+    return enqueue_assign_half(ctx->c);
+}
+
+int dpmm_get_params(dpmm_ctx* ctx, float* logpi, float* logtheta) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    const int K = c.sc_host->K;
+    if (logpi) CK(cudaMemcpy(logpi, c.logpi, sizeof(float) * (K + 1), cudaMemcpyDefault));
+    if (logtheta) {
+        std::vector<float> lc((size_t)c.kmax * c.D), ls(2 * (size_t)c.kmax * c.D);
+        CK(cudaMemcpy(lc.data(), c.Lc, sizeof(float) * lc.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ls.data(), c.Ls, sizeof(float) * ls.size(), cudaMemcpyDeviceToHost));
+        std::vector<float> out(3 * (size_t)K * c.D);
+        for (int k = 0; k < K; ++k)
+            for (int u = 0; u < c.D; ++u) {
+                out[(size_t)(3 * k) * c.D + u] = lc[(size_t)u * c.kmax + k];
+                out[(size_t)(3 * k + 1) * c.D + u] = ls[((size_t)u * c.kmax + k) * 2];
+                out[(size_t)(3 * k + 2) * c.D + u] = ls[((size_t)u * c.kmax + k) * 2 + 1];
+            }
+        CK(cudaMemcpy(logtheta, out.data(), sizeof(float) * out.size(), cudaMemcpyDefault));
+    }
+    return DPMM_OK;
+}
+
+int dpmm_set_params(dpmm_ctx* ctx, const float* logpi, const float* logtheta) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (!logpi || !logtheta) return fail(DPMM_EINVAL, "logpi/logtheta are null");
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    const int K = c.sc_host->K;
+    std::vector<float> lt, lp;
+    if ((rc = fetch(lp, logpi, (size_t)K + 1))) return rc;
+    if ((rc = fetch(lt, logtheta, 3 * (size_t)K * c.D))) return rc;
+    std::vector<float> lc((size_t)c.kmax * c.D, 0.0f), ls(2 * (size_t)c.kmax * c.D, 0.0f);
+    for (int k = 0; k < K; ++k)
+        for (int u = 0; u < c.D; ++u) {
+            lc[(size_t)u * c.kmax + k] = lt[(size_t)(3 * k) * c.D + u];
+            ls[((size_t)u * c.kmax + k) * 2] = lt[(size_t)(3 * k + 1) * c.D + u];
+            ls[((size_t)u * c.kmax + k) * 2 + 1] = lt[(size_t)(3 * k + 2) * c.D + u];
+        }
+    CK(cudaMemcpy(c.logpi, lp.data(), sizeof(float) * (K + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.Lc, lc.data(), sizeof(float) * lc.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.Ls, ls.data(), sizeof(float) * ls.size(), cudaMemcpyHostToDevice));
+    return DPMM_OK;
+}
+
+int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (n <= 0 || !cells || !out) return fail(DPMM_EINVAL, "bad cells/out");
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    const int K = c.sc_host->K;
+    std::vector<int32_t> hc;
+    if ((rc = fetch(hc, cells, (size_t)n))) return rc;
+    for (int32_t i = 0; i < n; ++i)
+        if (hc[i] < 0 || hc[i] >= c.N) return fail(DPMM_EINVAL, "cell %d out of range", hc[i]);
+    int32_t* dcells = nullptr;
+    float* dout = nullptr;
+    CK(dalloc(&dcells, (size_t)n));
+    cudaError_t e = dalloc(&dout, (size_t)n * 3 * K);
+    if (e == cudaSuccess) e = cudaMemcpy(dcells, hc.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_debug_scores(c, dcells, n, dout);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, dout, sizeof(float) * (size_t)n * 3 * K, cudaMemcpyDefault);
+    cudaFree(dcells);
+    if (dout) cudaFree(dout);
+    CK(e);
+    return DPMM_OK;
+}
+
+int dpmm_debug_moves(dpmm_ctx* ctx, int32_t* chain, double* log_h, int32_t* pair_ab,
+                     int32_t* n_entries) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    if (chain) *chain = c.sc_host->chain_sel;
+    if (n_entries) *n_entries = c.sc_host->n_entries;
+    if (log_h) CK(cudaMemcpy(log_h, c.log_h, sizeof(double) * c.kmax, cudaMemcpyDefault));
+    if (pair_ab) CK(cudaMemcpy(pair_ab, c.pair_ab, sizeof(int32_t) * 2 * c.kmax, cudaMemcpyDefault));
+    return DPMM_OK;
+}
+
+// ---- collapsed log marginal likelihood -----------------------------------
+
+static void free_lml(LmlPlan& p) {
+    void* ptrs[] = {p.indptr, p.cols, p.counts, p.labels, p.n, p.S, p.T, p.common, p.out, p.grad,
+                    p.beta_stage};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
+}
+
+int dpmm_logml_create(dpmm_logml** out, const int32_t* indptr, const int32_t* indices,
+                      const int32_t* data, int64_t N, int32_t D, const int32_t* labels, int32_t K,
+                      void* stream) {
+    if (!out) return fail(DPMM_EINVAL, "out is null");
+    *out = nullptr;
+    if (N < 1 || D < 1 || K < 1) return fail(DPMM_EINVAL, "need N, D, K >= 1");
+    if (N >= (1ll << 31)) return fail(DPMM_EINVAL, "N exceeds 2^31 - 1");
+    if (!indptr || !labels) return fail(DPMM_EINVAL, "indptr/labels are null");
+    std::vector<int32_t> hptr, hidx, hval, hlab;
+    int rc;
+    if ((rc = fetch(hptr, indptr, (size_t)N + 1))) return rc;
+    const int64_t nnz = hptr[N];
+    if (nnz < 0) return fail(DPMM_EINVAL, "indptr[N] < 0");
+    if (nnz > 0 && (!indices || !data)) return fail(DPMM_EINVAL, "indices/data are null");
+    if ((rc = fetch(hidx, indices, (size_t)nnz))) return rc;
+    if ((rc = fetch(hval, data, (size_t)nnz))) return rc;
+    if ((rc = fetch(hlab, labels, (size_t)N))) return rc;
+    int32_t mx;
+    if ((rc = check_csr(hptr, hidx, hval, N, D, &mx))) return rc;
+    for (int64_t i = 0; i < N; ++i)
+        if (hlab[i] < 0 || hlab[i] >= K)
+            return fail(DPMM_EINVAL, "label %d of cell %lld outside [0, %d)", hlab[i],
+                        (long long)i, K);
+    dpmm_logml* h = new (std::nothrow) dpmm_logml();
+    if (!h) return fail(DPMM_ENOMEM, "host allocation failed");
+    LmlPlan& p = h->p;
+    p.N = N;
+    p.D = D;
+    p.K = K;
+    auto bail = [&](cudaError_t e, const char* what) {
+        free_lml(p);
+        delete h;
+        return fail(e == cudaErrorMemoryAllocation ? DPMM_ENOMEM : DPMM_ECUDA, "%s: %s", what,
+                    cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    int dev;
+    if ((e = cudaGetDevice(&dev))) return bail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev)))
+        return bail(e, "attribute");
+    if (stream) {
+        p.stream = (cudaStream_t)stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking)))
+            return bail(e, "stream");
+        p.own_stream = true;
+    }
+    if ((e = dalloc(&p.indptr, (size_t)N + 1)) || (e = dalloc(&p.cols, (size_t)nnz)) ||
+        (e = dalloc(&p.counts, (size_t)nnz)) || (e = dalloc(&p.labels, (size_t)N)) ||
+        (e = dalloc(&p.n, (size_t)K)) || (e = dalloc(&p.S, (size_t)K * D)) ||
+        (e = dalloc(&p.T, (size_t)K)) || (e = dalloc(&p.common, 1)) || (e = dalloc(&p.out, 2)) ||
+        (e = dalloc(&p.grad, (size_t)D)) || (e = dalloc(&p.beta_stage, (size_t)D)))
+        return bail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(p.indptr, hptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice)) ||
+        (nnz && (e = cudaMemcpy(p.cols, hidx.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice))) ||
+        (nnz && (e = cudaMemcpy(p.counts, hval.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice))) ||
+        (e = cudaMemcpy(p.labels, hlab.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice)))
+        return bail(e, "upload");
+    if ((e = lml_compute_stats(p)) || (e = cudaStreamSynchronize(p.stream)))
+        return bail(e, "statistics");
+    *out = h;
+    return DPMM_OK;
+}
+
+void dpmm_logml_free(dpmm_logml* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->p.stream);
+    free_lml(h->p);
+    delete h;
+}
+
+static int stage_beta(LmlPlan& p, const float* log_beta, const float** dev) {
+    if (!log_beta) return fail(DPMM_EINVAL, "log_beta is null");
+    if (is_device_ptr(log_beta)) {
+        *dev = log_beta;
+        return DPMM_OK;
+    }
+    CK(cudaMemcpyAsync(p.beta_stage, log_beta, sizeof(float) * p.D, cudaMemcpyHostToDevice,
+                       p.stream));
+    *dev = p.beta_stage;
+    return DPMM_OK;
+}
+
+int dpmm_logml_forward(dpmm_logml* h, double log_alpha, const float* log_beta, double* logml) {
+    if (!h || !logml) return fail(DPMM_EINVAL, "null argument");
+    LmlPlan& p = h->p;
+    const float* lb;
+    int rc = stage_beta(p, log_beta, &lb);
+    if (rc) return rc;
+    CK(lml_forward(p, log_alpha, lb, p.out));
+    CK(cudaMemcpyAsync(logml, p.out, sizeof(double), cudaMemcpyDefault, p.stream));
+    CK(cudaStreamSynchronize(p.stream));
+    return DPMM_OK;
+}
+
+int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
+                        double* grad_log_alpha, float* grad_log_beta) {
+    if (!h || !grad_log_beta) return fail(DPMM_EINVAL, "null argument");
+    LmlPlan& p = h->p;
+    const float* lb;
+    int rc = stage_beta(p, log_beta, &lb);
+    if (rc) return rc;
+    const bool dev_out = is_device_ptr(grad_log_beta);
+    CK(lml_backward(p, log_alpha, lb, dev_out ? grad_log_beta : p.grad, p.out + 1));
+    if (!dev_out)
+        CK(cudaMemcpyAsync(grad_log_beta, p.grad, sizeof(float) * p.D, cudaMemcpyDeviceToHost,
+                           p.stream));
+    if (grad_log_alpha) {
+        CK(cudaMemcpyAsync(grad_log_alpha, p.out + 1, sizeof(double), cudaMemcpyDefault, p.stream));
+        CK(cudaStreamSynchronize(p.stream));
+    } else if (!dev_out) {
+        CK(cudaStreamSynchronize(p.stream));
+    }
+    return DPMM_OK;
+}
+
+// ---- generator test hooks --------------------------------------------------
+
+__global__ void k_debug_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                               uint4* __restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+__global__ void k_debug_curand(unsigned long long seed, uint4* __restrict__ out, int64_t n) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    curandStatePhilox4_32_10_t s;
+    curand_init(seed, 0ull, 0ull, &s);
+    for (int64_t i = 0; i < n; ++i) out[i] = curand4(&s);
+}
+
+int dpmm_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n) {
+    if (n <= 0 || !ctr || !out) return fail(DPMM_EINVAL, "bad arguments");
+    uint4 *dc = nullptr, *dout = nullptr;
+    CK(dalloc(&dc, (size_t)n));
+    cudaError_t e = dalloc(&dout, (size_t)n);
+    if (!e) e = cudaMemcpy(dc, ctr, sizeof(uint4) * n, cudaMemcpyDefault);
+    if (!e) {
+        k_debug_philox<<<(unsigned)((n + 255) / 256), 256>>>(dc, (uint32_t)seed,
+                                                            (uint32_t)(seed >> 32), dout, n);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaDeviceSynchronize();
+    if (!e) e = cudaMemcpy(out, dout, sizeof(uint4) * n, cudaMemcpyDefault);
+    cudaFree(dc);
+    if (dout) cudaFree(dout);
+    CK(e);
+    return DPMM_OK;
+}
+
+int dpmm_debug_curand_philox(uint64_t seed, int64_t n, uint32_t* out) {
+    if (n <= 0 || n > (1 << 20) || !out) return fail(DPMM_EINVAL, "bad arguments");
+    uint4* dout = nullptr;
+    CK(dalloc(&dout, (size_t)n));
+    k_debug_curand<<<1, 1>>>((unsigned long long)seed, dout, n);
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaDeviceSynchronize();
+    if (!e) e = cudaMemcpy(out, dout, sizeof(uint4) * n, cudaMemcpyDefault);
+    cudaFree(dout);
+    CK(e);
+    return DPMM_OK;
+}
+
+}  // extern "C"

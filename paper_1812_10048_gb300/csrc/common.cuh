@@ -1,0 +1,275 @@
+// Shared declarations of the GB300 Para-DPMM library: the context layout,
+// the Philox stream map, device math helpers and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dpmm.h"
+
+namespace dpmm {
+
+// ---------------------------------------------------------------------------
+// Philox stream map (one specification shared with the oracle, written twice).
+// Counter (c0, c1, c2, c3) = (index, step, tag << 24 | chain, j); key = seed.
+// ---------------------------------------------------------------------------
+enum Tag : uint32_t {
+    TAG_LABEL = 0,     // eq. 4 label Gumbels: (cell, t, ., k / 4), word k % 4
+    TAG_SUBLABEL = 1,  // eq. 8 sub-label Gumbels: (cell, t, ., 0), words 0, 1
+    TAG_THETA = 2,     // eq. 4 / eq. 19 Gamma draws: (row * D + u, t, ., attempt)
+    TAG_PI = 3,        // eq. 4 weight Gamma draws: (k, t, ., attempt)
+    TAG_MOVE = 4,      // coin (0, m, ., 0) and split accept (k + 1, m, ., 0)
+    TAG_PAIR = 5,      // merge pairing keys (k, m, ., 0)
+    TAG_MERGE = 6,     // merge accept (a, m, ., 0)
+    TAG_SUBINIT = 7,   // fair-coin sub-labels (cell, step, ., kind)
+};
+enum SubInit : uint32_t { SUBINIT_INIT = 0, SUBINIT_RESET = 1, SUBINIT_SPLIT = 2 };
+
+constexpr int kMaxGammaAttempts = 64;
+constexpr int kMaxKmax = 1024;
+
+// ---------------------------------------------------------------------------
+// Cell state word: bits 0..30 label, bit 31 sub-label.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t pack_state(uint32_t label, uint32_t sub) {
+    return label | (sub << 31);
+}
+__host__ __device__ __forceinline__ uint32_t state_label(uint32_t s) { return s & 0x7FFFFFFFu; }
+__host__ __device__ __forceinline__ uint32_t state_sub(uint32_t s) { return s >> 31; }
+
+// Label-map entry of a move plan: bits 0..27 new label, bits 28..29 sub mode.
+enum SubMode : uint32_t { SUB_KEEP = 0, SUB_SET0 = 1, SUB_SET1 = 2, SUB_COIN = 3 };
+__host__ __device__ __forceinline__ uint32_t lmap_entry(uint32_t label, uint32_t mode) {
+    return label | (mode << 28);
+}
+
+// Stats-gather descriptor of a destination row (k, r): source cluster << 2 | mode.
+enum DescMode : int32_t { DESC_SUB0 = 0, DESC_SUB1 = 1, DESC_SUM = 2, DESC_ZERO = 3 };
+__host__ __device__ __forceinline__ int32_t desc_entry(int32_t src, int32_t mode) {
+    return (src << 2) | mode;
+}
+
+// Plan kinds.
+enum PlanKind : int32_t { PLAN_COMPACT = 0, PLAN_SPLIT = 1, PLAN_MERGE = 2 };
+
+// ---------------------------------------------------------------------------
+// Device-side scalars of one chain.
+// ---------------------------------------------------------------------------
+struct DevScalars {
+    int32_t K;            // current number of clusters
+    int32_t K_new;        // K after the pending plan
+    uint32_t t;           // sweep counter
+    uint32_t m;           // split/merge call counter
+    int32_t chain_sel;    // chain of the current split/merge call: 1 split, 2 merge
+    int32_t n_accepted;   // accepted moves of the last call
+    int32_t capacity_rejects;
+    int32_t any_reinit;   // a plan asked for fair-coin sub-labels + recount
+    int32_t any_relabel;  // a plan changes some label or sub-label
+    int32_t n_entries;    // split: K proposals; merge: number of pairs
+    int32_t error;        // sticky device error (DPMM_E*)
+    int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// The context (owned by the C ABI layer).
+// ---------------------------------------------------------------------------
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+
+    int64_t N = 0;
+    int32_t D = 0;
+    int64_t nnz = 0;
+    double alpha = 1.0, beta = 1.0;
+    dpmm_opts opts{};
+    int32_t kmax = 0;
+    bool packed = false;   // entries stored as (col << 16 | count)
+
+    // CSR (device)
+    int32_t* indptr = nullptr;
+    uint32_t* entries = nullptr;  // packed, or nullptr
+    int32_t* cols = nullptr;      // unpacked fallback
+    int32_t* counts = nullptr;
+
+    // chain state
+    uint32_t* state = nullptr;    // [N]
+    DevScalars* sc = nullptr;     // device scalars
+    DevScalars* sc_host = nullptr;  // pinned mirror for reads
+
+    // statistics: main (current state) and accumulators (being built)
+    uint32_t* nsub = nullptr;     // [kmax][2]
+    uint32_t* Ssub = nullptr;     // [kmax][2][D]
+    double* sumlogq = nullptr;    // [kmax]
+    uint32_t* acc_nsub = nullptr;
+    uint32_t* acc_Ssub = nullptr;
+    double* acc_sumlogq = nullptr;
+
+    // parameters
+    float* logpi = nullptr;       // [kmax + 1]
+    float* Lc = nullptr;          // [D][kmax] cluster log theta, gene-major
+    float* Ls = nullptr;          // [D][kmax][2] sub-cluster log theta, gene-major
+
+    // move plan
+    uint32_t* lmap = nullptr;     // [2 kmax] old (k, r) -> new label | sub mode
+    int32_t* desc = nullptr;      // [2 kmax] destination (k, r) <- source descriptor
+    uint32_t* plan_nsub = nullptr;   // [2 kmax]
+    double* plan_sumlogq = nullptr;  // [kmax]
+    uint8_t* reinit = nullptr;    // [kmax] new cluster needs fair-coin sub-labels
+    int32_t* decide = nullptr;    // [kmax] split decisions / merge pair decisions
+    double* log_h = nullptr;      // [kmax]
+    int32_t* pair_ab = nullptr;   // [2 kmax]
+
+    // launch configuration
+    int assign_blocks = 0;
+    int stats_blocks = 0;
+    size_t assign_smem = 0;
+    size_t stats_smem = 0;
+
+    // CUDA graph of dpmm_step
+    cudaGraphExec_t step_exec = nullptr;
+
+    // per-phase timing events (dpmm_profile)
+    bool profile = false;
+    bool graph_profiled = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+struct Stream {
+    uint32_t k0, k1, chain;
+    __device__ __forceinline__ uint4 words(uint32_t tag, uint32_t index, uint32_t step,
+                                           uint32_t j) const {
+        return philox4x32_10(make_uint4(index, step, (tag << 24) | chain, j), k0, k1);
+    }
+};
+
+__host__ __device__ __forceinline__ Stream make_stream(uint64_t seed, int32_t chain) {
+    return Stream{(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32),
+                  (uint32_t)chain & 0xFFFFFFu};
+}
+
+// u = ((w >> 9) + 0.5) 2^-23: in (0, 1) and exact in FP32.
+__device__ __forceinline__ float word_uniform(uint32_t w) {
+    return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-7f;
+}
+__device__ __forceinline__ float gumbel(uint32_t w) { return -logf(-logf(word_uniform(w))); }
+
+__device__ __forceinline__ uint32_t word_of(uint4 v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// log G, G ~ Gamma(a): Marsaglia & Tsang (2000) with the a < 1 boost, FP32.
+// Attempt j uses the words of counter (index, step, tag|chain, j): Box-Muller
+// normal from words 0, 1; accept uniform word 2; boost uniform word 3.
+__device__ __forceinline__ float log_gamma_draw(const Stream& st, uint32_t tag, float a,
+                                                uint32_t index, uint32_t step) {
+    const bool boost = a < 1.0f;
+    const float aa = boost ? a + 1.0f : a;
+    const float d = aa - (1.0f / 3.0f);
+    const float c = 1.0f / sqrtf(9.0f * d);
+    for (int j = 0; j < kMaxGammaAttempts; ++j) {
+        const uint4 w = st.words(tag, index, step, (uint32_t)j);
+        const float u0 = word_uniform(w.x), u1 = word_uniform(w.y);
+        const float z = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+        const float y = c * z;
+        if (y > -1.0f) {
+            const float e = y * (3.0f + y * (3.0f + y));
+            if (logf(word_uniform(w.z)) < 0.5f * z * z + d * (log1pf(e) - e)) {
+                float lg = logf(d) + 3.0f * log1pf(y);
+                if (boost) lg += logf(word_uniform(w.w)) / a;
+                return lg;
+            }
+        }
+    }
+    return logf(d);
+}
+
+// Digamma psi(x), x > 0: upward recurrence psi(x) = psi(x+1) - 1/x to x >= 6,
+// then the asymptotic series ln x - 1/(2x) - 1/(12x^2) + 1/(120x^4)
+// - 1/(252x^6) + 1/(240x^8) (Abramowitz & Stegun 6.3.5, 6.3.18).
+template <typename T>
+__device__ __forceinline__ T digamma(T x) {
+    T acc = 0;
+    while (x < T(6)) {
+        acc -= T(1) / x;
+        x += T(1);
+    }
+    const T r = T(1) / x, r2 = r * r;
+    const T series = r2 * (T(-1.0 / 12) + r2 * (T(1.0 / 120) + r2 * (T(-1.0 / 252) + r2 * T(1.0 / 240))));
+    return acc + log(x) - T(0.5) * r + series;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Row entry access for both CSR storage forms.
+struct Csr {
+    const int32_t* indptr;
+    const uint32_t* entries;  // packed (col << 16 | count) or nullptr
+    const int32_t* cols;
+    const int32_t* counts;
+    __device__ __forceinline__ void get(int64_t e, int32_t& u, int32_t& x) const {
+        if (entries) {
+            const uint32_t v = __ldg(entries + e);
+            u = (int32_t)(v >> 16);
+            x = (int32_t)(v & 0xFFFFu);
+        } else {
+            u = __ldg(cols + e);
+            x = __ldg(counts + e);
+        }
+    }
+};
+
+inline Csr csr_of(const Ctx& c) { return Csr{c.indptr, c.entries, c.cols, c.counts}; }
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (sweep.cu, moves.cu).
+// ---------------------------------------------------------------------------
+cudaError_t configure_launches(Ctx& c);
+cudaError_t launch_draw_params(Ctx& c);
+cudaError_t launch_assign(Ctx& c);
+cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub,
+                         uint32_t* bump);
+cudaError_t launch_plan(Ctx& c, int32_t kind);
+cudaError_t launch_apply_plan(Ctx& c, int32_t kind);
+cudaError_t launch_move_score(Ctx& c, int32_t mode);
+cudaError_t launch_init_state(Ctx& c);
+cudaError_t launch_debug_scores(Ctx& c, const int32_t* cells, int32_t n, float* out);
+
+}  // namespace dpmm

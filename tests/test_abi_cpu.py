@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dpmm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dpmm_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libdpmm():
+    from paper_1812_10048_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["dpmm_init", "dpmm_sweep", "dpmm_split_merge", "dpmm_labels",
+                     "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_free", "dpmm_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libdpmm):
+    missing = [n for n in declared_functions() if not hasattr(libdpmm, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1812_10048_gb300 import _lib
+    missing = [n for n in declared_functions() if n not in _lib.SIGNATURES]
+    assert not missing, missing
+
+
+def test_default_opts_without_gpu(libdpmm):
+    from paper_1812_10048_gb300 import dpmm_default_opts
+    o = dpmm_default_opts()
+    assert o.kmax == 256 and o.split_q == 1 and o.seed == 42 and o.engine == 0
+
+
+def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1812_10048_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.lib()

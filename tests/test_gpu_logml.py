@@ -1,0 +1,67 @@
+"""Collapsed log marginal likelihood: GPU forward (FP64) / backward (FP32) vs oracle."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1812_10048_gb300 import build
+    build.build()
+    import paper_1812_10048_gb300 as P
+    return P
+
+
+def problem(seed=0, N=3000, D=300, K=7):
+    from paper_1812_10048_gb300 import synth
+    ds = synth.make_dataset(N, D, K, gamma=0.1, lib_mu=np.log(800.0), lib_sigma=0.5, seed=seed)
+    rng = np.random.default_rng(seed)
+    log_beta = (np.log(0.1) + 0.1 * rng.standard_normal(D)).astype(np.float32)
+    return ds, log_beta
+
+
+def test_forward_and_backward_match_oracle(P):
+    import torch
+    from oracle.logml import cluster_stats, log_ml, log_ml_grad
+    ds, lb = problem()
+    K = int(ds.labels.max()) + 2          # one empty cluster index, ignored
+    h = P.LogML(ds.indptr, ds.indices, ds.data, ds.N, ds.D, ds.labels, K)
+    la = 0.3
+    n, S = cluster_stats(ds.indptr, ds.indices, ds.data, ds.N, ds.D, ds.labels, K)
+    ref = log_ml(n, S, la, lb.astype(np.float64))
+    got = h.forward(la, torch.from_numpy(lb).cuda())
+    assert abs(got - ref) <= 1e-10 * abs(ref)
+    ga_ref, gb_ref = log_ml_grad(n, S, la, lb.astype(np.float64))
+    gb = torch.empty(ds.D, dtype=torch.float32, device="cuda")
+    ga = h.backward(la, torch.from_numpy(lb).cuda(), gb)
+    torch.cuda.synchronize()
+    assert abs(ga - ga_ref) <= 1e-9 * max(1.0, abs(ga_ref))
+    np.testing.assert_allclose(gb.cpu().numpy(), gb_ref, rtol=2e-4, atol=1e-3)
+    # host pointers work too
+    gb_host = np.empty(ds.D, np.float32)
+    h.backward(la, lb, gb_host)
+    np.testing.assert_allclose(gb_host, gb.cpu().numpy(), rtol=0, atol=0)
+
+
+def test_autograd_function_matches_finite_differences(P):
+    import torch
+    ds, lb = problem(seed=1, N=1500, D=120, K=5)
+    model = P.LogML(ds.indptr, ds.indices, ds.data, ds.N, ds.D, ds.labels, 5)
+    la = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    lbt = torch.from_numpy(lb).cuda().requires_grad_(True)
+    out = model(la, lbt)
+    out.backward()
+    h = 1e-3
+    for u in [0, 7, 33, 119]:
+        e = np.zeros_like(lb)
+        e[u] = h
+        fp = model.forward(0.1, torch.from_numpy(lb + e).cuda())
+        fm = model.forward(0.1, torch.from_numpy(lb - e).cuda())
+        fd = (fp - fm) / (2 * h)
+        assert abs(lbt.grad[u].item() - fd) <= 2e-3 * max(1.0, abs(fd))
+    fa = (model.forward(0.1 + 1e-6, lbt.detach()) - model.forward(0.1 - 1e-6, lbt.detach())) / 2e-6
+    assert abs(la.grad.item() - fa) <= 1e-5 * max(1.0, abs(fa))

@@ -1,0 +1,336 @@
+"""GPU path vs FP64 oracle, through the C ABI (libdpmm.so).
+
+Tolerances (derived from the arithmetic):
+* generator words, labels given identical perturbed-score order, integer
+  statistics: bit-exact;
+* FP32 scores: |s_gpu - s_oracle| <= 1e-5 |s| + 1e-4 (eq. 4 / eq. 26 sums of
+  up to a few thousand FP32 products);
+* labels: identical except cells whose top-two perturbed scores differ by
+  less than that bound (near-ties);
+* log theta draws: rtol 1e-5, atol 1e-4, except rare Marsaglia-Tsang
+  accept/reject flips where FP32 and FP64 land on opposite sides of the
+  acceptance boundary (counted, at most 0.1% of the draws);
+* FP64 Hastings ratios: rtol 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SCORE_RTOL, SCORE_ATOL = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1812_10048_gb300 import build
+    build.build()
+    import paper_1812_10048_gb300 as P
+    torch.cuda.init()
+    return P
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    from paper_1812_10048_gb300 import synth
+    return synth.tiny()
+
+
+def make_pair(P, ds, alpha=1.0, beta=0.5, seed=42, kmax=64, **kw):
+    from oracle.sampler import Sampler as OracleSampler
+    g = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, alpha, beta, kmax=kmax, seed=seed, **kw)
+    o = OracleSampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, alpha, beta, seed=seed, kmax=kmax)
+    return g, o
+
+
+def oracle_warm_state(ds, n_steps=4, alpha=1.0, beta=0.5, seed=7):
+    from oracle.sampler import Sampler as OracleSampler
+    o = OracleSampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, alpha, beta, seed=seed)
+    for _ in range(n_steps):
+        o.sweep()
+        o.split_merge(0)
+    return o
+
+
+def test_device_philox_matches_oracle(P):
+    from oracle import philox
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    seed = 0x1234567890ABCDEF
+    got = P.dpmm_debug_philox(ctr, seed)
+    ref = philox.philox4x32_10(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3], seed & 0xFFFFFFFF, seed >> 32)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_curand_philox_reference_matches_oracle(P):
+    """cuRAND's Philox4_32_10: consecutive outputs of curand_init(seed, 0, 0)."""
+    from oracle import philox
+    seed = 987654321
+    got = P.dpmm_debug_curand_philox(seed, 8)
+    ref = philox.philox4x32_10(np.arange(8), 0, 0, 0, seed & 0xFFFFFFFF, seed >> 32)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_init_state_and_stats_match_oracle(P, tiny):
+    g, o = make_pair(P, tiny)
+    labels, sub, K, t, m = g.get_state()
+    assert K == 1 and t == 0 and m == 0
+    np.testing.assert_array_equal(labels, o.labels)
+    np.testing.assert_array_equal(sub, o.sub)
+    nsub, Ssub, sumlogq = g.stats()
+    on, oS = o.stats()
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    np.testing.assert_allclose(sumlogq, o.sumlogq, rtol=1e-12)
+
+
+def inject(P, g, o):
+    P.dpmm_set_state(g.ctx, o.labels, o.sub, o.K, o.t, o.m, o.sumlogq)
+
+
+def test_set_state_roundtrip_and_stats_exact(P, tiny):
+    o = oracle_warm_state(tiny)
+    g, _ = make_pair(P, tiny)
+    inject(P, g, o)
+    labels, sub, K, t, m = g.get_state()
+    np.testing.assert_array_equal(labels, o.labels)
+    np.testing.assert_array_equal(sub, o.sub)
+    assert (K, t, m) == (o.K, o.t, o.m)
+    nsub, Ssub, _ = g.stats()
+    on, oS = o.stats()
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+
+
+def test_draw_params_match_oracle(P, tiny):
+    from oracle.sampler import draw_pi, draw_theta
+    o = oracle_warm_state(tiny)
+    g, _ = make_pair(P, tiny, seed=7)
+    inject(P, g, o)
+    P.dpmm_draw_params(g.ctx)
+    logpi, logtheta = P.dpmm_get_params(g.ctx, o.K, tiny.D)
+    nsub, Ssub = o.stats()
+    ref_pi = draw_pi(nsub.sum(axis=1), o.alpha, o.seed, o.chain_id, o.t)
+    ref_th = draw_theta(Ssub, o.beta, o.seed, o.chain_id, o.t)
+    bad_pi = ~np.isclose(logpi, ref_pi, rtol=1e-5, atol=1e-4)
+    assert bad_pi.sum() == 0, (logpi, ref_pi)
+    bad = ~np.isclose(logtheta, ref_th, rtol=1e-5, atol=1e-4)
+    # a flip changes one Gamma variate, which shifts the whole row's normaliser slightly;
+    # count flips as elements far outside tolerance
+    flips = (np.abs(logtheta - ref_th) > 1e-2).sum()
+    assert flips <= max(2, 1e-3 * ref_th.size), flips
+    rows_with_flip = np.unique(np.nonzero(np.abs(logtheta - ref_th) > 1e-2)[0])
+    clean = np.setdiff1d(np.arange(ref_th.shape[0]), rows_with_flip)
+    assert bad[clean].sum() == 0
+
+
+def oracle_perturbed(o, logpi, logtheta):
+    """Oracle perturbed scores (FP64) for the injected parameters."""
+    from oracle.sampler import label_gumbels
+    from oracle.model import multinomial_scores
+    X = o.X.astype(np.float64)
+    s = multinomial_scores(X, logpi[:o.K], logtheta[0::3])
+    return s, s + label_gumbels(o.N, o.K, o.seed, o.chain_id, o.t)
+
+
+def test_assign_with_injected_params_matches_oracle(P, tiny):
+    o = oracle_warm_state(tiny)
+    g, _ = make_pair(P, tiny, seed=7)
+    inject(P, g, o)
+    P.dpmm_draw_params(g.ctx)
+    logpi32, logtheta32 = P.dpmm_get_params(g.ctx, o.K, tiny.D)
+    P.dpmm_set_params(g.ctx, logpi32, logtheta32)
+    logpi, logtheta = logpi32.astype(np.float64), logtheta32.astype(np.float64)
+    s, v = oracle_perturbed(o, logpi, logtheta)
+    srt = np.sort(v, axis=1)
+    gap = srt[:, -1] - srt[:, -2] if o.K > 1 else np.full(o.N, np.inf)
+    tol = SCORE_RTOL * np.abs(s).max(axis=1) + SCORE_ATOL
+    near = gap < tol
+    K0 = o.K
+    o.assign_and_update(logpi, logtheta)
+    P.dpmm_assign(g.ctx)
+    labels, sub, K, t, m = g.get_state()
+    assert t == o.t
+    if K == o.K:
+        mism = labels != o.labels
+        assert np.all(near[mism]), f"{mism.sum()} label mismatches, {near.sum()} near-ties"
+    else:
+        assert near.any()
+    # statistics are exact for the GPU's own labels
+    from oracle.sampler import sufficient_stats
+    nsub, Ssub, _ = g.stats()
+    on, oS = sufficient_stats(o.X, labels, sub, K)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    assert K0 >= 1
+
+
+def test_scores_match_oracle_fp64(P, tiny):
+    o = oracle_warm_state(tiny)
+    g, _ = make_pair(P, tiny, seed=7)
+    inject(P, g, o)
+    P.dpmm_draw_params(g.ctx)
+    logpi32, logtheta32 = P.dpmm_get_params(g.ctx, o.K, tiny.D)
+    cells = np.arange(0, tiny.N, 7)
+    got = P.dpmm_debug_scores(g.ctx, cells, o.K)
+    X = o.X[cells].astype(np.float64)
+    lt = logtheta32.astype(np.float64)
+    ref_c = np.asarray(X @ lt[0::3].T) + logpi32[:o.K].astype(np.float64)
+    ref_s = np.stack([np.asarray(X @ lt[1::3].T), np.asarray(X @ lt[2::3].T)], axis=2).reshape(len(cells), -1)
+    ref = np.concatenate([ref_c, ref_s], axis=1)
+    np.testing.assert_allclose(got, ref, rtol=SCORE_RTOL, atol=SCORE_ATOL)
+
+
+def test_one_full_sweep_agrees_with_oracle(P, tiny):
+    o = oracle_warm_state(tiny)
+    g, _ = make_pair(P, tiny, seed=7)
+    inject(P, g, o)
+    o.sweep()
+    g.sweep(1)
+    labels, sub, K, t, m = g.get_state()
+    assert t == o.t
+    agree = np.mean(labels == o.labels) if K == o.K else 0.0
+    assert agree > 0.99, (agree, K, o.K)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_split_merge_matches_oracle(P, tiny, mode):
+    o = oracle_warm_state(tiny, n_steps=3)
+    g, _ = make_pair(P, tiny, seed=7)
+    inject(P, g, o)
+    n_acc = g.split_merge(mode)
+    chain, log_h, pair_ab = P.dpmm_debug_moves(g.ctx, g.kmax)
+    assert chain == mode
+    if mode == 1:
+        ref = o.split_log_hastings()
+        assert np.array_equal(np.isnan(log_h), np.isnan(ref))
+        ok = ~np.isnan(ref)
+        np.testing.assert_allclose(log_h[ok], ref[ok], rtol=1e-10, atol=1e-8)
+    else:
+        pairs = o.merge_pairs()
+        np.testing.assert_array_equal(pair_ab, np.array(pairs, dtype=np.int32).reshape(-1, 2))
+        ref = o.merge_log_hastings(pairs)
+        np.testing.assert_allclose(log_h, ref, rtol=1e-10, atol=1e-8)
+    ref_acc = o.split_merge(mode)
+    assert n_acc == ref_acc
+    labels, sub, K, t, m = g.get_state()
+    assert (K, m) == (o.K, o.m)
+    np.testing.assert_array_equal(labels, o.labels)
+    np.testing.assert_array_equal(sub, o.sub)
+    nsub, Ssub, sumlogq = g.stats()
+    on, oS = o.stats()
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    np.testing.assert_allclose(sumlogq, o.sumlogq, rtol=1e-6, atol=1e-6)
+
+
+def test_forced_split_then_merge_and_capacity(P):
+    rng = np.random.default_rng(6)
+    n, D = 40, 3
+    x = rng.integers(1, 4, size=(n, D))
+    indptr = (np.arange(n + 1) * D).astype(np.int32)
+    indices = np.tile(np.arange(D), n).astype(np.int32)
+    g = P.Sampler(indptr, indices, x.ravel(), n, D, 1e300, 1.0, kmax=2, seed=1)
+    _, sub0, _, _, _ = g.get_state()
+    assert g.split_merge(1) == 1
+    labels, _, K, _, _ = g.get_state()
+    assert K == 2
+    np.testing.assert_array_equal(labels, sub0)
+    assert g.split_merge(1) == 0          # capacity: kmax = 2
+    g2 = P.Sampler(indptr, indices, x.ravel(), n, D, 1e-300, 1.0, kmax=4, seed=1)
+    P.dpmm_set_state(g2.ctx, sub0, np.zeros(n, np.uint8), 2)
+    assert g2.split_merge(2) == 1
+    labels, sub, K, _, _ = g2.get_state()
+    assert K == 1 and np.all(labels == 0)
+    np.testing.assert_array_equal(sub, sub0)
+
+
+def test_graph_step_equals_eager_calls(P, tiny):
+    g1, _ = make_pair(P, tiny, seed=11)
+    g2, _ = make_pair(P, tiny, seed=11)
+    for _ in range(5):
+        g1.sweep(1)
+        P.dpmm_split_merge(g1.ctx, 0, want_count=False)
+    g2.step(5)
+    a, b = g1.get_state(), g2.get_state()
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert a[2:] == b[2:]
+
+
+def test_chain_invariants_and_recovery(P, tiny):
+    from oracle.ari import adjusted_rand_index
+    from oracle.sampler import sufficient_stats, csr_matrix
+    g = P.Sampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, seed=3)
+    g.step(40)
+    labels, sub, K, t, m = g.get_state()
+    assert (t, m) == (40, 40)
+    assert labels.min() >= 0 and labels.max() < K
+    nsub, Ssub, _ = g.stats()
+    X = csr_matrix(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D)
+    on, oS = sufficient_stats(X, labels, sub, K)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    assert np.all(nsub.sum(axis=1) > 0)
+    assert adjusted_rand_index(labels, tiny.labels) > 0.95
+
+
+def test_resume_is_bit_identical(P, tiny):
+    g1, _ = make_pair(P, tiny, seed=5)
+    g1.step(6)
+    labels, sub, K, t, m = g1.get_state()
+    _, _, sq = g1.stats()
+    g2, _ = make_pair(P, tiny, seed=5)
+    P.dpmm_set_state(g2.ctx, labels, sub, K, t, m, sq)
+    g1.step(4)
+    g2.step(4)
+    a, b = g1.get_state(), g2.get_state()
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_edge_cases_empty_rows_wide_counts_single_cell(P):
+    from oracle.sampler import sufficient_stats, csr_matrix
+    rng = np.random.default_rng(9)
+    # empty rows and counts above 65535 (unpacked storage path)
+    N, D = 300, 17
+    dense = rng.integers(0, 5, size=(N, D)) * (rng.random((N, D)) < 0.3)
+    dense[::10] = 0
+    dense[3, 2] = 70000
+    r, c = np.nonzero(dense)
+    indptr = np.concatenate([[0], np.cumsum(np.count_nonzero(dense, axis=1))]).astype(np.int32)
+    g = P.Sampler(indptr, c.astype(np.int32), dense[r, c].astype(np.int32), N, D, 1.0, 0.3, seed=2)
+    g.step(10)
+    labels, sub, K, _, _ = g.get_state()
+    nsub, Ssub, _ = g.stats()
+    on, oS = sufficient_stats(csr_matrix(indptr, c, dense[r, c], N, D), labels, sub, K)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    # a single cell, a single gene
+    g1 = P.Sampler(np.array([0, 1], np.int32), np.array([0], np.int32), np.array([5], np.int32),
+                   1, 1, 1.0, 1.0, seed=1)
+    g1.step(3)
+    labels, _, K, _, _ = g1.get_state()
+    assert K == 1 and labels[0] == 0
+
+
+def test_invalid_inputs_raise(P):
+    ok_ptr = np.array([0, 1, 2], np.int32)
+    with pytest.raises(P.DpmmError, match="EINVAL"):
+        P.Sampler(ok_ptr, np.array([0, 5], np.int32), np.array([1, 1], np.int32), 2, 3, 1.0, 1.0)
+    with pytest.raises(P.DpmmError, match="EINVAL"):
+        P.Sampler(np.array([0, 2, 1], np.int32), np.array([0, 1], np.int32),
+                  np.array([1, 1], np.int32), 2, 3, 1.0, 1.0)
+    with pytest.raises(P.DpmmError, match="EINVAL"):
+        P.Sampler(ok_ptr, np.array([0, 1], np.int32), np.array([1, -1], np.int32), 2, 3, 1.0, 1.0)
+    with pytest.raises(P.DpmmError, match="EINVAL"):
+        P.Sampler(ok_ptr, np.array([0, 1], np.int32), np.array([1, 1], np.int32), 2, 3, 0.0, 1.0)
+    with pytest.raises(P.DpmmError, match="EINVAL"):
+        P.Sampler(ok_ptr, np.array([0, 1], np.int32), np.array([1, 1], np.int32), 2, 3, 1.0, 1.0,
+                  kmax=0)
+    with pytest.raises(P.DpmmError, match="EOVERFLOW"):
+        big = np.full(70000, 65535, np.int32)
+        P.Sampler(np.arange(70001, dtype=np.int32), np.zeros(70000, np.int32), big, 70000, 1, 1.0, 1.0)
