@@ -112,7 +112,9 @@ void free_ctx(Ctx& c) {
 
 #define MARK(i)                                                    \
     do {                                                           \
-        if (c.profile) CK(cudaEventRecord(c.ev[i], c.stream));     \
+        if (c.profile)                                             \
+            CK(cudaEventRecordWithFlags(c.ev[i], c.stream,         \
+                                        cudaEventRecordExternal)); \
     } while (0)
 
 int enqueue_sweep(Ctx& c) {

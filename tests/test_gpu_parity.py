@@ -334,3 +334,14 @@ def test_invalid_inputs_raise(P):
     with pytest.raises(P.DpmmError, match="EOVERFLOW"):
         big = np.full(70000, 65535, np.int32)
         P.Sampler(np.arange(70001, dtype=np.int32), np.zeros(70000, np.int32), big, 70000, 1, 1.0, 1.0)
+
+
+def test_phase_timing_events_in_graph(P, tiny):
+    g, _ = make_pair(P, tiny, seed=13)
+    P.dpmm_profile(g.ctx, True)
+    g.step(3)
+    ms = P.dpmm_phase_times(g.ctx, 5)
+    assert np.all(ms > 0) and np.all(ms < 1000)
+    g.sweep(1)                      # eager calls record the same events
+    ms2 = P.dpmm_phase_times(g.ctx, 4)
+    assert np.all(ms2 > 0)
