@@ -110,11 +110,22 @@ void free_ctx(Ctx& c) {
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
 }
 
-#define MARK(i)                                                    \
-    do {                                                           \
-        if (c.profile)                                             \
-            CK(cudaEventRecordWithFlags(c.ev[i], c.stream,         \
-                                        cudaEventRecordExternal)); \
+// Inside a stream capture the event becomes an event-record node of the graph
+// (external record); outside a capture it is an ordinary record.
+int mark(Ctx& c, int i) {
+    if (!c.profile) return DPMM_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(c.stream, &cs));
+    CK(cudaEventRecordWithFlags(c.ev[i], c.stream,
+                                cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                    : cudaEventRecordDefault));
+    return DPMM_OK;
+}
+
+#define MARK(i)                          \
+    do {                                 \
+        int _rc = mark(c, (i));          \
+        if (_rc) return _rc;             \
     } while (0)
 
 int enqueue_sweep(Ctx& c) {
