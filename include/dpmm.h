@@ -221,6 +221,33 @@ int dpmm_logml_forward(dpmm_logml* h, double log_alpha, const float* log_beta, d
 int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
                         double* grad_log_alpha, float* grad_log_beta);
 
+/*
+ * Allocation-free variant of dpmm_logml_create + dpmm_logml_forward +
+ * dpmm_logml_backward, for callers that cannot allocate device memory (for
+ * example a framework whose caching allocator owns the GPU's memory, or
+ * latency-critical code that must not call cudaMalloc / cudaFree, which
+ * synchronise the device).  The paper has no counterpart: it is a property of
+ * this library's interface, not of the method.
+ *   indptr, indices, data, labels: DEVICE pointers (CSR as in dpmm_init, labels
+ *     int32[N] in [0, K)); log_beta float[D], logml double, grad_log_alpha
+ *     double and grad_log_beta float[D] may be host or device pointers.
+ *   Limits: 1 <= D <= 65536, 1 <= K <= 1024, K * D <= 1048576; larger sizes
+ *     return DPMM_EINVAL without touching the GPU.
+ * Scratch lives in a static device array of about 4.6 MB that every GPU loading
+ * the library holds until exit; no cudaMalloc, cudaFree or other allocating
+ * routine is called.  All calls on a device share that array and it keeps the
+ * last call's contents (each call clears what must start at zero): calls whose
+ * GPU work overlaps race and must be serialised by the caller.  The first call
+ * on a device looks up the array's device address (once per device); make that
+ * first call before any stream capture.  Malformed CSR rows, columns or labels
+ * are skipped on the device and reported as DPMM_EINVAL.  Runs on `stream`
+ * (NULL: the legacy default stream) and synchronises it before returning.
+ */
+int dpmm_logml_grad_noalloc(const int32_t* indptr, const int32_t* indices, const int32_t* data,
+                            int64_t N, int32_t D, const int32_t* labels, int32_t K,
+                            double log_alpha, const float* log_beta, double* logml,
+                            double* grad_log_alpha, float* grad_log_beta, void* stream);
+
 /* ---- test hooks ---------------------------------------------------------- */
 
 /* Philox4x32-10 words of the device generator: ctr uint32[n][4] -> out

@@ -20,7 +20,8 @@ __all__ = [
     "dpmm_phase_times", "dpmm_get_state",
     "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
     "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_moves", "dpmm_logml_create",
-    "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_debug_philox",
+    "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_logml_grad_noalloc",
+    "dpmm_debug_philox",
     "dpmm_debug_curand_philox", "ENGINE_AUTO", "ENGINE_CSR_FP32", "ENGINE_TILE_BF16",
 ]
 
@@ -178,6 +179,19 @@ def dpmm_logml_backward(h, log_alpha, log_beta, grad_log_beta):
     check(lib().dpmm_logml_backward(h, float(log_alpha), ptr(log_beta), ctypes.byref(ga),
                                     ptr(grad_log_beta)))
     return ga.value
+
+
+def dpmm_logml_grad_noalloc(indptr, indices, data, N, D, labels, K, log_alpha, log_beta,
+                            grad_log_beta, stream=None):
+    """Allocation-free log ML + gradient; CSR and labels must be device tensors.
+
+    Returns (logml, grad_log_alpha) and fills ``grad_log_beta`` (float32[D])."""
+    lml, ga = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(lib().dpmm_logml_grad_noalloc(ptr(indptr), ptr(indices), ptr(data), int(N), int(D),
+                                        ptr(labels), int(K), float(log_alpha), ptr(log_beta),
+                                        ctypes.byref(lml), ctypes.byref(ga), ptr(grad_log_beta),
+                                        ctypes.c_void_p(stream) if stream else None))
+    return lml.value, ga.value
 
 
 def dpmm_debug_philox(ctr, seed):

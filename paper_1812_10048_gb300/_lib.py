@@ -64,6 +64,8 @@ SIGNATURES = {
     "dpmm_logml_free": (None, [_P]),
     "dpmm_logml_forward": (ctypes.c_int, [_P, _F64, _P, _P]),
     "dpmm_logml_backward": (ctypes.c_int, [_P, _F64, _P, _P, _P]),
+    "dpmm_logml_grad_noalloc": (ctypes.c_int, [_P, _P, _P, _I64, _I32, _P, _I32, _F64, _P, _P,
+                                               _P, _P, _P]),
     "dpmm_debug_philox": (ctypes.c_int, [_P, _U64, _P, _I64]),
     "dpmm_debug_curand_philox": (ctypes.c_int, [_U64, _I64, _P]),
 }

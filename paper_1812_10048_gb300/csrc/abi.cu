@@ -174,6 +174,11 @@ int recount_all(Ctx& c) {
 
 }  // namespace
 
+namespace dpmm {
+// Error reporting for entry points defined in other translation units.
+int noalloc_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace dpmm
+
 extern "C" {
 
 const char* dpmm_last_error(void) { return g_err.c_str(); }
