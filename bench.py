@@ -33,7 +33,7 @@ L2_FLUSH_BYTES = 256 << 20
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
-KERNELS_PER_STEP = 14     # 8 sweep kernels + 6 move kernels (see csrc/sweep.cu, moves.cu)
+KERNELS_PER_STEP = 16     # 8 sweep kernels + 8 move kernels (see csrc/sweep.cu, moves.cu)
 
 
 def parse():

@@ -103,7 +103,8 @@ void free_ctx(Ctx& c) {
         if (e) cudaEventDestroy(e);
     void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
-                    c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab};
+                    c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
+                    c.move_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.sc_host) cudaFreeHost(c.sc_host);
@@ -134,7 +135,7 @@ int enqueue_sweep(Ctx& c) {
     MARK(1);
     CK(launch_assign(c));
     MARK(2);
-    CK(launch_stats(c, nullptr, c.acc_nsub, c.acc_Ssub, nullptr));
+    CK(launch_sweep_stats(c));
     MARK(3);
     CK(launch_plan(c, PLAN_COMPACT));
     CK(launch_apply_plan(c, PLAN_COMPACT));
@@ -144,7 +145,7 @@ int enqueue_sweep(Ctx& c) {
 
 int enqueue_assign_half(Ctx& c) {
     CK(launch_assign(c));
-    CK(launch_stats(c, nullptr, c.acc_nsub, c.acc_Ssub, nullptr));
+    CK(launch_sweep_stats(c));
     CK(launch_plan(c, PLAN_COMPACT));
     CK(launch_apply_plan(c, PLAN_COMPACT));
     return DPMM_OK;
@@ -282,6 +283,8 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     CKI(dalloc(&c.decide, (size_t)c.kmax));
     CKI(dalloc(&c.log_h, (size_t)c.kmax));
     CKI(dalloc(&c.pair_ab, K2));
+    CKI(dalloc(&c.lg_table, lg_table_entries()));
+    CKI(dalloc(&c.move_part, move_partial_bytes()));
 
     CKI(cudaMemcpyAsync(c.indptr, hptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice,
                         c.stream));
@@ -308,6 +311,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     c.sc_host->K_new = 1;
     CKI(cudaMemcpyAsync(c.sc, c.sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c.stream));
     CKI(configure_launches(c));
+    CKI(launch_lg_table(c));
     CKI(launch_init_state(c));
     if (recount_all(c) != DPMM_OK) return bail(DPMM_ECUDA);
     const double s0 = (double)N * std::log(0.5);

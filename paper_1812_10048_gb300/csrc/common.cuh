@@ -69,7 +69,7 @@ struct DevScalars {
     int32_t any_relabel;  // a plan changes some label or sub-label
     int32_t n_entries;    // split: K proposals; merge: number of pairs
     int32_t error;        // sticky device error (DPMM_E*)
-    int32_t pad;
+    int32_t stats_fused;  // the label kernel of this sweep also added the statistics
 };
 
 // ---------------------------------------------------------------------------
@@ -123,6 +123,8 @@ struct Ctx {
     int32_t* decide = nullptr;    // [kmax] split decisions / merge pair decisions
     double* log_h = nullptr;      // [kmax]
     int32_t* pair_ab = nullptr;   // [2 kmax]
+    double* lg_table = nullptr;   // lgamma(beta + S) - lgamma(beta), S < 1024
+    unsigned char* move_part = nullptr;  // per-block partial sums of the move scores
 
     // launch configuration
     int assign_blocks = 0;
@@ -266,9 +268,13 @@ cudaError_t launch_draw_params(Ctx& c);
 cudaError_t launch_assign(Ctx& c);
 cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub,
                          uint32_t* bump);
+cudaError_t launch_sweep_stats(Ctx& c);
 cudaError_t launch_plan(Ctx& c, int32_t kind);
 cudaError_t launch_apply_plan(Ctx& c, int32_t kind);
 cudaError_t launch_move_score(Ctx& c, int32_t mode);
+cudaError_t launch_lg_table(Ctx& c);
+size_t move_partial_bytes();
+size_t lg_table_entries();
 cudaError_t launch_init_state(Ctx& c);
 cudaError_t launch_debug_scores(Ctx& c, const int32_t* cells, int32_t n, float* out);
 

@@ -1,8 +1,9 @@
 // Split/merge moves (Sections 2.3-2.4) and the move plans shared with the
 // sweep's empty-cluster removal.
 //
-//   k_move_score  picks the chain (fair coin on the tag-4 stream unless the
-//                 caller fixes it) and scores every proposal in FP64:
+//   k_move_prep / k_move_partial / k_move_final
+//                 pick the chain (fair coin on the tag-4 stream unless the
+//                 caller fixes it) and score every proposal in FP64:
 //                 split of cluster k into its sub-clusters (eq. 7, with the
 //                 likelihood ratio of eq. 9 / 14 / 16 taken with theta and
 //                 pi integrated out, and q(S*|S) from eq. 8), or merge of a
@@ -16,8 +17,29 @@
 
 namespace dpmm {
 
-constexpr int kScoreThreads = 256;
 constexpr int kPlanThreads = kMaxKmax;
+
+constexpr int kLgTable = 1024;      // lgamma(beta + S) - lgamma(beta) tabulated for S < this
+constexpr int kPartialThreads = 64;
+constexpr int kMaxPartials = 1216;  // = 8 x 152 blocks of the partial-sum kernel
+
+// lgamma(beta + S) - lgamma(beta), FP64.  Small S from the per-chain table;
+// large S by Stirling's series for lgamma(x), x >= 1024 (Abramowitz & Stegun
+// 6.1.41, truncated after the x^-3 term: the next term is below 1e-18).
+__device__ __forceinline__ double lg_shift(uint32_t S, double beta, double lg_beta,
+                                           const double* __restrict__ tab) {
+    if (S < (uint32_t)kLgTable) return tab[S];
+    const double x = beta + (double)S;
+    const double r = 1.0 / x;
+    const double r2 = r * r;
+    const double half_log_2pi = 0.91893853320467274178;
+    return (x - 0.5) * log(x) - x + half_log_2pi + r * (1.0 / 12.0 - r2 * (1.0 / 360.0)) - lg_beta;
+}
+
+__global__ void k_lg_table(double* __restrict__ tab, double beta) {
+    const int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S < kLgTable) tab[S] = S ? lgamma(beta + (double)S) - lgamma(beta) : 0.0;
+}
 
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
     v = warp_sum(v);
@@ -42,112 +64,144 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return r;
 }
 
-// lgamma(beta + S) - lgamma(beta); zero statistics contribute nothing.
-__device__ __forceinline__ double lg_shift(uint32_t S, double beta, double lg_beta) {
-    return S ? lgamma(beta + (double)S) - lg_beta : 0.0;
-}
-
-__global__ void __launch_bounds__(kScoreThreads)
-k_move_score(DevScalars* sc, const uint32_t* __restrict__ nsub, const uint32_t* __restrict__ Ssub,
-             const double* __restrict__ sumlogq, int32_t* __restrict__ decide,
-             double* __restrict__ log_h, int32_t* __restrict__ pair_ab, int32_t D, double alpha,
-             double beta, int32_t split_q, int32_t mode, Stream st) {
-    __shared__ double redd[32];
-    __shared__ unsigned long long redu[32];
+// Chain choice (fair coin on the tag-4 stream unless `mode` fixes it) and, for
+// the merge chain, the random disjoint pairs from sorted tag-5 keys.
+__global__ void __launch_bounds__(kMaxKmax)
+k_move_prep(DevScalars* sc, int32_t* __restrict__ pair_ab, int32_t mode, Stream st) {
     __shared__ uint32_t keys[kMaxKmax];
-    __shared__ int32_t order[kMaxKmax];
     const int K = sc->K;
     const uint32_t m = sc->m;
     int chain = mode;
     if (mode == 0) chain = word_uniform(st.words(TAG_MOVE, 0u, m, 0u).x) < 0.5f ? 1 : 2;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         sc->chain_sel = chain;
         sc->n_entries = chain == 1 ? K : K / 2;
     }
-    const double lgb = lgamma(beta);
-    const double Db = (double)D * beta;
-    const double lgDb = lgamma(Db);
-    if (chain == 1) {
-        for (int k = blockIdx.x; k < K; k += gridDim.x) {
-            const uint32_t n0 = nsub[2 * k], n1 = nsub[2 * k + 1];
-            if (n0 < 1 || n1 < 1) {
-                if (threadIdx.x == 0) {
-                    decide[k] = 0;
-                    log_h[k] = CUDART_NAN;
-                }
-                continue;
-            }
-            const uint32_t* S0 = Ssub + (size_t)(2 * k) * D;
-            const uint32_t* S1 = S0 + D;
-            double acc = 0.0;
-            unsigned long long T0 = 0, T1 = 0;
-            for (int u = threadIdx.x; u < D; u += blockDim.x) {
-                const uint32_t a = S0[u], b = S1[u];
-                T0 += a;
-                T1 += b;
-                acc += lg_shift(a, beta, lgb) + lg_shift(b, beta, lgb) - lg_shift(a + b, beta, lgb);
-            }
-            acc = block_sum_d(acc, redd);
-            T0 = block_sum_u64(T0, redu);
-            T1 = block_sum_u64(T1, redu);
-            if (threadIdx.x == 0) {
-                const double lf0 = lgDb - lgamma(Db + (double)T0);
-                const double lf1 = lgDb - lgamma(Db + (double)T1);
-                const double lfk = lgDb - lgamma(Db + (double)(T0 + T1));
-                double lh = log(alpha) + lgamma((double)n0) + lgamma((double)n1) -
-                            lgamma((double)(n0 + n1)) + lf0 + lf1 - lfk + acc;
-                if (split_q) lh -= sumlogq[k];
-                const double u = (double)word_uniform(st.words(TAG_MOVE, (uint32_t)k + 1u, m, 0u).x);
-                decide[k] = log(u) < lh ? 1 : 0;
-                log_h[k] = lh;
-            }
-        }
-        return;
-    }
-    // merge chain: random disjoint pairs from sorted tag-5 keys (ties by index)
-    const int P = K / 2;
-    if ((int)blockIdx.x >= P) return;
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-        keys[k] = st.words(TAG_PAIR, (uint32_t)k, m, 0u).x;
+    if (chain != 2) return;
+    const int k = threadIdx.x;
+    if (k < K) keys[k] = st.words(TAG_PAIR, (uint32_t)k, m, 0u).x;
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    if (k < K) {
         int rank = 0;
         const uint32_t kk = keys[k];
         for (int j = 0; j < K; ++j) rank += (keys[j] < kk) || (keys[j] == kk && j < k);
-        order[rank] = k;
+        // rank r joins pair r / 2; the smaller index is a
+        if (rank < 2 * (K / 2)) pair_ab[2 * (rank >> 1) + (rank & 1)] = k;
     }
     __syncthreads();
-    for (int p = blockIdx.x; p < P; p += gridDim.x) {
-        const int x = order[2 * p], y = order[2 * p + 1];
-        const int a = min(x, y), b = max(x, y);
-        const uint32_t na = nsub[2 * a] + nsub[2 * a + 1];
-        const uint32_t nb = nsub[2 * b] + nsub[2 * b + 1];
+    if (k < K / 2) {
+        const int x = pair_ab[2 * k], y = pair_ab[2 * k + 1];
+        pair_ab[2 * k] = min(x, y);
+        pair_ab[2 * k + 1] = max(x, y);
+    }
+}
+
+struct MovePartial {
+    double acc;
+    unsigned long long Ta, Tb;
+};
+
+// Per (proposal, gene chunk): sum over the chunk of the lgamma terms of the
+// Hastings ratio and the two gene totals.  Block b serves proposal b / G,
+// chunk b % G, with G chosen so that proposals x G fills the grid.
+__global__ void __launch_bounds__(kPartialThreads)
+k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ Ssub,
+               const int32_t* __restrict__ pair_ab, const double* __restrict__ tab,
+               MovePartial* __restrict__ part, int32_t D, double beta) {
+    __shared__ double redd[2];
+    __shared__ unsigned long long redu[2];
+    const int E = sc->n_entries;
+    if (E <= 0) return;
+    const bool split = sc->chain_sel == 1;
+    const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
+    const int G = max(1, min((int)gridDim.x / E, maxG));
+    const int e = blockIdx.x / G, g = blockIdx.x - e * G;
+    if (e >= E) return;
+    const int Dc = (D + G - 1) / G;
+    const int u0 = g * Dc, u1 = min(D, u0 + Dc);
+    const double lgb = lgamma(beta);
+    double acc = 0.0;
+    unsigned long long Ta = 0, Tb = 0;
+    if (split) {
+        const uint32_t* S0 = Ssub + (size_t)(2 * e) * D;
+        const uint32_t* S1 = S0 + D;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+            const uint32_t a = S0[u], b = S1[u];
+            Ta += a;
+            Tb += b;
+            if (a && b)
+                acc += lg_shift(a, beta, lgb, tab) + lg_shift(b, beta, lgb, tab) -
+                       lg_shift(a + b, beta, lgb, tab);
+        }
+    } else {
+        const int a = pair_ab[2 * e], b = pair_ab[2 * e + 1];
         const uint32_t* A0 = Ssub + (size_t)(2 * a) * D;
         const uint32_t* B0 = Ssub + (size_t)(2 * b) * D;
-        double acc = 0.0;
-        unsigned long long Ta = 0, Tb = 0;
-        for (int u = threadIdx.x; u < D; u += blockDim.x) {
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
             const uint32_t sa = A0[u] + A0[D + u], sb = B0[u] + B0[D + u];
             Ta += sa;
             Tb += sb;
-            acc += lg_shift(sa + sb, beta, lgb) - lg_shift(sa, beta, lgb) - lg_shift(sb, beta, lgb);
+            if (sa && sb)
+                acc += lg_shift(sa + sb, beta, lgb, tab) - lg_shift(sa, beta, lgb, tab) -
+                       lg_shift(sb, beta, lgb, tab);
         }
-        acc = block_sum_d(acc, redd);
-        Ta = block_sum_u64(Ta, redu);
-        Tb = block_sum_u64(Tb, redu);
-        if (threadIdx.x == 0) {
-            const double lfab = lgDb - lgamma(Db + (double)(Ta + Tb));
-            const double lfa = lgDb - lgamma(Db + (double)Ta);
-            const double lfb = lgDb - lgamma(Db + (double)Tb);
-            const double lh = -log(alpha) + lgamma((double)(na + nb)) - lgamma((double)na) -
-                              lgamma((double)nb) + lfab - lfa - lfb + acc +
-                              (double)(na + nb - 2) * log(0.5);
-            const double u = (double)word_uniform(st.words(TAG_MERGE, (uint32_t)a, m, 0u).x);
-            decide[p] = log(u) < lh ? 1 : 0;
-            log_h[p] = lh;
-            pair_ab[2 * p] = a;
-            pair_ab[2 * p + 1] = b;
+    }
+    acc = block_sum_d(acc, redd);
+    Ta = block_sum_u64(Ta, redu);
+    Tb = block_sum_u64(Tb, redu);
+    if (threadIdx.x == 0) part[blockIdx.x] = MovePartial{acc, Ta, Tb};
+}
+
+// Sum the chunks of every proposal, add the count and total terms, decide.
+__global__ void __launch_bounds__(kMaxKmax)
+k_move_final(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
+             const double* __restrict__ sumlogq, const int32_t* __restrict__ pair_ab,
+             const MovePartial* __restrict__ part, int32_t* __restrict__ decide,
+             double* __restrict__ log_h, int32_t D, double alpha, double beta, int32_t split_q,
+             int32_t grid_partial, Stream st) {
+    const int E = sc->n_entries;
+    const int e = threadIdx.x;
+    if (e >= E) return;
+    const uint32_t m = sc->m;
+    const bool split = sc->chain_sel == 1;
+    const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
+    const int G = max(1, min(grid_partial / E, maxG));
+    double acc = 0.0;
+    unsigned long long Ta = 0, Tb = 0;
+    for (int g = 0; g < G; ++g) {
+        const MovePartial p = part[e * G + g];
+        acc += p.acc;
+        Ta += p.Ta;
+        Tb += p.Tb;
+    }
+    const double Db = (double)D * beta;
+    const double lgDb = lgamma(Db);
+    const double lfa = lgDb - lgamma(Db + (double)Ta);
+    const double lfb = lgDb - lgamma(Db + (double)Tb);
+    const double lfab = lgDb - lgamma(Db + (double)(Ta + Tb));
+    if (split) {
+        const uint32_t n0 = nsub[2 * e], n1 = nsub[2 * e + 1];
+        if (n0 < 1 || n1 < 1) {
+            decide[e] = 0;
+            log_h[e] = CUDART_NAN;
+            return;
         }
+        double lh = log(alpha) + lgamma((double)n0) + lgamma((double)n1) -
+                    lgamma((double)(n0 + n1)) + lfa + lfb - lfab + acc;
+        if (split_q) lh -= sumlogq[e];
+        const double u = (double)word_uniform(st.words(TAG_MOVE, (uint32_t)e + 1u, m, 0u).x);
+        decide[e] = log(u) < lh ? 1 : 0;
+        log_h[e] = lh;
+    } else {
+        const int a = pair_ab[2 * e], b = pair_ab[2 * e + 1];
+        const uint32_t na = nsub[2 * a] + nsub[2 * a + 1];
+        const uint32_t nb = nsub[2 * b] + nsub[2 * b + 1];
+        const double lh = -log(alpha) + lgamma((double)(na + nb)) - lgamma((double)na) -
+                          lgamma((double)nb) + lfab - lfa - lfb + acc +
+                          (double)(na + nb - 2) * log(0.5);
+        const double u = (double)word_uniform(st.words(TAG_MERGE, (uint32_t)a, m, 0u).x);
+        decide[e] = log(u) < lh ? 1 : 0;
+        log_h[e] = lh;
     }
 }
 
@@ -337,13 +391,26 @@ k_plan(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub, double* __rest
     }
 }
 
-cudaError_t launch_move_score(Ctx& c, int32_t mode) {
-    const int grid = c.kmax < 2 * c.num_sms ? c.kmax : 2 * c.num_sms;
-    k_move_score<<<grid, kScoreThreads, 0, c.stream>>>(
-        c.sc, c.nsub, c.Ssub, c.sumlogq, c.decide, c.log_h, c.pair_ab, c.D, c.alpha, c.beta,
-        c.opts.split_q, mode, make_stream(c.opts.seed, c.opts.chain_id));
+cudaError_t launch_lg_table(Ctx& c) {
+    k_lg_table<<<(kLgTable + 255) / 256, 256, 0, c.stream>>>(c.lg_table, c.beta);
     return cudaGetLastError();
 }
+
+cudaError_t launch_move_score(Ctx& c, int32_t mode) {
+    const Stream st = make_stream(c.opts.seed, c.opts.chain_id);
+    const int grid = kMaxPartials;
+    k_move_prep<<<1, kMaxKmax, 0, c.stream>>>(c.sc, c.pair_ab, mode, st);
+    k_move_partial<<<grid, kPartialThreads, 0, c.stream>>>(
+        c.sc, c.Ssub, c.pair_ab, c.lg_table, reinterpret_cast<MovePartial*>(c.move_part), c.D,
+        c.beta);
+    k_move_final<<<1, kMaxKmax, 0, c.stream>>>(
+        c.sc, c.nsub, c.sumlogq, c.pair_ab, reinterpret_cast<const MovePartial*>(c.move_part),
+        c.decide, c.log_h, c.D, c.alpha, c.beta, c.opts.split_q, grid, st);
+    return cudaGetLastError();
+}
+
+size_t move_partial_bytes() { return sizeof(MovePartial) * kMaxPartials; }
+size_t lg_table_entries() { return kLgTable; }
 
 cudaError_t launch_plan(Ctx& c, int32_t kind) {
     k_plan<<<1, kPlanThreads, 0, c.stream>>>(c.sc, kind, c.nsub, c.sumlogq, c.acc_nsub,

@@ -18,7 +18,6 @@
 namespace dpmm {
 
 constexpr int kAssignThreads = 1024;
-constexpr int kAssignWarps = kAssignThreads / 32;
 constexpr int kStatsThreads = 1024;
 constexpr int kDrawThreads = 256;
 
@@ -153,72 +152,334 @@ __device__ __forceinline__ float2 sub_scores(const Csr& csr, int64_t beg, int64_
 
 struct AssignArgs {
     Csr csr;
-    const DevScalars* sc;
+    DevScalars* sc;
     uint32_t* state;
     const uint32_t* nsub;     // sweep-start n-bar
     const float* logpi;
     const float* Lc;
     const float2* Ls2;
     double* acc_sumlogq;
+    uint32_t* acc_nsub;       // statistics accumulators (fused path)
+    uint32_t* acc_Ssub;
     int64_t N;
     int32_t D, kmax;
-    int32_t table_cap;        // max K*D floats of the shared-memory table
+    int64_t smem_bytes;       // dynamic shared memory of the launch
     Stream st;
 };
 
-template <int Q>
+// eq. 8 draw for cell `cell` of cluster c given its two likelihood factors;
+// returns the sub-label and writes log q_i.
+__device__ __forceinline__ uint32_t draw_sublabel(const AssignArgs& a, int64_t cell, int c,
+                                                  float2 lik, uint32_t t, float* logq) {
+    const uint32_t old = a.state[cell];
+    const bool stays = state_label(old) == (uint32_t)c;
+    const uint32_t so = state_sub(old);
+    float w0 = (float)a.nsub[2 * c] - (float)(stays && so == 0);
+    float w1 = (float)a.nsub[2 * c + 1] - (float)(stays && so == 1);
+    if (w0 + w1 == 0.0f) w0 = w1 = 1.0f;
+    const float l0 = w0 > 0.0f ? logf(w0) + lik.x : -CUDART_INF_F;
+    const float l1 = w1 > 0.0f ? logf(w1) + lik.y : -CUDART_INF_F;
+    const uint4 h = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+    const uint32_t s = (l1 + gumbel(h.y) > l0 + gumbel(h.x)) ? 1u : 0u;
+    const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
+    *logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
+    return s;
+}
+
+// Warp argmax of (value, index): largest value, lowest index on ties.
+__device__ __forceinline__ int warp_argmax(float best, int bestk) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        const int ok = __shfl_xor_sync(0xFFFFFFFFu, bestk, o);
+        if (ov > best || (ov == best && ok < bestk)) {
+            best = ov;
+            bestk = ok;
+        }
+    }
+    return bestk;
+}
+
+// K > 32: lanes own clusters lane, lane + 32, ...; the row is contracted once
+// per chunk of 32 clusters and the running Gumbel-max kept across chunks.
 __device__ __forceinline__ void assign_cells(const AssignArgs& a, const float* L, int ldL, int K,
                                              uint32_t t, double* blk_sumlogq) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (int64_t)blockIdx.x * kAssignWarps + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * kAssignWarps;
+    const int64_t warp0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t cell = warp0; cell < a.N; cell += nwarps) {
         const int64_t beg = a.csr.indptr[cell], end = a.csr.indptr[cell + 1];
-        float acc[Q];
-        cluster_scores<Q>(a.csr, beg, end, L, ldL, K, lane, acc);
         // eq. 4 third line: Gumbel-max over log pi_k + score (ties -> lowest k)
         float best = -CUDART_INF_F;
         int bestk = 0x7FFFFFFF;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int k = lane + 32 * q;
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            float acc[1];
+            cluster_scores<1>(a.csr, beg, end, L + k0, ldL, K - k0, lane, acc);
+            const int k = k0 + lane;
             if (k < K) {
                 const uint4 w = a.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
-                const float v = (__ldg(a.logpi + k) + acc[q]) + gumbel(word_of(w, k & 3));
+                const float v = (__ldg(a.logpi + k) + acc[0]) + gumbel(word_of(w, k & 3));
                 if (v > best) {
                     best = v;
                     bestk = k;
                 }
             }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-            const int ok = __shfl_xor_sync(0xFFFFFFFFu, bestk, o);
-            if (ov > best || (ov == best && ok < bestk)) {
-                best = ov;
-                bestk = ok;
-            }
-        }
-        const int c = bestk;
+        const int c = warp_argmax(best, bestk);
         // eq. 8 with the sweep-start counts minus this cell's own old membership
         const float2 lik = sub_scores(a.csr, beg, end, a.Ls2, a.kmax, c, lane);
         if (lane == 0) {
-            const uint32_t old = a.state[cell];
-            const bool stays = state_label(old) == (uint32_t)c;
-            const uint32_t so = state_sub(old);
-            float w0 = (float)a.nsub[2 * c] - (float)(stays && so == 0);
-            float w1 = (float)a.nsub[2 * c + 1] - (float)(stays && so == 1);
-            if (w0 + w1 == 0.0f) w0 = w1 = 1.0f;
-            const float l0 = w0 > 0.0f ? logf(w0) + lik.x : -CUDART_INF_F;
-            const float l1 = w1 > 0.0f ? logf(w1) + lik.y : -CUDART_INF_F;
-            const uint4 h = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
-            const uint32_t s = (l1 + gumbel(h.y) > l0 + gumbel(h.x)) ? 1u : 0u;
-            const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
-            const float lse = mx + log1pf(expf(mn - mx));
-            const float logq = (s ? l1 : l0) - lse;
+            float logq;
+            const uint32_t s = draw_sublabel(a, cell, c, lik, t, &logq);
             a.state[cell] = pack_state((uint32_t)c, s);
             atomicAdd(&blk_sumlogq[c], (double)logq);
+        }
+    }
+}
+
+// Reduce-scatter over the warp: P partial sums per lane in, one total per
+// lane out (lane l gets column *col; 32 / P lanes share each column).
+template <int P>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[P], int lane, int* col) {
+    int base = 0;
+    int o = 16;
+#pragma unroll
+    for (int m = P; m > 1; m >>= 1) {
+        const int h = m >> 1;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+            const float send = up ? v[j] : v[j + h];
+            const float keep = up ? v[j + h] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
+        }
+        if (up) base += h;
+        o >>= 1;
+    }
+    float r = v[0];
+    for (; o; o >>= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
+    *col = base;
+    return r;
+}
+
+// Per-lane partial sums of the contraction for P >= K columns: lane takes the
+// row's entries lane, lane + 32, ...; table row u holds the K log theta values
+// (row stride ld, a multiple of 4 when VEC loads float4 from shared memory).
+template <int P, bool VEC>
+__device__ __forceinline__ void lane_partials(const Csr& csr, int64_t beg, int64_t end,
+                                              const float* __restrict__ L, int ld, int K,
+                                              int lane, float (&acc)[P]) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) acc[j] = 0.0f;
+    for (int64_t e = beg + lane; e < end; e += 32) {
+        int32_t u, x;
+        csr.get(e, u, x);
+        const float xf = (float)x;
+        const float* row = L + (size_t)u * ld;
+        if (VEC) {
+#pragma unroll
+            for (int q = 0; q < P / 4; ++q) {
+                if (4 * q < K) {
+                    const float4 l = reinterpret_cast<const float4*>(row)[q];
+                    acc[4 * q] = fmaf(xf, l.x, acc[4 * q]);
+                    acc[4 * q + 1] = fmaf(xf, l.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(xf, l.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(xf, l.w, acc[4 * q + 3]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                if (j < K) acc[j] = fmaf(xf, row[j], acc[j]);
+        }
+    }
+}
+
+// Sub-cluster likelihood factors of cluster c from a table of float2 rows.
+__device__ __forceinline__ float2 sub_pair(const Csr& csr, int64_t beg, int64_t end,
+                                           const float2* __restrict__ Ls2, int ld, int c,
+                                           int lane) {
+    float t0 = 0.0f, t1 = 0.0f;
+    for (int64_t e = beg + lane; e < end; e += 32) {
+        int32_t u, x;
+        csr.get(e, u, x);
+        const float2 l = Ls2[(size_t)u * ld + c];
+        t0 = fmaf((float)x, l.x, t0);
+        t1 = fmaf((float)x, l.y, t1);
+    }
+    return make_float2(warp_sum(t0), warp_sum(t1));
+}
+
+// Column of the reduce-scatter result held by `lane` (see warp_reduce_scatter).
+template <int P>
+__device__ __forceinline__ int lane_column(int lane) {
+    int base = 0, o = 16;
+#pragma unroll
+    for (int m = P; m > 1; m >>= 1) {
+        if (lane & o) base += m >> 1;
+        o >>= 1;
+    }
+    return base;
+}
+
+// Smallest lane holding column `col` (inverse of lane_column).
+template <int P>
+__device__ __forceinline__ int lane_of_column(int col) {
+    int lane = 0, o = 16;
+#pragma unroll
+    for (int m = P; m > 1; m >>= 1) {
+        const int h = m >> 1;
+        if (col >= h) {
+            lane |= o;
+            col -= h;
+        }
+        o >>= 1;
+    }
+    return lane;
+}
+
+constexpr int kRowRegs = 8;   // row entries a lane keeps in registers (rows up to 256)
+
+// K <= 32: tables (and, when they fit, the statistics) in shared memory.
+// Per cell (one warp): the Philox words and the old state are fetched first;
+// the row's entries are read once into registers (rows longer than 256
+// entries re-read their tail); pass 1 forms per-lane partial sums against the
+// cluster table and a reduce-scatter gives every lane one cluster total;
+// Gumbel-max picks c; pass 2 gathers the two sub-cluster factors of c; lane 0
+// draws the eq. 8 sub-label; pass 3 adds the row into the block's statistics.
+template <int P>
+__device__ __forceinline__ void assign_cells_v2(const AssignArgs& a, const float* sLc, int Kp,
+                                                const float2* Ls2, int ldS, int K, uint32_t t,
+                                                const float* spi, const float* slw,
+                                                double* wsq, uint32_t* wn, uint32_t* sS) {
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int64_t warp0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int col = lane_column<P>(lane);
+    // lanes whose column is unused draw the eq. 8 Gumbels: the lane of
+    // column K takes word 0, that of column K + 1 word 1 (when P >= K + 2)
+    const bool spare = P >= K + 2;
+    const int sub_word = col - K;                       // 0 or 1 on those lanes
+    const bool packed = a.csr.entries != nullptr;
+    constexpr int R = P <= 16 ? kRowRegs : kRowRegs / 2;   // register budget at 1024 threads
+    double* my_sq = wsq + (size_t)wid * K;
+    uint32_t* my_n = wn + (size_t)wid * 2 * K;
+    for (int64_t cell = warp0; cell < a.N; cell += nwarps) {
+        const int64_t beg = a.csr.indptr[cell], end = a.csr.indptr[cell + 1];
+        const uint32_t old = lane == 0 ? a.state[cell] : 0u;
+        // one Philox call and one Gumbel per lane: label noise of the lane's
+        // column, or (spare lanes) the sub-label noise
+        // counters chosen per lane so that the whole warp runs one Philox call
+        const bool lab = col < K;
+        const uint4 w = a.st.words(lab ? TAG_LABEL : TAG_SUBLABEL, (uint32_t)cell, t,
+                                   lab ? (uint32_t)(col >> 2) : 0u);
+        const float g = gumbel(word_of(w, lab ? (col & 3) : (sub_word & 1)));
+        float h0, h1;
+        if (spare) {
+            h0 = __shfl_sync(0xFFFFFFFFu, g, lane_of_column<P>(K));
+            h1 = __shfl_sync(0xFFFFFFFFu, g, lane_of_column<P>(K + 1));
+        } else {
+            const uint4 ws = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+            h0 = gumbel(ws.x);
+            h1 = gumbel(ws.y);
+        }
+        const int len = (int)(end - beg);
+        const int slots = min(R, (len + 31) >> 5);
+        const uint32_t* row_ent = a.csr.entries + beg;
+        // pass 1: entries -> registers, partial sums against the cluster table
+        uint32_t ent[R];
+        float acc[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) acc[j] = 0.0f;
+        auto add_row = [&](int32_t u, int32_t x) {
+            const float xf = (float)x;
+            const float4* row = reinterpret_cast<const float4*>(sLc + u * Kp);
+#pragma unroll
+            for (int q = 0; q < P / 4; ++q) {
+                if (4 * q < Kp) {
+                    const float4 l = row[q];
+                    acc[4 * q] = fmaf(xf, l.x, acc[4 * q]);
+                    acc[4 * q + 1] = fmaf(xf, l.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(xf, l.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(xf, l.w, acc[4 * q + 3]);
+                }
+            }
+        };
+        if (packed) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ent[r] = 0u;
+                if (r < slots && lane + 32 * r < len) ent[r] = __ldg(row_ent + lane + 32 * r);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (r < slots && lane + 32 * r < len)
+                    add_row((int32_t)(ent[r] >> 16), (int32_t)(ent[r] & 0xFFFFu));
+        }
+        for (int64_t e = beg + lane + (packed ? 32 * R : 0); e < end; e += 32) {
+            int32_t u, x;
+            a.csr.get(e, u, x);
+            add_row(u, x);
+        }
+        int colr;
+        const float sc = warp_reduce_scatter<P>(acc, lane, &colr);
+        const float v = col < K ? (spi[col] + sc) + g : -CUDART_INF_F;
+        const int c = warp_argmax(v, col < K ? col : 0x7FFFFFFF);
+        // pass 2: eq. 8 likelihood factors of cluster c
+        float t0 = 0.0f, t1 = 0.0f;
+        if (packed) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < slots && lane + 32 * r < len) {
+                    const float2 l = Ls2[(int)(ent[r] >> 16) * ldS + c];
+                    const float xf = (float)(ent[r] & 0xFFFFu);
+                    t0 = fmaf(xf, l.x, t0);
+                    t1 = fmaf(xf, l.y, t1);
+                }
+            }
+        }
+        for (int64_t e = beg + lane + (packed ? 32 * R : 0); e < end; e += 32) {
+            int32_t u, x;
+            a.csr.get(e, u, x);
+            const float2 l = Ls2[(size_t)u * ldS + c];
+            t0 = fmaf((float)x, l.x, t0);
+            t1 = fmaf((float)x, l.y, t1);
+        }
+        t0 = warp_sum(t0);
+        t1 = warp_sum(t1);
+        uint32_t s = 0;
+        if (lane == 0) {
+            // log weights of eq. 8: log n-bar, or log(n-bar - 1) for the cell's own old slot
+            const bool stays = state_label(old) == (uint32_t)c;
+            const uint32_t so = state_sub(old);
+            const float lw0 = slw[4 * c + (stays && so == 0 ? 1 : 0)];
+            const float lw1 = slw[4 * c + 2 + (stays && so == 1 ? 1 : 0)];
+            const bool both_empty = lw0 == -CUDART_INF_F && lw1 == -CUDART_INF_F;
+            const float l0 = (both_empty ? 0.0f : lw0) + t0;
+            const float l1 = (both_empty ? 0.0f : lw1) + t1;
+            s = (l1 + h1 > l0 + h0) ? 1u : 0u;
+            const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
+            const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
+            a.state[cell] = pack_state((uint32_t)c, s);
+            my_sq[c] += (double)logq;
+            my_n[2 * c + s] += 1u;
+        }
+        if (sS) {
+            // pass 3: the row into the block's statistics of (c, s)
+            s = __shfl_sync(0xFFFFFFFFu, s, 0);
+            uint32_t* dst = sS + (size_t)(2 * c + s) * a.D;
+            if (packed) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (r < slots && lane + 32 * r < len && (ent[r] & 0xFFFFu))
+                        atomicAdd(dst + (ent[r] >> 16), ent[r] & 0xFFFFu);
+            }
+            for (int64_t e = beg + lane + (packed ? 32 * R : 0); e < end; e += 32) {
+                int32_t u, x;
+                a.csr.get(e, u, x);
+                if (x) atomicAdd(dst + u, (uint32_t)x);
+            }
         }
     }
 }
@@ -226,28 +487,94 @@ __device__ __forceinline__ void assign_cells(const AssignArgs& a, const float* L
 __global__ void __launch_bounds__(kAssignThreads, 1)
 k_assign(AssignArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* blk_sumlogq = reinterpret_cast<double*>(smem_raw);
-    float* sL = reinterpret_cast<float*>(smem_raw + (size_t)a.kmax * sizeof(double));
     const int K = a.sc->K;
     const uint32_t t = a.sc->t;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) blk_sumlogq[k] = 0.0;
-    const bool in_smem = (int64_t)K * a.D <= a.table_cap;
-    if (in_smem) {
-        for (int64_t i = threadIdx.x; i < (int64_t)K * a.D; i += blockDim.x) {
-            const int64_t u = i / K, k = i - u * K;
-            sL[i] = __ldg(a.Lc + u * a.kmax + k);
-        }
+    // per-warp accumulators exist only on the K <= 32 path
+    const int nw = K <= 32 ? (int)(blockDim.x >> 5) : 0;
+    // small per-block arrays first: per-warp sum log q and n-bar, block sum log q,
+    // log pi and the sweep-start n-bar
+    double* wsq = reinterpret_cast<double*>(smem_raw);                  // [nw][K]
+    double* blk_sumlogq = wsq + (size_t)nw * K;                          // [K]
+    uint32_t* wn = reinterpret_cast<uint32_t*>(blk_sumlogq + K);         // [nw][2K]
+    float* spi = reinterpret_cast<float*>(wn + (size_t)nw * 2 * K);      // [K]
+    float* slw = spi + K;                                                // [K][2][2]
+    const size_t head = ((size_t)(reinterpret_cast<unsigned char*>(slw + 4 * K) - smem_raw) + 15) &
+                        ~(size_t)15;
+    unsigned char* rest = smem_raw + head;
+    const int64_t avail = a.smem_bytes - (int64_t)head;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        blk_sumlogq[k] = 0.0;
+        spi[k] = a.logpi[k];
     }
-    __syncthreads();
-    const float* L = in_smem ? sL : a.Lc;
-    const int ldL = in_smem ? K : a.kmax;
-    const int Q = (K + 31) >> 5;
-    if (Q <= 1) assign_cells<1>(a, L, ldL, K, t, blk_sumlogq);
-    else if (Q <= 2) assign_cells<2>(a, L, ldL, K, t, blk_sumlogq);
-    else if (Q <= 4) assign_cells<4>(a, L, ldL, K, t, blk_sumlogq);
-    else if (Q <= 8) assign_cells<8>(a, L, ldL, K, t, blk_sumlogq);
-    else if (Q <= 16) assign_cells<16>(a, L, ldL, K, t, blk_sumlogq);
-    else assign_cells<32>(a, L, ldL, K, t, blk_sumlogq);
+    for (int i = threadIdx.x; i < nw * K; i += blockDim.x) wsq[i] = 0.0;
+    for (int i = threadIdx.x; i < nw * 2 * K; i += blockDim.x) wn[i] = 0u;
+    // eq. 8 weights: log n-bar_{k,r} and log(n-bar_{k,r} - 1); log 0 = -inf
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
+        const float n = (float)a.nsub[i];
+        slw[2 * i] = n > 0.0f ? logf(n) : -CUDART_INF_F;
+        slw[2 * i + 1] = n > 1.0f ? logf(n - 1.0f) : -CUDART_INF_F;
+    }
+    const int D = a.D;
+    const int Kp = (K + 3) & ~3;
+    const int64_t bytes_c = (int64_t)D * Kp * 4, bytes_s = (int64_t)D * K * 8;
+    const int64_t bytes_st = (int64_t)2 * K * D * 4;
+    if (K <= 32 && bytes_c <= avail) {
+        float* sLc = reinterpret_cast<float*>(rest);
+        const bool sub_in = bytes_c + bytes_s <= avail;
+        float2* sLs = reinterpret_cast<float2*>(rest + bytes_c);
+        const bool fused = sub_in && bytes_c + bytes_s + bytes_st <= avail;
+        uint32_t* sS = fused ? reinterpret_cast<uint32_t*>(rest + bytes_c + bytes_s) : nullptr;
+        for (int64_t i = threadIdx.x; i < (int64_t)D * Kp; i += blockDim.x) {
+            const int64_t u = i / Kp, k = i - u * Kp;
+            sLc[i] = k < K ? __ldg(a.Lc + u * a.kmax + k) : 0.0f;
+        }
+        if (sub_in)
+            for (int64_t i = threadIdx.x; i < (int64_t)D * K; i += blockDim.x) {
+                const int64_t u = i / K, k = i - u * K;
+                sLs[i] = __ldg(a.Ls2 + u * a.kmax + k);
+            }
+        if (fused)
+            for (int64_t i = threadIdx.x; i < (int64_t)2 * K * D; i += blockDim.x) sS[i] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->stats_fused = fused ? 1 : 0;
+        __syncthreads();
+        const float2* Ls2 = sub_in ? sLs : a.Ls2;
+        const int ldS = sub_in ? K : a.kmax;
+        if (K <= 4) assign_cells_v2<4>(a, sLc, Kp, Ls2, ldS, K, t, spi, slw, wsq, wn, sS);
+        else if (K <= 8) assign_cells_v2<8>(a, sLc, Kp, Ls2, ldS, K, t, spi, slw, wsq, wn, sS);
+        else if (K <= 16) assign_cells_v2<16>(a, sLc, Kp, Ls2, ldS, K, t, spi, slw, wsq, wn, sS);
+        else assign_cells_v2<32>(a, sLc, Kp, Ls2, ldS, K, t, spi, slw, wsq, wn, sS);
+        __syncthreads();
+        if (fused) {
+            for (int64_t i = threadIdx.x; i < (int64_t)2 * K * D; i += blockDim.x) {
+                const uint32_t v = sS[i];
+                if (v) atomicAdd(&a.acc_Ssub[i], v);
+            }
+            for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
+                uint32_t v = 0;
+                for (int w = 0; w < nw; ++w) v += wn[w * 2 * K + i];
+                if (v) atomicAdd(&a.acc_nsub[i], v);
+            }
+        }
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            double v = 0.0;
+            for (int w = 0; w < nw; ++w) v += wsq[w * K + k];
+            blk_sumlogq[k] = v;
+        }
+    } else {
+        // large K: lanes own clusters, table in shared memory when it fits
+        float* sL = reinterpret_cast<float*>(rest);
+        const bool in_smem = (int64_t)K * D * 4 <= avail;
+        if (in_smem)
+            for (int64_t i = threadIdx.x; i < (int64_t)K * D; i += blockDim.x) {
+                const int64_t u = i / K, k = i - u * K;
+                sL[i] = __ldg(a.Lc + u * a.kmax + k);
+            }
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->stats_fused = 0;
+        __syncthreads();
+        const float* L = in_smem ? sL : a.Lc;
+        const int ldL = in_smem ? K : a.kmax;
+        assign_cells(a, L, ldL, K, t, blk_sumlogq);
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x)
         if (blk_sumlogq[k] != 0.0) atomicAdd(&a.acc_sumlogq[k], blk_sumlogq[k]);
@@ -265,7 +592,7 @@ k_stats(Csr csr, const DevScalars* __restrict__ sc_ro, DevScalars* sc_rw,
         uint32_t* __restrict__ nsub, uint32_t* __restrict__ Ssub, uint32_t* bump, int64_t N,
         int32_t D, int64_t priv_cap, int only_if_reinit) {
     extern __shared__ __align__(16) uint32_t spriv[];
-    if (only_if_reinit && !sc_ro->any_reinit) {
+    if ((only_if_reinit == 1 && !sc_ro->any_reinit) || (only_if_reinit == 2 && sc_ro->stats_fused)) {
         if (bump && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1u;
         return;
     }
@@ -382,7 +709,19 @@ __global__ void k_init_state(uint32_t* __restrict__ state, int64_t N, Stream st)
     }
 }
 
-// Scores of selected cells with the sweep's own contraction routines.
+// Scores of selected cells with the label kernel's own contraction routines
+// (same per-lane order of products and the same reductions).
+template <int P>
+__device__ __forceinline__ void debug_cell_v2(const Csr& csr, int64_t beg, int64_t end,
+                                              const float* Lc, int kmax, int K, int lane,
+                                              const float* logpi, float* o) {
+    float acc[P];
+    lane_partials<P, false>(csr, beg, end, Lc, kmax, K, lane, acc);
+    int col;
+    const float sc = warp_reduce_scatter<P>(acc, lane, &col);
+    if (col < K && (lane & ((32 / P) - 1)) == 0) o[col] = __ldg(logpi + col) + sc;
+}
+
 __global__ void k_debug_scores(Csr csr, const DevScalars* __restrict__ sc,
                                const float* __restrict__ logpi, const float* __restrict__ Lc,
                                const float2* __restrict__ Ls2, int32_t kmax,
@@ -395,13 +734,19 @@ __global__ void k_debug_scores(Csr csr, const DevScalars* __restrict__ sc,
     const int64_t cell = cells[wid];
     const int64_t beg = csr.indptr[cell], end = csr.indptr[cell + 1];
     float* o = out + (size_t)wid * 3 * K;
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        float acc[1];
-        cluster_scores<1>(csr, beg, end, Lc + k0, kmax, K - k0, lane, acc);
-        if (k0 + lane < K) o[k0 + lane] = __ldg(logpi + k0 + lane) + acc[0];
+    if (K <= 4) debug_cell_v2<4>(csr, beg, end, Lc, kmax, K, lane, logpi, o);
+    else if (K <= 8) debug_cell_v2<8>(csr, beg, end, Lc, kmax, K, lane, logpi, o);
+    else if (K <= 16) debug_cell_v2<16>(csr, beg, end, Lc, kmax, K, lane, logpi, o);
+    else if (K <= 32) debug_cell_v2<32>(csr, beg, end, Lc, kmax, K, lane, logpi, o);
+    else {
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            float acc[1];
+            cluster_scores<1>(csr, beg, end, Lc + k0, kmax, K - k0, lane, acc);
+            if (k0 + lane < K) o[k0 + lane] = __ldg(logpi + k0 + lane) + acc[0];
+        }
     }
     for (int k = 0; k < K; ++k) {
-        const float2 l = sub_scores(csr, beg, end, Ls2, kmax, k, lane);
+        const float2 l = sub_pair(csr, beg, end, Ls2, kmax, k, lane);
         if (lane == 0) {
             o[K + 2 * k] = l.x;
             o[K + 2 * k + 1] = l.y;
@@ -453,7 +798,9 @@ cudaError_t launch_assign(Ctx& c) {
     a.N = c.N;
     a.D = c.D;
     a.kmax = c.kmax;
-    a.table_cap = (int32_t)((c.assign_smem - (size_t)c.kmax * sizeof(double)) / sizeof(float));
+    a.acc_nsub = c.acc_nsub;
+    a.acc_Ssub = c.acc_Ssub;
+    a.smem_bytes = (int64_t)c.assign_smem;
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
     k_assign<<<c.assign_blocks, kAssignThreads, c.assign_smem, c.stream>>>(a);
     return cudaGetLastError();
@@ -464,6 +811,14 @@ cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* 
     k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
         csr_of(c), c.sc, c.sc, c.state, mask, nsub, Ssub, bump, c.N, c.D,
         (int64_t)(c.stats_smem / sizeof(uint32_t)), mask != nullptr ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Statistics of a sweep's new labels unless the label kernel already added them.
+cudaError_t launch_sweep_stats(Ctx& c) {
+    k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
+        csr_of(c), c.sc, c.sc, c.state, nullptr, c.acc_nsub, c.acc_Ssub, nullptr, c.N, c.D,
+        (int64_t)(c.stats_smem / sizeof(uint32_t)), 2);
     return cudaGetLastError();
 }
 

@@ -345,3 +345,45 @@ def test_phase_timing_events_in_graph(P, tiny):
     g.sweep(1)                      # eager calls record the same events
     ms2 = P.dpmm_phase_times(g.ctx, 4)
     assert np.all(ms2 > 0)
+
+
+@pytest.mark.parametrize("K", [2, 4, 8, 14, 16, 24, 32, 40, 120])
+def test_assign_parity_across_kernel_variants(P, tiny, K):
+    """Every label-kernel variant (lanes per column P = 4..32 with and without spare
+    lanes, fused and separate statistics, shared-memory and global tables for K > 32)
+    against the oracle from an injected state and injected parameters."""
+    from oracle.sampler import Sampler as OracleSampler, sufficient_stats
+    rng = np.random.default_rng(K)
+    labels = rng.integers(0, K, size=tiny.N)
+    labels[:K] = np.arange(K)
+    sub = rng.integers(0, 2, size=tiny.N)
+    o = OracleSampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, seed=17,
+                      kmax=128)
+    o.set_state(labels, sub, K, t=5, m=2)
+    g = P.Sampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, kmax=128, seed=17)
+    P.dpmm_set_state(g.ctx, o.labels, o.sub, o.K, o.t, o.m, o.sumlogq)
+    P.dpmm_draw_params(g.ctx)
+    logpi32, logtheta32 = P.dpmm_get_params(g.ctx, K, tiny.D)
+    P.dpmm_set_params(g.ctx, logpi32, logtheta32)
+    logpi, logtheta = logpi32.astype(np.float64), logtheta32.astype(np.float64)
+    s, v = oracle_perturbed(o, logpi, logtheta)
+    srt = np.sort(v, axis=1)
+    near = (srt[:, -1] - srt[:, -2]) < SCORE_RTOL * np.abs(s).max(axis=1) + SCORE_ATOL
+    cells = np.arange(0, tiny.N, 37)
+    got = P.dpmm_debug_scores(g.ctx, cells, K)
+    np.testing.assert_allclose(got[:, :K], s[cells], rtol=SCORE_RTOL, atol=SCORE_ATOL)
+    o.assign_and_update(logpi, logtheta)
+    P.dpmm_assign(g.ctx)
+    lab, sb, Kg, t, m = g.get_state()
+    assert t == o.t
+    if Kg == o.K:
+        mism = lab != o.labels
+        assert np.all(near[mism]), f"{mism.sum()} mismatches, {near.sum()} near-ties"
+        # sub-labels agree wherever the label agrees, up to near-ties of eq. 8
+        assert np.mean(sb[~mism] == o.sub[~mism]) > 0.995
+    nsub, Ssub, sq = g.stats()
+    on, oS = sufficient_stats(o.X, lab, sb, Kg)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    if Kg == o.K and np.array_equal(lab, o.labels) and np.array_equal(sb, o.sub):
+        np.testing.assert_allclose(sq, o.sumlogq, rtol=1e-4, atol=1e-2)
