@@ -33,7 +33,7 @@ L2_FLUSH_BYTES = 256 << 20
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
-KERNELS_PER_STEP = 16     # 8 sweep kernels + 8 move kernels (see csrc/sweep.cu, moves.cu)
+KERNELS_PER_STEP = 18     # 10 sweep kernels (tile engine) + 8 move kernels (csrc/*.cu)
 
 
 def parse():
@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--engine", default="csr_fp32", choices=["csr_fp32", "auto"])
+    ap.add_argument("--engine", default="both", choices=["both", "csr_fp32"])
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -208,6 +208,43 @@ def oracle_steps_per_sec(ds, state, seconds, cells=None):
 
 
 # ---------------------------------------------------------------------------
+def timed_chain(P, ds, engine, args, rank, local, torch):
+    """Warm up and time one chain on `engine`; per-step device times with the L2
+    flushed before every step."""
+    s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                  chain_id=rank, engine=engine)
+    stream = torch.cuda.ExternalStream(s.stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    P.dpmm_profile(s.ctx, True)
+    s.step(args.warmup)
+    s.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phases = np.zeros((args.steps, 5), dtype=np.float64)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            starts[i].record(stream)
+        s.step(1)
+        ends[i].record(stream)
+        phases[i] = P.dpmm_phase_times(s.ctx, 5)   # events of this step (synchronises)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
+    labels, K = s.labels()
+    state = s.get_state()
+    _, _, sumlogq = s.stats()
+    s.close()
+    return {"total_ms": float(step_ms.sum()), "step_ms": step_ms, "phases": phases, "K": K,
+            "labels": labels, "wall_s": wall, "clocks": clk,
+            "state": (state[0], state[1], state[2], state[3], state[4], sumlogq)}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -222,61 +259,30 @@ def run_ours(args, rank, world, local):
     import paper_1812_10048_gb300 as P
 
     ds, gen_s = workload()
-    engine = P.ENGINE_CSR_FP32 if args.engine == "csr_fp32" else P.ENGINE_AUTO
-    s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
-                  chain_id=rank, engine=engine)
-    stream = torch.cuda.ExternalStream(s.stream)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    engines = {"bf16": P.ENGINE_AUTO, "fp32": P.ENGINE_CSR_FP32}
+    if args.engine == "csr_fp32":
+        engines = {"fp32": P.ENGINE_CSR_FP32}
+    res = {}
+    for name, eng in engines.items():
+        if world > 1:
+            dist.barrier()
+        r = timed_chain(P, ds, eng, args, rank, local, torch)
+        if world > 1:
+            t = torch.tensor([r["total_ms"]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            r["total_ms"] = float(t.item())
+        res[name] = r
+    result = {"rank": rank, "forms": res, "ds": ds, "gen_s": gen_s,
+              "primary": "bf16" if "bf16" in res else "fp32"}
 
-    # warm-up (also captures the step graph, with per-phase timing events)
-    P.dpmm_profile(s.ctx, True)
-    s.step(args.warmup)
-    s.sync()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    phases = np.zeros((args.steps, 5), dtype=np.float64)
-    Ks = np.zeros(args.steps, dtype=np.int64)
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            starts[i].record(stream)
-        s.step(1)
-        ends[i].record(stream)
-        phases[i] = P.dpmm_phase_times(s.ctx, 5)   # events of this step (synchronises)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    clk = clocks.stop()
-    step_ms = np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    labels, K_final = s.labels()
-    state = s.get_state()
-    _, _, sumlogq = s.stats()
-
-    result = {"rank": rank, "total_ms": total_ms, "step_ms": step_ms, "phases": phases,
-              "K_final": K_final, "wall_s": wall, "clocks": clk, "labels": labels,
-              "state": (state[0], state[1], state[2], state[3], state[4], sumlogq), "ds": ds,
-              "gen_s": gen_s}
-
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers (primary form)
     if rank == 0:
         pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                for a in (ds.indptr, ds.indices, ds.data)]
-        lab_out = torch.empty(ds.N, dtype=torch.int32).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = P.Sampler(pin[0], pin[1], pin[2], ds.N, ds.D, 1.0, 0.1, kmax=256, seed=43,
-                       engine=engine)
+                       engine=engines[result["primary"]])
         s2.step(args.e2e_steps)
         lab, K2 = P.dpmm_labels(s2.ctx, ds.N)
         e2e_s = time.perf_counter() - t0
@@ -288,7 +294,6 @@ def run_ours(args, rank, world, local):
             "steps": args.e2e_steps, "seconds": e2e_s,
             "what": "dpmm_init from pinned host CSR + steps + dpmm_labels to host, wall clock",
         }
-    s.close()
     return result
 
 
@@ -308,26 +313,46 @@ def main():
     if rank != 0:
         return 0
     ds = r["ds"]
-    K = int(r["K_final"])
+    prim = r["forms"][r["primary"]]
+    K = int(prim["K"])
     steps = args.steps
-    ms_per_step = r["total_ms"] / steps
-    value = world * steps / (r["total_ms"] / 1e3)
+    ms_per_step = prim["total_ms"] / steps
+    value = world * steps / (prim["total_ms"] / 1e3)
     peak, peak_kind = hbm_peak()
-    assign_ms = float(np.mean(r["phases"][:, 1]))
+    assign_ms = float(np.mean(prim["phases"][:, 1]))
     a_bytes = assign_algorithmic_bytes(ds, K)
     achieved = a_bytes / (assign_ms * 1e-3) / 1e9
     step_bytes = step_algorithmic_bytes(ds, K)
-
+    from oracle.ari import adjusted_rand_index
+    forms = {}
+    for name, f in r["forms"].items():
+        forms[name] = {
+            "sweeps_per_s": round(world * steps / (f["total_ms"] / 1e3), 2),
+            "ms_per_step": round(f["total_ms"] / steps, 5),
+            "phase_ms": {n: round(float(np.mean(f["phases"][:, i])), 5) for i, n in
+                         enumerate(["draw", "assign", "stats", "compact", "moves"])},
+            "K_final": int(f["K"]),
+            "ari_vs_truth": round(adjusted_rand_index(f["labels"], ds.labels), 4),
+            "clocks": f["clocks"],
+        }
+    if "bf16" in r["forms"] and "fp32" in r["forms"]:
+        forms["ari_bf16_vs_fp32_labels"] = round(
+            adjusted_rand_index(r["forms"]["bf16"]["labels"], r["forms"]["fp32"]["labels"]), 4)
+    kname = ("k_assign_tc (tcgen05 BF16 hi/lo contraction + Gumbel-max + eq. 8 + statistics)"
+             if r["primary"] == "bf16" else
+             "k_assign (FP32 CSR contraction + Gumbel-max + eq. 8 + statistics)")
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if r["primary"] == "bf16" else "f32",
         "data": "synthetic", "config": workload_config(ds),
         "roofline": {
-            "kernel": "k_assign (contraction + Gumbel-max labels + eq. 8 sub-labels)",
+            "kernel": kname,
             "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-            "traffic": traffic_for("k_assign", "pbmc68k"),
+            "traffic": traffic_for("k_assign_tc" if r["primary"] == "bf16" else "k_assign",
+                                   "pbmc68k"),
             "algorithmic_bytes_per_launch": int(a_bytes), "avg_launch_ms": round(assign_ms, 5),
             "K": K,
         },
@@ -336,21 +361,15 @@ def main():
             "unit": "GB/s", "frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
             "algorithmic_bytes_per_step": int(step_bytes),
         },
-        "phase_ms": {n: round(float(np.mean(r["phases"][:, i])), 5) for i, n in
-                     enumerate(["draw", "assign", "stats", "compact", "moves"])},
+        "forms": forms,
         "e2e": r.get("e2e"),
         "gpu_launches": KERNELS_PER_STEP * steps,
-        "clocks": r["clocks"],
-        "wall_s_timed_loop": round(r["wall_s"], 3),
+        "clocks": prim["clocks"],
+        "wall_s_timed_loop": round(prim["wall_s"], 3),
     }
-    try:
-        from oracle.ari import adjusted_rand_index
-        line["ari_vs_truth"] = round(adjusted_rand_index(r["labels"], ds.labels), 4)
-    except Exception as e:  # noqa: BLE001
-        line["ari_vs_truth"] = f"unavailable: {e}"
     if not args.no_cpu_baseline and world == 1:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
-        rate, n_steps, el, cells = oracle_steps_per_sec(ds, r["state"], args.cpu_seconds)
+        rate, n_steps, el, cells = oracle_steps_per_sec(ds, prim["state"], args.cpu_seconds)
         line["cpu_baseline"] = {
             "value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n_steps} oracle steps (sweep + split/merge, FP64 numpy/scipy) on the "

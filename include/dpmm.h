@@ -182,6 +182,17 @@ int dpmm_set_params(dpmm_ctx* ctx, const float* logpi, const float* logtheta);
  */
 int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out);
 
+/*
+ * Dense-tile engine scores of every cell under the current parameters, from
+ * the tensor-core contraction without changing the chain: out float[N][3K],
+ * column k = sum_u x_i^u (log theta_k^u - m_u) and column K + 2k + r =
+ * sum_u x_i^u (log theta-bar_{k,r}^u - m_u), where m_u is the mean of the 3K
+ * log theta values of gene u (the centring the engine applies; it shifts a
+ * cell's scores by a common constant).  DPMM_ESTATE if the engine is off or
+ * K > 40.  Synchronises.
+ */
+int dpmm_debug_tile_scores(dpmm_ctx* ctx, float* out);
+
 /* Split/merge diagnostics of the last dpmm_split_merge call: chain (1 split,
  * 2 merge), and log H per cluster (split; NaN where no proposal) or per pair
  * (merge, with the pair's cluster indices a < b in pair_ab int32[2][n]).
@@ -253,6 +264,13 @@ int dpmm_logml_grad_noalloc(const int32_t* indptr, const int32_t* indices, const
 /* Philox4x32-10 words of the device generator: ctr uint32[n][4] -> out
  * uint32[n][4] with key (seed lo, seed hi).  Synchronises. */
 int dpmm_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n);
+
+/* Tensor-core self-test: C[128][N] = A[128][Kd] * B[N][Kd]^T with BF16
+ * operands (uint16 bit patterns) and FP32 accumulation, through the same
+ * operand layout, descriptors and tensor-memory path as the dense-tile
+ * engine.  Kd in {64, 128, 192, 256}, N a multiple of 16 in [16, 256].
+ * Host or device pointers.  Synchronises. */
+int dpmm_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int32_t Kd, int32_t N, float* C);
 
 /* The first n 4-word outputs of cuRAND's Philox4_32_10 generator after
  * curand_init(seed, 0, 0) (consecutive curand4 calls), out uint32[n][4]:

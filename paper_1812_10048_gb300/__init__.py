@@ -19,10 +19,10 @@ __all__ = [
     "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
     "dpmm_phase_times", "dpmm_get_state",
     "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
-    "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_moves", "dpmm_logml_create",
+    "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_tile_scores", "dpmm_debug_moves", "dpmm_logml_create",
     "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_logml_grad_noalloc",
     "dpmm_debug_philox",
-    "dpmm_debug_curand_philox", "ENGINE_AUTO", "ENGINE_CSR_FP32", "ENGINE_TILE_BF16",
+    "dpmm_debug_curand_philox", "dpmm_debug_tc_gemm", "ENGINE_AUTO", "ENGINE_CSR_FP32", "ENGINE_TILE_BF16",
 ]
 
 
@@ -146,6 +146,12 @@ def dpmm_debug_scores(ctx, cells, K):
     return out
 
 
+def dpmm_debug_tile_scores(ctx, N, K):
+    out = np.empty((int(N), 3 * int(K)), dtype=np.float32)
+    check(lib().dpmm_debug_tile_scores(ctx, ptr(out)))
+    return out
+
+
 def dpmm_debug_moves(ctx, kmax):
     chain, n = ctypes.c_int32(0), ctypes.c_int32(0)
     log_h = np.empty(kmax, dtype=np.float64)
@@ -205,6 +211,15 @@ def dpmm_debug_curand_philox(seed, n):
     out = np.empty((int(n), 4), dtype=np.uint32)
     check(lib().dpmm_debug_curand_philox(int(seed), int(n), ptr(out)))
     return out
+
+
+def dpmm_debug_tc_gemm(A_bf16, B_bf16):
+    """C = A B^T on the tensor cores; A uint16[128][Kd], B uint16[N][Kd] (bf16 bits)."""
+    A = np.ascontiguousarray(A_bf16, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bf16, dtype=np.uint16)
+    C = np.empty((128, B.shape[0]), dtype=np.float32)
+    check(lib().dpmm_debug_tc_gemm(ptr(A), ptr(B), int(A.shape[1]), int(B.shape[0]), ptr(C)))
+    return C
 
 
 class Sampler:

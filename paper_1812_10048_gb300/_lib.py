@@ -59,6 +59,7 @@ SIGNATURES = {
     "dpmm_set_params": (ctypes.c_int, [_P, _P, _P]),
     "dpmm_debug_scores": (ctypes.c_int, [_P, _P, _I32, _P]),
     "dpmm_debug_moves": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "dpmm_debug_tile_scores": (ctypes.c_int, [_P, _P]),
     "dpmm_logml_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, _P, _I64, _I32, _P, _I32,
                                          _P]),
     "dpmm_logml_free": (None, [_P]),
@@ -68,6 +69,7 @@ SIGNATURES = {
                                                _P, _P, _P]),
     "dpmm_debug_philox": (ctypes.c_int, [_P, _U64, _P, _I64]),
     "dpmm_debug_curand_philox": (ctypes.c_int, [_U64, _I64, _P]),
+    "dpmm_debug_tc_gemm": (ctypes.c_int, [_P, _P, _I32, _I32, _P]),
 }
 
 _lib = None

@@ -104,7 +104,7 @@ void free_ctx(Ctx& c) {
     void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
                     c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
-                    c.move_part};
+                    c.move_part, c.tile_ent, c.tile_ptr, c.tile_B};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.sc_host) cudaFreeHost(c.sc_host);
@@ -301,6 +301,37 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         CKI(cudaMemcpyAsync(c.counts, hval.data(), sizeof(int32_t) * nnz,
                             cudaMemcpyHostToDevice, c.stream));
     }
+    if (c.packed && o.engine != DPMM_ENGINE_CSR_FP32) {
+        // blocked copy for the dense-tile engine: entries grouped by (tile, chunk)
+        c.tile_T = (int32_t)((N + 127) / 128);
+        c.tile_C = (D + 63) / 64;
+        const size_t TC = (size_t)c.tile_T * c.tile_C;
+        std::vector<int32_t> tptr(TC + 1, 0);
+        for (int64_t i = 0; i < N; ++i) {
+            const size_t tb = (size_t)(i >> 7) * c.tile_C;
+            for (int32_t e = hptr[i]; e < hptr[i + 1]; ++e) tptr[tb + (hidx[e] >> 6) + 1]++;
+        }
+        for (size_t j = 0; j < TC; ++j) tptr[j + 1] += tptr[j];
+        std::vector<int32_t> cur(tptr.begin(), tptr.end() - 1);
+        std::vector<uint32_t> tent((size_t)nnz);
+        for (int64_t i = 0; i < N; ++i) {
+            const size_t tb = (size_t)(i >> 7) * c.tile_C;
+            const uint32_t r = (uint32_t)(i & 127);
+            for (int32_t e = hptr[i]; e < hptr[i + 1]; ++e)
+                tent[cur[tb + (hidx[e] >> 6)]++] =
+                    (r << 22) | ((uint32_t)(hidx[e] & 63) << 16) | (uint32_t)hval[e];
+        }
+        CKI(dalloc(&c.tile_ent, (size_t)nnz));
+        CKI(dalloc(&c.tile_ptr, TC + 1));
+        CKI(dalloc(&c.tile_B, tile_b_bytes(c.tile_C)));
+        CKI(cudaMemcpyAsync(c.tile_ptr, tptr.data(), sizeof(int32_t) * (TC + 1),
+                            cudaMemcpyHostToDevice, c.stream));
+        if (nnz)
+            CKI(cudaMemcpyAsync(c.tile_ent, tent.data(), sizeof(uint32_t) * nnz,
+                                cudaMemcpyHostToDevice, c.stream));
+        CKI(cudaStreamSynchronize(c.stream));
+        c.tile_enabled = true;
+    }
     CKI(cudaMemsetAsync(c.acc_nsub, 0, sizeof(uint32_t) * K2, c.stream));
     CKI(cudaMemsetAsync(c.acc_Ssub, 0, sizeof(uint32_t) * K2 * D, c.stream));
     CKI(cudaMemsetAsync(c.acc_sumlogq, 0, sizeof(double) * c.kmax, c.stream));
@@ -311,6 +342,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     c.sc_host->K_new = 1;
     CKI(cudaMemcpyAsync(c.sc, c.sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c.stream));
     CKI(configure_launches(c));
+    if (c.tile_enabled) CKI(configure_tile(c));
     CKI(launch_lg_table(c));
     CKI(launch_init_state(c));
     if (recount_all(c) != DPMM_OK) return bail(DPMM_ECUDA);
@@ -582,6 +614,27 @@ int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out
     return DPMM_OK;
 }
 
+int dpmm_debug_tile_scores(dpmm_ctx* ctx, float* out) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (!out) return fail(DPMM_EINVAL, "out is null");
+    if (!c.tile_enabled) return fail(DPMM_ESTATE, "the dense-tile engine is not enabled");
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    const int K = c.sc_host->K;
+    if (K > 40) return fail(DPMM_ESTATE, "K = %d exceeds the dense-tile engine's 40", K);
+    float* d = nullptr;
+    CK(dalloc(&d, (size_t)c.N * 3 * K));
+    cudaError_t e = launch_tile_assign(c, d);
+    if (!e) e = cudaStreamSynchronize(c.stream);
+    if (!e) e = cudaMemcpy(out, d, sizeof(float) * (size_t)c.N * 3 * K, cudaMemcpyDefault);
+    cudaFree(d);
+    CK(e);
+    if ((rc = sync_scalars(c))) return rc;
+    if (c.sc_host->error) return fail(c.sc_host->error, "device error %d", c.sc_host->error);
+    return DPMM_OK;
+}
+
 int dpmm_debug_moves(dpmm_ctx* ctx, int32_t* chain, double* log_h, int32_t* pair_ab,
                      int32_t* n_entries) {
     CHECK_CTX(ctx);
@@ -765,6 +818,34 @@ int dpmm_debug_curand_philox(uint64_t seed, int64_t n, uint32_t* out) {
     if (!e) e = cudaMemcpy(out, dout, sizeof(uint4) * n, cudaMemcpyDefault);
     cudaFree(dout);
     CK(e);
+    return DPMM_OK;
+}
+
+int dpmm_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int32_t Kd, int32_t N, float* C) {
+    if (!A || !B || !C) return fail(DPMM_EINVAL, "null pointer");
+    if (Kd < 64 || Kd > 256 || Kd % 64 || N < 16 || N > 256 || N % 16)
+        return fail(DPMM_EINVAL, "need Kd in {64,128,192,256} and N a multiple of 16 in [16, 256]");
+    uint16_t *dA = nullptr, *dB = nullptr;
+    float* dC = nullptr;
+    int* derr = nullptr;
+    cudaError_t e = dalloc(&dA, (size_t)128 * Kd);
+    if (!e) e = dalloc(&dB, (size_t)N * Kd);
+    if (!e) e = dalloc(&dC, (size_t)128 * N);
+    if (!e) e = dalloc(&derr, 1);
+    if (!e) e = cudaMemcpy(dA, A, sizeof(uint16_t) * 128 * Kd, cudaMemcpyDefault);
+    if (!e) e = cudaMemcpy(dB, B, sizeof(uint16_t) * N * Kd, cudaMemcpyDefault);
+    if (!e) e = cudaMemset(derr, 0, sizeof(int));
+    if (!e) e = launch_debug_tc_gemm(dA, dB, Kd, N, dC, derr);
+    if (!e) e = cudaDeviceSynchronize();
+    int herr = 0;
+    if (!e) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(C, dC, sizeof(float) * 128 * N, cudaMemcpyDefault);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dC);
+    cudaFree(derr);
+    CK(e);
+    if (herr) return fail(herr, "tensor-core self-test: bounded wait gave up");
     return DPMM_OK;
 }
 

@@ -70,6 +70,8 @@ struct DevScalars {
     int32_t n_entries;    // split: K proposals; merge: number of pairs
     int32_t error;        // sticky device error (DPMM_E*)
     int32_t stats_fused;  // the label kernel of this sweep also added the statistics
+    int32_t tile_used;    // the dense-tile engine labelled this sweep's cells
+    int32_t pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -131,6 +133,13 @@ struct Ctx {
     int stats_blocks = 0;
     size_t assign_smem = 0;
     size_t stats_smem = 0;
+
+    // dense-tile engine: counts blocked by (128-cell tile, 64-gene chunk)
+    bool tile_enabled = false;
+    int32_t tile_T = 0, tile_C = 0;
+    uint32_t* tile_ent = nullptr;   // row << 22 | gene-in-chunk << 16 | count
+    int32_t* tile_ptr = nullptr;    // [T * C + 1]
+    unsigned char* tile_B = nullptr;  // per-sweep BF16 hi/lo table, [C][256 rows][64] swizzled
 
     // CUDA graph of dpmm_step
     cudaGraphExec_t step_exec = nullptr;
@@ -277,5 +286,10 @@ size_t move_partial_bytes();
 size_t lg_table_entries();
 cudaError_t launch_init_state(Ctx& c);
 cudaError_t launch_debug_scores(Ctx& c, const int32_t* cells, int32_t n, float* out);
+cudaError_t configure_tile(Ctx& c);
+cudaError_t launch_tile_assign(Ctx& c, float* dbg);
+size_t tile_b_bytes(int32_t C);
+cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, int N, float* C,
+                                 int* err);
 
 }  // namespace dpmm

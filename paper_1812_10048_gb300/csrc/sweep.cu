@@ -487,6 +487,7 @@ __device__ __forceinline__ void assign_cells_v2(const AssignArgs& a, const float
 __global__ void __launch_bounds__(kAssignThreads, 1)
 k_assign(AssignArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.sc->tile_used) return;   // the dense-tile engine labelled this sweep
     const int K = a.sc->K;
     const uint32_t t = a.sc->t;
     // per-warp accumulators exist only on the K <= 32 path
@@ -802,6 +803,10 @@ cudaError_t launch_assign(Ctx& c) {
     a.acc_Ssub = c.acc_Ssub;
     a.smem_bytes = (int64_t)c.assign_smem;
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
+    if (c.tile_enabled) {
+        cudaError_t e = launch_tile_assign(c, nullptr);
+        if (e != cudaSuccess) return e;
+    }
     k_assign<<<c.assign_blocks, kAssignThreads, c.assign_smem, c.stream>>>(a);
     return cudaGetLastError();
 }

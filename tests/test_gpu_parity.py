@@ -39,7 +39,10 @@ def tiny():
 
 
 def make_pair(P, ds, alpha=1.0, beta=0.5, seed=42, kmax=64, **kw):
+    """A GPU chain on the FP32 CSR engine (the FP32 tolerances of this file) and an
+    oracle chain with the same seed."""
     from oracle.sampler import Sampler as OracleSampler
+    kw.setdefault("engine", P.ENGINE_CSR_FP32)
     g = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, alpha, beta, kmax=kmax, seed=seed, **kw)
     o = OracleSampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, alpha, beta, seed=seed, kmax=kmax)
     return g, o
@@ -360,7 +363,8 @@ def test_assign_parity_across_kernel_variants(P, tiny, K):
     o = OracleSampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, seed=17,
                       kmax=128)
     o.set_state(labels, sub, K, t=5, m=2)
-    g = P.Sampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, kmax=128, seed=17)
+    g = P.Sampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, kmax=128, seed=17,
+                  engine=P.ENGINE_CSR_FP32)
     P.dpmm_set_state(g.ctx, o.labels, o.sub, o.K, o.t, o.m, o.sumlogq)
     P.dpmm_draw_params(g.ctx)
     logpi32, logtheta32 = P.dpmm_get_params(g.ctx, K, tiny.D)

@@ -1,0 +1,146 @@
+"""Tensor-core engine: the tcgen05 self-test against numpy, then the dense-tile
+label engine against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1812_10048_gb300 import build
+    build.build()
+    import paper_1812_10048_gb300 as P
+    return P
+
+
+def to_bf16_bits(x):
+    """Round-toward-zero float32 -> bf16 bit patterns, and their exact values."""
+    b = (np.ascontiguousarray(x, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    v = (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return b, v
+
+
+@pytest.mark.parametrize("Kd,N", [(64, 16), (64, 64), (128, 96), (192, 128), (256, 256)])
+def test_tcgen05_gemm_matches_numpy(P, Kd, N):
+    rng = np.random.default_rng(Kd + N)
+    A, Av = to_bf16_bits(rng.integers(0, 256, size=(128, Kd)).astype(np.float32))
+    B, Bv = to_bf16_bits(rng.standard_normal((N, Kd)).astype(np.float32) * 3)
+    C = P.dpmm_debug_tc_gemm(A, B)
+    ref = Av @ Bv.T
+    np.testing.assert_allclose(C, ref, rtol=2e-6, atol=1e-3 * np.abs(ref).max() * 1e-3 + 1e-4)
+
+
+# ---------------------------------------------------------------------------
+# dense-tile label engine
+# ---------------------------------------------------------------------------
+TWO_M16 = 2.0 ** -16
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    from paper_1812_10048_gb300 import synth
+    return synth.tiny()
+
+
+def injected(P, ds, K, seed, engine=None, kmax=128):
+    """GPU chain (dense-tile engine) and oracle chain in the same random state with
+    K clusters, with parameters drawn on the GPU and injected back (FP32)."""
+    from oracle.sampler import Sampler as OracleSampler
+    rng = np.random.default_rng(seed)
+    labels = rng.integers(0, K, size=ds.N)
+    labels[:K] = np.arange(K)
+    sub = rng.integers(0, 2, size=ds.N)
+    o = OracleSampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, seed=seed, kmax=kmax)
+    o.set_state(labels, sub, K, t=3, m=1)
+    g = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, kmax=kmax, seed=seed,
+                  engine=P.ENGINE_TILE_BF16 if engine is None else engine)
+    P.dpmm_set_state(g.ctx, o.labels, o.sub, o.K, o.t, o.m, o.sumlogq)
+    P.dpmm_draw_params(g.ctx)
+    logpi, logtheta = P.dpmm_get_params(g.ctx, K, ds.D)
+    P.dpmm_set_params(g.ctx, logpi, logtheta)
+    return g, o, logpi.astype(np.float64), logtheta.astype(np.float64)
+
+
+def centred_reference(o, logtheta):
+    """FP64 centred scores and the BF16 hi/lo error bound of each (cell, column)."""
+    X = o.X.astype(np.float64)
+    m = logtheta.mean(axis=0)
+    d = logtheta - m[None, :]
+    K = logtheta.shape[0] // 3
+    order = np.concatenate([np.arange(0, 3 * K, 3),
+                            np.stack([np.arange(1, 3 * K, 3), np.arange(2, 3 * K, 3)], 1).ravel()])
+    dd = d[order]
+    ref = np.asarray(X @ dd.T)
+    bound = 2 * TWO_M16 * np.asarray(X @ np.abs(dd).T) + 1e-5 * np.abs(ref) + 1e-3
+    return ref, bound
+
+
+@pytest.mark.parametrize("K", [1, 2, 5, 10, 16, 23, 40])
+def test_tile_scores_within_bf16_bound(P, tiny, K):
+    g, o, logpi, logtheta = injected(P, tiny, K, seed=100 + K)
+    got = P.dpmm_debug_tile_scores(g.ctx, tiny.N, K)
+    ref, bound = centred_reference(o, logtheta)
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), (err.max(), (err / bound).max())
+
+
+@pytest.mark.parametrize("K", [2, 7, 10, 40])
+def test_tile_assign_matches_oracle_except_near_ties(P, tiny, K):
+    from oracle.sampler import sufficient_stats, label_gumbels
+    g, o, logpi, logtheta = injected(P, tiny, K, seed=200 + K)
+    ref, bound = centred_reference(o, logtheta)
+    v = ref[:, :K] + logpi[None, :K] + label_gumbels(o.N, K, o.seed, o.chain_id, o.t)
+    srt = np.sort(v, axis=1)
+    gap = srt[:, -1] - srt[:, -2] if K > 1 else np.full(o.N, np.inf)
+    near = gap < 2 * bound[:, :K].max(axis=1)
+    o.assign_and_update(logpi, logtheta)
+    P.dpmm_assign(g.ctx)
+    lab, sb, Kg, t, m = g.get_state()
+    assert t == o.t
+    if Kg == o.K:
+        mism = lab != o.labels
+        assert np.all(near[mism]), f"{mism.sum()} mismatches, {near.sum()} near-ties"
+        assert np.mean(sb[~mism] == o.sub[~mism]) > 0.995
+    nsub, Ssub, _ = g.stats()
+    on, oS = sufficient_stats(o.X, lab, sb, Kg)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+
+
+def test_tile_chain_invariants_and_recovery(P, tiny):
+    from oracle.ari import adjusted_rand_index
+    from oracle.sampler import csr_matrix, sufficient_stats
+    g = P.Sampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, seed=3,
+                  engine=P.ENGINE_TILE_BF16)
+    g.step(40)
+    labels, sub, K, t, m = g.get_state()
+    nsub, Ssub, _ = g.stats()
+    on, oS = sufficient_stats(csr_matrix(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D),
+                              labels, sub, K)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    assert adjusted_rand_index(labels, tiny.labels) > 0.95
+
+
+def test_tile_engine_small_shapes(P):
+    """One partial tile (N < 128), one partial chunk (D < 64), counts above 255."""
+    from oracle.sampler import csr_matrix, sufficient_stats
+    rng = np.random.default_rng(5)
+    N, D = 77, 23
+    dense = rng.integers(0, 6, size=(N, D)) * (rng.random((N, D)) < 0.5)
+    dense[5, 3] = 1000
+    dense[9] = 0
+    r, c = np.nonzero(dense)
+    indptr = np.concatenate([[0], np.cumsum(np.count_nonzero(dense, axis=1))]).astype(np.int32)
+    g = P.Sampler(indptr, c.astype(np.int32), dense[r, c].astype(np.int32), N, D, 1.0, 0.5, seed=4,
+                  engine=P.ENGINE_TILE_BF16)
+    g.step(8)
+    labels, sub, K, _, _ = g.get_state()
+    nsub, Ssub, _ = g.stats()
+    on, oS = sufficient_stats(csr_matrix(indptr, c, dense[r, c], N, D), labels, sub, K)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
