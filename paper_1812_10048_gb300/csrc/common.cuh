@@ -7,7 +7,7 @@
 
 #include <string>
 
-#include "../../include/dpmm.h"
+#include "dpmm.h"
 
 namespace dpmm {
 

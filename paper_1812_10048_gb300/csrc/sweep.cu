@@ -593,7 +593,8 @@ k_stats(Csr csr, const DevScalars* __restrict__ sc_ro, DevScalars* sc_rw,
         uint32_t* __restrict__ nsub, uint32_t* __restrict__ Ssub, uint32_t* bump, int64_t N,
         int32_t D, int64_t priv_cap, int only_if_reinit) {
     extern __shared__ __align__(16) uint32_t spriv[];
-    if ((only_if_reinit == 1 && !sc_ro->any_reinit) || (only_if_reinit == 2 && sc_ro->stats_fused)) {
+    if ((only_if_reinit == 1 && !sc_ro->any_reinit) ||
+        (only_if_reinit == 2 && (sc_ro->stats_fused || sc_ro->tile_used))) {
         if (bump && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1u;
         return;
     }

@@ -64,6 +64,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Barrier among `n` threads (a multiple of 32) of the CTA, id 1..15.
+__device__ __forceinline__ void named_bar(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // 1-D bulk copy global -> shared, completion counted on `bar` (bytes and
 // both addresses multiples of 16).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,

@@ -115,11 +115,9 @@ cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, i
 // counts into shared-memory statistics.
 // ===========================================================================
 
-constexpr int kTileThreads = 256;
 constexpr int kNtotMax = 256;
 constexpr int kTileMaxK = 40;
 constexpr uint32_t kBChunkBytes = kNtotMax * 128;   // one chunk of B in global memory
-constexpr size_t kTileFixedBytes = 131072 + 8192;   // operand stages + small area
 
 __host__ __device__ __forceinline__ bool tile_usable(int K) {
     return K >= 1 && K <= kTileMaxK;
@@ -198,7 +196,26 @@ struct TileArgs {
     Stream st;
 };
 
-__global__ void __launch_bounds__(kTileThreads, 1)
+// Warp roles of the pipelined engine (416 threads):
+//   warps 0-3   epilogue: one cell per thread (TMEM lanes 0-127), label and
+//               sub-label
+//   warps 4-11  producers: densify each chunk into a stage of the ring (entries
+//               prefetched two chunks ahead in registers) and start the
+//               stage's B bulk copy
+//   warp 12     lane 0 issues the MMAs (two TMEM accumulators, 2 x 256 columns)
+// Stage hand-offs use mbarriers: a_full (producers -> MMA), b_full (bulk copy
+// -> MMA), stage_free (MMA commit -> producers), acc_full (MMA commit ->
+// epilogue), acc_empty (epilogue -> MMA).  Every wait is bounded; a timeout
+// records DPMM_ETIMEOUT and every role leaves its loop at its next barrier.
+constexpr int kStages = 3;
+constexpr int kProdWarp0 = 4;
+constexpr int kProdThreads = 256;
+constexpr int kMmaWarp = 12;
+constexpr int kTileThreadsP = 13 * 32;
+constexpr int kBarProd = 1, kBarLabel = 2;
+constexpr int kProdRegs = 8;    // entries per producer thread and chunk held in registers
+
+__global__ void __launch_bounds__(kTileThreadsP, 1)
 k_assign_tc(TileArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -210,252 +227,371 @@ k_assign_tc(TileArgs a) {
     if (!use) return;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
     const uint32_t t = a.sc->t;
-    // stage st: A_lo at base + 16 KB st, A_hi at base + 32 KB + 16 KB st, B at base + 64 KB + 32 KB st
-    unsigned char* small = base + 131072;
-    uint64_t* mma_done = reinterpret_cast<uint64_t*>(small);   // [2]
-    uint64_t* b_full = mma_done + 2;                            // [2]
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(b_full + 2);
-    int* flags = reinterpret_cast<int*>(taddr_s + 1);          // [0..1] A_hi dirty, [2] error
-    uint32_t* rows_cs = reinterpret_cast<uint32_t*>(flags + 4);  // [128]
-    uint32_t* sn = rows_cs + 128;                                // [2K]
-    float* spi = reinterpret_cast<float*>(sn + 2 * kTileMaxK);   // [K]
-    float* slw = spi + kTileMaxK;                                // [4K]
-    float* wsq = slw + 4 * kTileMaxK;                            // [4][K]
-    unsigned char* stats_base = base + kTileFixedBytes;
-    const int64_t stats_bytes = (int64_t)2 * K * a.D * 4;
-    const bool fused = !a.dbg && (int64_t)(stats_base - smem_raw) + stats_bytes <= a.smem_bytes;
-    uint32_t* sS = fused ? reinterpret_cast<uint32_t*>(stats_base) : nullptr;
-    if (!a.dbg && blockIdx.x == 0 && tid == 0) a.sc->stats_fused = fused ? 1 : 0;
+    const uint32_t b_stage = ((uint32_t)Ntot * 128u + 1023u) & ~1023u;
+    unsigned char* A_base = base;                                    // stage s: lo, then hi
+    unsigned char* B_base = base + kStages * 32768;
+    unsigned char* small = B_base + kStages * b_stage;
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(small);           // [kStages]
+    uint64_t* b_full = a_full + kStages;                              // [kStages]
+    uint64_t* stage_free = b_full + kStages;                          // [kStages]
+    uint64_t* acc_full = stage_free + kStages;                        // [2]
+    uint64_t* acc_empty = acc_full + 2;                               // [2]
+    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    volatile int* err = reinterpret_cast<volatile int*>(taddr_s + 1);
+    int* stage_hi = const_cast<int*>(err) + 1;                        // [kStages]
+    int* dirty = stage_hi + kStages;                                  // [kStages]
+    uint32_t* rows_cs = reinterpret_cast<uint32_t*>(dirty + kStages);  // [2][128]
+    uint32_t* sn = rows_cs + 256;                                     // [2K]
+    float* spi = reinterpret_cast<float*>(sn + 2 * kTileMaxK);        // [K]
+    float* slw = spi + kTileMaxK;                                     // [4K]
+    float* wsq = slw + 4 * kTileMaxK;                                 // [4][K]
+    // role-uniform stop decisions: sampled by one thread before a role's
+    // barrier, read by every thread of the role after it
+    int* prod_stop = reinterpret_cast<int*>(wsq + 4 * kTileMaxK);
+    int* epi_stop = prod_stop + 1;
+    // the statistics of the new labels come from k_stats_tile, launched after this kernel
+    if (!a.dbg && blockIdx.x == 0 && tid == 0) a.sc->stats_fused = 0;
 
     for (int k = tid; k < K; k += blockDim.x) spi[k] = a.logpi[k];
     for (int i = tid; i < 2 * K; i += blockDim.x) {
         const float n = (float)a.nsub[i];
         slw[2 * i] = n > 0.0f ? logf(n) : -CUDART_INF_F;
         slw[2 * i + 1] = n > 1.0f ? logf(n - 1.0f) : -CUDART_INF_F;
-        sn[i] = 0u;
     }
     for (int i = tid; i < 4 * K; i += blockDim.x) wsq[i] = 0.0f;
-    // stages' hi-count operands start dirty so that their first use zeroes them
-    if (tid < 4) flags[tid] = tid < 2 ? 1 : 0;
-    if (sS)
-        for (int64_t i = tid; i < (int64_t)2 * K * a.D; i += blockDim.x) sS[i] = 0u;
+    if (tid < kStages) {
+        stage_hi[tid] = 0;
+        dirty[tid] = 1;   // hi-count operands start dirty: their first use zeroes them
+    }
     if (tid == 0) {
-        tc::mbar_init(&mma_done[0], 1);
-        tc::mbar_init(&mma_done[1], 1);
-        tc::mbar_init(&b_full[0], 1);
-        tc::mbar_init(&b_full[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *err = 0;
+        for (int i = 0; i < kStages; ++i) {
+            tc::mbar_init(&a_full[i], 1);
+            tc::mbar_init(&b_full[i], 1);
+            tc::mbar_init(&stage_free[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], 1);
+        }
+        tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(taddr_s, kNtotMax);
+        tc::tmem_alloc(taddr_s, 512);
         tc::tmem_relinquish();
     }
-    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *taddr_s;
-    const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)Ntot);
-    uint32_t uses0 = 0u, uses1 = 0u;       // issued uses per stage (mma_done / b_full phases)
-    int pend0 = -1, pend1 = -1;            // thread 0: phase parity of an unwaited bulk copy
 
-    for (int tile = blockIdx.x; tile < a.T; tile += gridDim.x) {
-        for (int c = 0; c < a.C; ++c) {
-            const int st = c & 1;
-            unsigned char* A_lo = base + 16384 * st;
-            unsigned char* A_hi = base + 32768 + 16384 * st;
-            unsigned char* Bst = base + 65536 + 32768 * st;
-            const uint32_t use_n = st ? uses1 : uses0;
-            // the MMAs that last read this stage must be done before it is rewritten
-            if (use_n > 0 && !tc::mbar_wait(&mma_done[st], (use_n - 1) & 1, kWaitLimit))
-                flags[2] = DPMM_ETIMEOUT;
-            if (tid == 0 && !flags[2]) {
-                tc::mbar_arrive_expect_tx(&b_full[st], (uint32_t)Ntot * 128u);
-                tc::bulk_g2s(Bst, a.B + (size_t)c * kBChunkBytes, (uint32_t)Ntot * 128u,
-                             &b_full[st]);
-                if (st) pend1 = (int)(use_n & 1); else pend0 = (int)(use_n & 1);
+    if (warp >= kProdWarp0 && warp < kMmaWarp) {
+        // ---------------- producers ----------------
+        const int pt = tid - kProdWarp0 * 32;
+        uint32_t g = 0;
+        // register pipeline: entries of the current chunk and the next two
+        uint32_t e0[kProdRegs], e1[kProdRegs], e2[kProdRegs];
+        // chunk g's entry range [lo, hi); bounds are loaded one iteration before the
+        // entries that need them, entries two iterations before their chunk
+        auto bounds = [&](uint32_t gg, int& lo, int& hi) {
+            const uint32_t ti = gg / (uint32_t)a.C, ci = gg - ti * (uint32_t)a.C;
+            const int tile = (int)blockIdx.x + (int)ti * (int)gridDim.x;
+            lo = hi = 0;
+            if (tile < a.T) {
+                lo = __ldg(a.ptr + tile * a.C + ci);
+                hi = __ldg(a.ptr + tile * a.C + ci + 1);
             }
-            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-            for (int i = tid; i < 1024; i += blockDim.x) reinterpret_cast<uint4*>(A_lo)[i] = z;
-            if (flags[st])
-                for (int i = tid; i < 1024; i += blockDim.x) reinterpret_cast<uint4*>(A_hi)[i] = z;
-            __syncthreads();
-            const int p0 = a.ptr[tile * a.C + c], p1 = a.ptr[tile * a.C + c + 1];
-            int hi = 0;
-            for (int e = p0 + tid; e < p1; e += blockDim.x) {
-                const uint32_t v = __ldg(a.ent + e);
-                const uint32_t r = v >> 22, g = (v >> 16) & 63u, x = v & 0xFFFFu;
-                const uint32_t off = tc::swz_offset(r, g);
-                *reinterpret_cast<uint16_t*>(A_lo + off) = bf16_bits_rn((float)(x & 255u));
-                if (x >> 8) {
-                    *reinterpret_cast<uint16_t*>(A_hi + off) =
-                        bf16_bits_rn((float)((x >> 8) << 8));
-                    hi = 1;
+        };
+        auto fetch = [&](uint32_t (&dst)[kProdRegs], int lo, int hi) {
+#pragma unroll
+            for (int j = 0; j < kProdRegs; ++j) {
+                const int e = lo + pt + kProdThreads * j;
+                dst[j] = e < hi ? __ldg(a.ent + e) : 0xFFFFFFFFu;
+            }
+        };
+        int b1l, b1h, b2l, b2h, bnl, bnh;   // bounds of chunks g + 1, g + 2 and g + 3
+        bounds(0, b1l, b1h);
+        bounds(1, b2l, b2h);
+        fetch(e1, b1l, b1h);
+        fetch(e2, b2l, b2h);
+        bounds(2, bnl, bnh);
+        for (int tile = blockIdx.x; tile < a.T; tile += gridDim.x) {
+            bool stop = false;
+            for (int c = 0; c < a.C; ++c, ++g) {
+                const int st = (int)(g % kStages);
+                const uint32_t n = g / kStages;
+                unsigned char* A_lo = A_base + st * 32768;
+                unsigned char* A_hi = A_lo + 16384;
+                const int p0 = b1l, p1 = b1h;
+#pragma unroll
+                for (int j = 0; j < kProdRegs; ++j) {
+                    e0[j] = e1[j];
+                    e1[j] = e2[j];
+                }
+                b1l = b2l;
+                b1h = b2h;
+                b2l = bnl;
+                b2h = bnh;
+                fetch(e2, b2l, b2h);
+                bounds(g + 3, bnl, bnh);
+                if (g >= kStages && !tc::mbar_wait(&stage_free[st], (n - 1) & 1, kWaitLimit))
+                    *err = DPMM_ETIMEOUT;
+                if (pt == 0 && !*err) {
+                    stage_hi[st] = 0;
+                    tc::mbar_arrive_expect_tx(&b_full[st], (uint32_t)Ntot * 128u);
+                    tc::bulk_g2s(B_base + st * b_stage, a.B + (size_t)c * kBChunkBytes,
+                                 (uint32_t)Ntot * 128u, &b_full[st]);
+                }
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) reinterpret_cast<uint4*>(A_lo)[pt + kProdThreads * i] = z;
+                if (dirty[st]) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) reinterpret_cast<uint4*>(A_hi)[pt + kProdThreads * i] = z;
+                }
+                tc::named_bar(kBarProd, kProdThreads);
+                int hi = 0;
+                auto put = [&](uint32_t v) {
+                    const uint32_t r = v >> 22, gg = (v >> 16) & 63u, x = v & 0xFFFFu;
+                    const uint32_t off = tc::swz_offset(r, gg);
+                    *reinterpret_cast<uint16_t*>(A_lo + off) = bf16_bits_rn((float)(x & 255u));
+                    if (x >> 8) {
+                        *reinterpret_cast<uint16_t*>(A_hi + off) =
+                            bf16_bits_rn((float)((x >> 8) << 8));
+                        hi = 1;
+                    }
+                };
+#pragma unroll
+                for (int j = 0; j < kProdRegs; ++j)
+                    if (e0[j] != 0xFFFFFFFFu) put(e0[j]);
+                for (int e = p0 + pt + kProdThreads * kProdRegs; e < p1; e += kProdThreads)
+                    put(__ldg(a.ent + e));
+                if (hi) atomicOr(&stage_hi[st], 1);
+                tc::fence_async_smem();
+                if (pt == 0) *prod_stop = *err;
+                tc::named_bar(kBarProd, kProdThreads);
+                const bool halt = *prod_stop != 0;
+                if (pt == 0) {
+                    dirty[st] = stage_hi[st];
+                    if (!halt) tc::mbar_arrive(&a_full[st]);
+                }
+                if (halt) {
+                    stop = true;
+                    break;
                 }
             }
-            const int any_hi = __syncthreads_or(hi);
-            if (tid == 0) flags[st] = any_hi;
-            tc::fence_async_smem();
-            __syncthreads();
-            if (flags[2]) break;
-            if (tid == 0) {
-                const bool got = tc::mbar_wait(&b_full[st], use_n & 1, kWaitLimit);
-                if (got) {
-                    if (st) pend1 = -1; else pend0 = -1;
+            if (stop) break;
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issue ----------------
+        if ((tid & 31) == 0) {
+            uint32_t g = 0, it = 0;
+            const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)Ntot);
+            for (int tile = blockIdx.x; tile < a.T && !*err; tile += gridDim.x, ++it) {
+                const uint32_t buf = it & 1;
+                if (it >= 2 && !tc::mbar_wait(&acc_empty[buf], ((it >> 1) - 1) & 1, kWaitLimit)) {
+                    *err = DPMM_ETIMEOUT;
+                    break;
                 }
-                if (!got) {
-                    flags[2] = DPMM_ETIMEOUT;
-                } else {
+                tc::fence_after_sync();
+                const uint32_t acc = tmem + buf * 256u;
+                for (int c = 0; c < a.C; ++c, ++g) {
+                    const int st = (int)(g % kStages);
+                    const uint32_t n = g / kStages;
+                    if (!tc::mbar_wait(&a_full[st], n & 1, kWaitLimit) ||
+                        !tc::mbar_wait(&b_full[st], n & 1, kWaitLimit)) {
+                        *err = DPMM_ETIMEOUT;
+                        break;
+                    }
                     tc::fence_after_sync();
+                    const uint32_t alo = tc::smem_addr(A_base + st * 32768);
+                    const uint32_t bsm = tc::smem_addr(B_base + st * b_stage);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        tc::mma_bf16(tmem, tc::desc_sw128(tc::smem_addr(A_lo) + 32 * k),
-                                     tc::desc_sw128(tc::smem_addr(Bst) + 32 * k), idesc,
-                                     (c | k) != 0);
-                    if (any_hi) {
+                        tc::mma_bf16(acc, tc::desc_sw128(alo + 32 * k), tc::desc_sw128(bsm + 32 * k),
+                                     idesc, (c | k) != 0);
+                    if (stage_hi[st]) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            tc::mma_bf16(tmem, tc::desc_sw128(tc::smem_addr(A_hi) + 32 * k),
-                                         tc::desc_sw128(tc::smem_addr(Bst) + 32 * k), idesc,
-                                         1u);
+                            tc::mma_bf16(acc, tc::desc_sw128(alo + 16384 + 32 * k),
+                                         tc::desc_sw128(bsm + 32 * k), idesc, 1u);
                     }
-                    tc::mma_commit(&mma_done[st]);
+                    tc::mma_commit(&stage_free[st]);
                 }
+                if (*err) break;
+                tc::mma_commit(&acc_full[buf]);
             }
-            if (st) ++uses1; else ++uses0;
         }
-        __syncthreads();
-        if (flags[2]) break;
-        // every MMA of the tile has completed once the last chunk's commit has arrived
-        const int lst = (a.C - 1) & 1;
-        const uint32_t lst_n = lst ? uses1 : uses0;
-        if (!tc::mbar_wait(&mma_done[lst], (lst_n - 1) & 1, kWaitLimit)) flags[2] = DPMM_ETIMEOUT;
-        tc::fence_after_sync();
-        if (warp < 4) {
-            const int r = tid;
-            const int64_t cell = (int64_t)tile * 128 + r;
-            const bool live = cell < a.N && !flags[2];
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-            // cluster scores, 8 per 16-column group, with their Gumbel noise
-            float best = -CUDART_INF_F;
-            int c = 0;
-            for (int q = 0; q < S0 / 16; ++q) {
-                float v[16];
-                tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
-                tc::tmem_ld_wait();
-                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        // ---------------- epilogue and statistics (warps 0-3) ----------------
+        uint32_t it = 0;
+        for (int tile = blockIdx.x; tile < a.T; tile += gridDim.x, ++it) {
+            const uint32_t buf = it & 1;
+            uint32_t* rcs = rows_cs + 128 * buf;
+            {
+                if (!tc::mbar_wait(&acc_full[buf], (it >> 1) & 1, kWaitLimit)) *err = DPMM_ETIMEOUT;
+                tc::fence_after_sync();
+                const int r = tid;
+                const int64_t cell = (int64_t)tile * 128 + r;
+                const bool live = cell < a.N && !*err;
+                const uint32_t trow = tmem + buf * 256u + ((uint32_t)(warp * 32) << 16);
+                float best = -CUDART_INF_F;
+                int c = 0;
+                for (int q = 0; q < S0 / 16; ++q) {
+                    float v[16];
+                    tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
+                    tc::tmem_ld_wait();
+                    uint4 w = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int k = 8 * q + i;
-                    if ((i & 3) == 0 && k < K)
-                        w = a.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
-                    if (k < K) {
-                        const float sc = v[2 * i] + v[2 * i + 1];
-                        if (a.dbg && live) a.dbg[(size_t)cell * 3 * K + k] = sc;
-                        const float val = (spi[k] + sc) + gumbel(word_of(w, i & 3));
-                        if (val > best) {
-                            best = val;
-                            c = k;
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = 8 * q + i;
+                        if ((i & 3) == 0 && k < K)
+                            w = a.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
+                        if (k < K) {
+                            const float sc = v[2 * i] + v[2 * i + 1];
+                            if (a.dbg && live) a.dbg[(size_t)cell * 3 * K + k] = sc;
+                            const float val = (spi[k] + sc) + gumbel(word_of(w, i & 3));
+                            if (val > best) {
+                                best = val;
+                                c = k;
+                            }
                         }
                     }
                 }
-            }
-            // sub-cluster scores of cluster c (columns S0 + 4c .. S0 + 4c + 3)
-            float t0 = 0.0f, t1 = 0.0f;
-            const int s0 = S0 + 4 * c;
-            for (int q = S0 / 16; q < Ntot / 16; ++q) {
-                float v[16];
-                tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
-                tc::tmem_ld_wait();
-                if (a.dbg && live) {
+                float t0 = 0.0f, t1 = 0.0f;
+                const int s0 = S0 + 4 * c;
+                for (int q = S0 / 16; q < Ntot / 16; ++q) {
+                    float v[16];
+                    tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
+                    tc::tmem_ld_wait();
+                    if (a.dbg && live) {
 #pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const int col = 16 * q + i - S0;   // 4k + 2r
-                        if (col < 4 * K)
-                            a.dbg[(size_t)cell * 3 * K + K + (col >> 1)] = v[i] + v[i + 1];
+                        for (int i = 0; i < 16; i += 2) {
+                            const int col = 16 * q + i - S0;
+                            if (col < 4 * K)
+                                a.dbg[(size_t)cell * 3 * K + K + (col >> 1)] = v[i] + v[i + 1];
+                        }
+                    }
+                    if ((s0 >> 4) == q) {
+                        const int o = s0 & 15;
+                        if (o == 0) { t0 = v[0] + v[1]; t1 = v[2] + v[3]; }
+                        else if (o == 4) { t0 = v[4] + v[5]; t1 = v[6] + v[7]; }
+                        else if (o == 8) { t0 = v[8] + v[9]; t1 = v[10] + v[11]; }
+                        else { t0 = v[12] + v[13]; t1 = v[14] + v[15]; }
                     }
                 }
-                if ((s0 >> 4) == q) {
-                    const int o = s0 & 15;
-                    if (o == 0) { t0 = v[0] + v[1]; t1 = v[2] + v[3]; }
-                    else if (o == 4) { t0 = v[4] + v[5]; t1 = v[6] + v[7]; }
-                    else if (o == 8) { t0 = v[8] + v[9]; t1 = v[10] + v[11]; }
-                    else { t0 = v[12] + v[13]; t1 = v[14] + v[15]; }
+                tc::fence_before_sync();
+                uint32_t cs = 0xFFFFFFFFu;
+                if (live && !a.dbg) {
+                    const uint32_t old = a.state[cell];
+                    const bool stays = state_label(old) == (uint32_t)c;
+                    const uint32_t so = state_sub(old);
+                    const float lw0 = slw[4 * c + (stays && so == 0 ? 1 : 0)];
+                    const float lw1 = slw[4 * c + 2 + (stays && so == 1 ? 1 : 0)];
+                    const bool both_empty = lw0 == -CUDART_INF_F && lw1 == -CUDART_INF_F;
+                    const float l0 = (both_empty ? 0.0f : lw0) + t0;
+                    const float l1 = (both_empty ? 0.0f : lw1) + t1;
+                    const uint4 hw = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+                    const uint32_t s = (l1 + gumbel(hw.y) > l0 + gumbel(hw.x)) ? 1u : 0u;
+                    const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
+                    const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
+                    a.state[cell] = pack_state((uint32_t)c, s);
+                    atomicAdd(&wsq[warp * K + c], logq);
+                    cs = pack_state((uint32_t)c, s);
                 }
+                rcs[r] = cs;
+                if (tid == 0) *epi_stop = *err;
+                tc::named_bar(kBarLabel, 128);
+                if (tid == 0 && !*epi_stop) tc::mbar_arrive(&acc_empty[buf]);
             }
-            uint32_t cs = 0xFFFFFFFFu;
-            if (live && !a.dbg) {
-                const uint32_t old = a.state[cell];
-                const bool stays = state_label(old) == (uint32_t)c;
-                const uint32_t so = state_sub(old);
-                const float lw0 = slw[4 * c + (stays && so == 0 ? 1 : 0)];
-                const float lw1 = slw[4 * c + 2 + (stays && so == 1 ? 1 : 0)];
-                const bool both_empty = lw0 == -CUDART_INF_F && lw1 == -CUDART_INF_F;
-                const float l0 = (both_empty ? 0.0f : lw0) + t0;
-                const float l1 = (both_empty ? 0.0f : lw1) + t1;
-                const uint4 hw = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
-                const uint32_t s = (l1 + gumbel(hw.y) > l0 + gumbel(hw.x)) ? 1u : 0u;
-                const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
-                const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
-                a.state[cell] = pack_state((uint32_t)c, s);
-                atomicAdd(&wsq[warp * K + c], logq);
-                atomicAdd(&sn[2 * c + s], 1u);
-                cs = pack_state((uint32_t)c, s);
-            }
-            rows_cs[r] = cs;
+            if (*epi_stop) break;
         }
-        tc::fence_before_sync();
-        __syncthreads();
-        if (sS) {
-            // the tile's counts into the statistics of each cell's (cluster, sub-cluster)
-            for (int cc = 0; cc < a.C; ++cc) {
-                const int p0 = a.ptr[tile * a.C + cc], p1 = a.ptr[tile * a.C + cc + 1];
-                for (int e = p0 + tid; e < p1; e += blockDim.x) {
-                    const uint32_t v = __ldg(a.ent + e);
-                    const uint32_t cs = rows_cs[v >> 22];
-                    if (cs == 0xFFFFFFFFu) continue;
-                    const uint32_t k = state_label(cs), s = state_sub(cs);
-                    atomicAdd(&sS[(size_t)(2 * k + s) * a.D + cc * 64 + ((v >> 16) & 63u)],
-                              v & 0xFFFFu);
-                }
-            }
-        }
-        __syncthreads();
     }
-    // drain (bounded) anything still in flight before tensor and shared memory are released
-    if (uses0 > 0) tc::mbar_wait(&mma_done[0], (uses0 - 1) & 1, kWaitLimit);
-    if (uses1 > 0) tc::mbar_wait(&mma_done[1], (uses1 - 1) & 1, kWaitLimit);
-    if (tid == 0 && pend0 >= 0) tc::mbar_wait(&b_full[0], (uint32_t)pend0, kWaitLimit);
-    if (tid == 0 && pend1 >= 0) tc::mbar_wait(&b_full[1], (uint32_t)pend1, kWaitLimit);
-    tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
-        tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, kNtotMax);
-    }
-    if (flags[2]) {
-        if (tid == 0) atomicExch(&a.sc->error, flags[2]);
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (*err) {
+        if (tid == 0) atomicExch(&a.sc->error, *err);
         return;
     }
     if (a.dbg) return;
-    if (sS) {
-        for (int64_t i = tid; i < (int64_t)2 * K * a.D; i += blockDim.x) {
-            const uint32_t v = sS[i];
-            if (v) atomicAdd(&a.acc_Ssub[i], v);
-        }
-        for (int i = tid; i < 2 * K; i += blockDim.x)
-            if (sn[i]) atomicAdd(&a.acc_nsub[i], sn[i]);
-    }
     for (int k = tid; k < K; k += blockDim.x) {
         const double v = (double)wsq[k] + wsq[K + k] + wsq[2 * K + k] + wsq[3 * K + k];
         if (v != 0.0) atomicAdd(&a.acc_sumlogq[k], v);
     }
 }
 
+// Statistics n-bar[k][r], S-bar[k][r][u] of the labels the dense-tile engine
+// just drew, read from the blocked entries: one warp per (tile, chunk)
+// segment with the tile's 128 cell states cached in shared memory; counters
+// private to the block in shared memory when 2 K D words fit, else global
+// atomics.  Integer sums, exact.
+constexpr int kStatsTileThreads = 1024;
+
+__global__ void __launch_bounds__(kStatsTileThreads, 1)
+k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
+             const uint32_t* __restrict__ ent, const int32_t* __restrict__ ptr, int32_t T,
+             int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ nsub,
+             uint32_t* __restrict__ Ssub, int64_t smem_words) {
+    extern __shared__ __align__(16) uint32_t sm_words[];
+    if (!sc->tile_used) return;
+    const int K = sc->K;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t* cache = sm_words;                          // [nw][128]
+    uint32_t* priv = sm_words + nw * 128;                // [2K][D] + [2K]
+    const int64_t words = (int64_t)2 * K * D;
+    const bool use_priv = nw * 128 + words + 2 * K <= smem_words;
+    uint32_t* S = use_priv ? priv : Ssub;
+    uint32_t* n = use_priv ? priv + words : nsub;
+    if (use_priv)
+        for (int64_t i = threadIdx.x; i < words + 2 * K; i += blockDim.x) priv[i] = 0u;
+    __syncthreads();
+    uint32_t* my = cache + w * 128;
+    const int segs = T * C;
+    for (int seg = blockIdx.x * nw + w; seg < segs; seg += gridDim.x * nw) {
+        const int tile = seg / C, c = seg - tile * C;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t cell = (int64_t)tile * 128 + lane + 32 * j;
+            const uint32_t st = cell < N ? state[cell] : 0xFFFFFFFFu;
+            my[lane + 32 * j] = st;
+            if (c == 0 && st != 0xFFFFFFFFu) atomicAdd(&n[2 * state_label(st) + state_sub(st)], 1u);
+        }
+        __syncwarp();
+        const int p0 = ptr[seg], p1 = ptr[seg + 1];
+        const int gene0 = c * 64;
+        for (int e = p0 + lane; e < p1; e += 128) {
+            uint32_t v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = e + 32 * j < p1 ? __ldg(ent + e + 32 * j) : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t x = v[j] & 0xFFFFu;
+                if (!x) continue;
+                const uint32_t st = my[v[j] >> 22];
+                atomicAdd(&S[(size_t)(2 * state_label(st) + state_sub(st)) * D + gene0 +
+                             ((v[j] >> 16) & 63u)],
+                          x);
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (use_priv) {
+        for (int64_t i = threadIdx.x; i < words; i += blockDim.x)
+            if (priv[i]) atomicAdd(&Ssub[i], priv[i]);
+        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
+            if (priv[words + i]) atomicAdd(&nsub[i], priv[words + i]);
+    }
+}
+
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
 
 cudaError_t configure_tile(Ctx& c) {
-    return cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)c.smem_optin);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_stats_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)c.smem_optin);
 }
 
@@ -480,7 +616,11 @@ cudaError_t launch_tile_assign(Ctx& c, float* dbg) {
     a.smem_bytes = (int64_t)c.smem_optin;
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
     const int grid = c.tile_T < c.num_sms ? c.tile_T : c.num_sms;
-    k_assign_tc<<<grid, kTileThreads, c.smem_optin, c.stream>>>(a);
+    k_assign_tc<<<grid, kTileThreadsP, c.smem_optin, c.stream>>>(a);
+    if (!dbg)
+        k_stats_tile<<<c.num_sms, kStatsTileThreads, c.smem_optin, c.stream>>>(
+            c.sc, c.state, c.tile_ent, c.tile_ptr, c.tile_T, c.tile_C, c.N, c.D, c.acc_nsub,
+            c.acc_Ssub, (int64_t)(c.smem_optin / sizeof(uint32_t)));
     return cudaGetLastError();
 }
 
