@@ -33,7 +33,7 @@ L2_FLUSH_BYTES = 256 << 20
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
-KERNELS_PER_STEP = 18     # 10 sweep kernels (tile engine) + 8 move kernels (csrc/*.cu)
+KERNELS_PER_STEP = 17     # 10 sweep kernels (tile engine) + 7 move kernels (csrc/*.cu)
 
 
 def parse():

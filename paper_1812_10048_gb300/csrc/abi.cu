@@ -104,7 +104,7 @@ void free_ctx(Ctx& c) {
     void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
                     c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
-                    c.move_part, c.tile_ent, c.tile_ptr, c.tile_B};
+                    c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.sc_host) cudaFreeHost(c.sc_host);
@@ -285,6 +285,8 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     CKI(dalloc(&c.pair_ab, K2));
     CKI(dalloc(&c.lg_table, lg_table_entries()));
     CKI(dalloc(&c.move_part, move_partial_bytes()));
+    CKI(dalloc(&c.move_ticket, (size_t)c.kmax));
+    CKI(cudaMemsetAsync(c.move_ticket, 0, sizeof(int32_t) * c.kmax, c.stream));
 
     CKI(cudaMemcpyAsync(c.indptr, hptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice,
                         c.stream));

@@ -127,6 +127,7 @@ struct Ctx {
     int32_t* pair_ab = nullptr;   // [2 kmax]
     double* lg_table = nullptr;   // lgamma(beta + S) - lgamma(beta), S < 1024
     unsigned char* move_part = nullptr;  // per-block partial sums of the move scores
+    int32_t* move_ticket = nullptr;      // [kmax] finished chunks per proposal (reset to 0)
 
     // launch configuration
     int assign_blocks = 0;

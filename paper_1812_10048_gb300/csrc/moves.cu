@@ -1,7 +1,7 @@
 // Split/merge moves (Sections 2.3-2.4) and the move plans shared with the
 // sweep's empty-cluster removal.
 //
-//   k_move_prep / k_move_partial / k_move_final
+//   k_move_prep / k_move_partial
 //                 pick the chain (fair coin on the tag-4 stream unless the
 //                 caller fixes it) and score every proposal in FP64:
 //                 split of cluster k into its sub-clusters (eq. 7, with the
@@ -20,8 +20,8 @@ namespace dpmm {
 constexpr int kPlanThreads = kMaxKmax;
 
 constexpr int kLgTable = 1024;      // lgamma(beta + S) - lgamma(beta) tabulated for S < this
-constexpr int kPartialThreads = 64;
-constexpr int kMaxPartials = 1216;  // = 8 x 152 blocks of the partial-sum kernel
+constexpr int kPartialThreads = 128;
+constexpr int kMaxPartials = 304;   // = 2 x 152 blocks of the scoring kernel
 
 // lgamma(beta + S) - lgamma(beta), FP64.  Small S from the per-chain table;
 // large S by Stirling's series for lgamma(x), x >= 1024 (Abramowitz & Stegun
@@ -101,15 +101,91 @@ struct MovePartial {
     unsigned long long Ta, Tb;
 };
 
+// Sum the chunks of proposal e, add the count and total terms, decide (one
+// warp; lanes sum the chunk partials and evaluate the seven count/total
+// lgamma terms in parallel).
+__device__ __forceinline__ void finalize_proposal(
+    int e, int G, const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
+    const double* __restrict__ sumlogq, const int32_t* __restrict__ pair_ab,
+    const MovePartial* __restrict__ part, int32_t* __restrict__ decide, double* __restrict__ log_h,
+    int32_t D, double alpha, double beta, int32_t split_q, const Stream& st) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t m = sc->m;
+    const bool split = sc->chain_sel == 1;
+    const double Db = (double)D * beta;
+    double acc = 0.0;
+    unsigned long long Ta = 0, Tb = 0;
+    for (int g = lane; g < G; g += 32) {
+        const MovePartial p = part[e * G + g];
+        acc += p.acc;
+        Ta += p.Ta;
+        Tb += p.Tb;
+    }
+    acc = warp_sum(acc);
+    Ta = warp_sum(Ta);
+    Tb = warp_sum(Tb);
+    uint32_t na, nb;
+    int a = e;
+    if (split) {
+        na = nsub[2 * e];
+        nb = nsub[2 * e + 1];
+    } else {
+        a = pair_ab[2 * e];
+        const int b = pair_ab[2 * e + 1];
+        na = nsub[2 * a] + nsub[2 * a + 1];
+        nb = nsub[2 * b] + nsub[2 * b + 1];
+    }
+    double arg = 1.0;
+    if (lane == 0) arg = Db;
+    else if (lane == 1) arg = Db + (double)Ta;
+    else if (lane == 2) arg = Db + (double)Tb;
+    else if (lane == 3) arg = Db + (double)(Ta + Tb);
+    else if (lane == 4) arg = (double)na;
+    else if (lane == 5) arg = (double)nb;
+    else if (lane == 6) arg = (double)(na + nb);
+    const double lg = (lane < 7 && arg > 0.0) ? lgamma(arg) : 0.0;
+    const double lgDb = __shfl_sync(0xFFFFFFFFu, lg, 0);
+    const double lfa = lgDb - __shfl_sync(0xFFFFFFFFu, lg, 1);
+    const double lfb = lgDb - __shfl_sync(0xFFFFFFFFu, lg, 2);
+    const double lfab = lgDb - __shfl_sync(0xFFFFFFFFu, lg, 3);
+    const double lna = __shfl_sync(0xFFFFFFFFu, lg, 4);
+    const double lnb = __shfl_sync(0xFFFFFFFFu, lg, 5);
+    const double lnab = __shfl_sync(0xFFFFFFFFu, lg, 6);
+    if (lane != 0) return;
+    if (split) {
+        if (na < 1 || nb < 1) {
+            decide[e] = 0;
+            log_h[e] = CUDART_NAN;
+            return;
+        }
+        double lh = log(alpha) + lna + lnb - lnab + lfa + lfb - lfab + acc;
+        if (split_q) lh -= sumlogq[e];
+        const double u = (double)word_uniform(st.words(TAG_MOVE, (uint32_t)e + 1u, m, 0u).x);
+        decide[e] = log(u) < lh ? 1 : 0;
+        log_h[e] = lh;
+    } else {
+        const double lh = -log(alpha) + lnab - lna - lnb + lfab - lfa - lfb + acc +
+                          (double)(na + nb - 2) * log(0.5);
+        const double u = (double)word_uniform(st.words(TAG_MERGE, (uint32_t)a, m, 0u).x);
+        decide[e] = log(u) < lh ? 1 : 0;
+        log_h[e] = lh;
+    }
+}
+
 // Per (proposal, gene chunk): sum over the chunk of the lgamma terms of the
 // Hastings ratio and the two gene totals.  Block b serves proposal b / G,
-// chunk b % G, with G chosen so that proposals x G fills the grid.
+// chunk b % G, with G chosen so that proposals x G fills the grid.  The last
+// block to finish a proposal (a ticket counter, no waiting) completes it.
 __global__ void __launch_bounds__(kPartialThreads)
-k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ Ssub,
+k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
+               const uint32_t* __restrict__ Ssub, const double* __restrict__ sumlogq,
                const int32_t* __restrict__ pair_ab, const double* __restrict__ tab,
-               MovePartial* __restrict__ part, int32_t D, double beta) {
-    __shared__ double redd[2];
-    __shared__ unsigned long long redu[2];
+               MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
+               int32_t* __restrict__ decide, double* __restrict__ log_h, int32_t D, double alpha,
+               double beta, int32_t split_q, Stream st) {
+    __shared__ double redd[4];
+    __shared__ unsigned long long redu[4];
+    __shared__ int last;
     const int E = sc->n_entries;
     if (E <= 0) return;
     const bool split = sc->chain_sel == 1;
@@ -149,59 +225,18 @@ k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ S
     acc = block_sum_d(acc, redd);
     Ta = block_sum_u64(Ta, redu);
     Tb = block_sum_u64(Tb, redu);
-    if (threadIdx.x == 0) part[blockIdx.x] = MovePartial{acc, Ta, Tb};
-}
-
-// Sum the chunks of every proposal, add the count and total terms, decide.
-__global__ void __launch_bounds__(kMaxKmax)
-k_move_final(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
-             const double* __restrict__ sumlogq, const int32_t* __restrict__ pair_ab,
-             const MovePartial* __restrict__ part, int32_t* __restrict__ decide,
-             double* __restrict__ log_h, int32_t D, double alpha, double beta, int32_t split_q,
-             int32_t grid_partial, Stream st) {
-    const int E = sc->n_entries;
-    const int e = threadIdx.x;
-    if (e >= E) return;
-    const uint32_t m = sc->m;
-    const bool split = sc->chain_sel == 1;
-    const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
-    const int G = max(1, min(grid_partial / E, maxG));
-    double acc = 0.0;
-    unsigned long long Ta = 0, Tb = 0;
-    for (int g = 0; g < G; ++g) {
-        const MovePartial p = part[e * G + g];
-        acc += p.acc;
-        Ta += p.Ta;
-        Tb += p.Tb;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = MovePartial{acc, Ta, Tb};
+        __threadfence();
+        last = atomicAdd(&ticket[e], 1) == G - 1;
     }
-    const double Db = (double)D * beta;
-    const double lgDb = lgamma(Db);
-    const double lfa = lgDb - lgamma(Db + (double)Ta);
-    const double lfb = lgDb - lgamma(Db + (double)Tb);
-    const double lfab = lgDb - lgamma(Db + (double)(Ta + Tb));
-    if (split) {
-        const uint32_t n0 = nsub[2 * e], n1 = nsub[2 * e + 1];
-        if (n0 < 1 || n1 < 1) {
-            decide[e] = 0;
-            log_h[e] = CUDART_NAN;
-            return;
-        }
-        double lh = log(alpha) + lgamma((double)n0) + lgamma((double)n1) -
-                    lgamma((double)(n0 + n1)) + lfa + lfb - lfab + acc;
-        if (split_q) lh -= sumlogq[e];
-        const double u = (double)word_uniform(st.words(TAG_MOVE, (uint32_t)e + 1u, m, 0u).x);
-        decide[e] = log(u) < lh ? 1 : 0;
-        log_h[e] = lh;
-    } else {
-        const int a = pair_ab[2 * e], b = pair_ab[2 * e + 1];
-        const uint32_t na = nsub[2 * a] + nsub[2 * a + 1];
-        const uint32_t nb = nsub[2 * b] + nsub[2 * b + 1];
-        const double lh = -log(alpha) + lgamma((double)(na + nb)) - lgamma((double)na) -
-                          lgamma((double)nb) + lfab - lfa - lfb + acc +
-                          (double)(na + nb - 2) * log(0.5);
-        const double u = (double)word_uniform(st.words(TAG_MERGE, (uint32_t)a, m, 0u).x);
-        decide[e] = log(u) < lh ? 1 : 0;
-        log_h[e] = lh;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        finalize_proposal(e, G, sc, nsub, sumlogq, pair_ab, part, decide, log_h, D, alpha, beta,
+                          split_q, st);
+        if (threadIdx.x == 0) ticket[e] = 0;
     }
 }
 
@@ -398,14 +433,11 @@ cudaError_t launch_lg_table(Ctx& c) {
 
 cudaError_t launch_move_score(Ctx& c, int32_t mode) {
     const Stream st = make_stream(c.opts.seed, c.opts.chain_id);
-    const int grid = kMaxPartials;
     k_move_prep<<<1, kMaxKmax, 0, c.stream>>>(c.sc, c.pair_ab, mode, st);
-    k_move_partial<<<grid, kPartialThreads, 0, c.stream>>>(
-        c.sc, c.Ssub, c.pair_ab, c.lg_table, reinterpret_cast<MovePartial*>(c.move_part), c.D,
-        c.beta);
-    k_move_final<<<1, kMaxKmax, 0, c.stream>>>(
-        c.sc, c.nsub, c.sumlogq, c.pair_ab, reinterpret_cast<const MovePartial*>(c.move_part),
-        c.decide, c.log_h, c.D, c.alpha, c.beta, c.opts.split_q, grid, st);
+    k_move_partial<<<kMaxPartials, kPartialThreads, 0, c.stream>>>(
+        c.sc, c.nsub, c.Ssub, c.sumlogq, c.pair_ab, c.lg_table,
+        reinterpret_cast<MovePartial*>(c.move_part), c.move_ticket, c.decide, c.log_h, c.D,
+        c.alpha, c.beta, c.opts.split_q, st);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ namespace dpmm {
 
 constexpr int kAssignThreads = 1024;
 constexpr int kStatsThreads = 1024;
-constexpr int kDrawThreads = 256;
+constexpr int kDrawThreads = 1024;
 
 // ---------------------------------------------------------------------------
 // Parameter draws.

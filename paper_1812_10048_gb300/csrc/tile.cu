@@ -133,27 +133,36 @@ __device__ __forceinline__ float bf16_value(uint16_t b) {
     return __uint_as_float((uint32_t)b << 16);
 }
 
-// B operand of one sweep: block c fills chunk c (genes 64c .. 64c + 63).
+// B operand of one sweep: block (c, q) fills rows 16q .. 16q + 15 of chunk c
+// (genes 64c .. 64c + 63); every block of chunk c forms the same m_u.
 __global__ void __launch_bounds__(256)
 k_build_b(const DevScalars* __restrict__ sc, const float* __restrict__ Lc,
           const float* __restrict__ Ls, unsigned char* __restrict__ B, int32_t D, int32_t kmax) {
+    __shared__ float part[4][64];
     __shared__ float m[64];
     const int K = sc->K;
     if (!tile_usable(K)) return;
     const int c = blockIdx.x;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
-    if (threadIdx.x < 64) {
-        const int u = c * 64 + threadIdx.x;
+    if ((int)blockIdx.y * 16 >= Ntot) return;
+    {
+        // m_u: 4 threads per gene, each a quarter of the 3K rows, fixed order
+        const int g = threadIdx.x & 63, qq = threadIdx.x >> 6;
+        const int u = c * 64 + g;
         float s = 0.0f;
         if (u < D) {
-            for (int k = 0; k < K; ++k) s += Lc[(size_t)u * kmax + k];
-            for (int k = 0; k < 2 * K; ++k) s += Ls[(size_t)u * kmax * 2 + k];
+            for (int j = qq; j < 3 * K; j += 4)
+                s += j < K ? Lc[(size_t)u * kmax + j] : Ls[(size_t)u * kmax * 2 + (j - K)];
         }
-        m[threadIdx.x] = s / (float)(3 * K);
+        part[qq][g] = s;
+        __syncthreads();
+        if (threadIdx.x < 64)
+            m[g] = ((part[0][g] + part[1][g]) + (part[2][g] + part[3][g])) / (float)(3 * K);
+        __syncthreads();
     }
-    __syncthreads();
     unsigned char* dst = B + (size_t)c * kBChunkBytes;
-    for (int i = threadIdx.x; i < Ntot * 64; i += blockDim.x) {
+    for (int i = blockIdx.y * 1024 + threadIdx.x; i < min(Ntot, (int)blockIdx.y * 16 + 16) * 64;
+         i += blockDim.x) {
         const int row = i >> 6, g = i & 63, u = c * 64 + g;
         float L = 0.0f;
         int part = 0;
@@ -199,21 +208,21 @@ struct TileArgs {
 // Warp roles of the pipelined engine (416 threads):
 //   warps 0-3   epilogue: one cell per thread (TMEM lanes 0-127), label and
 //               sub-label
-//   warps 4-11  producers: densify each chunk into a stage of the ring (entries
-//               prefetched two chunks ahead in registers) and start the
-//               stage's B bulk copy
+//   warps 4-11  producers, two groups of 4 warps taking alternate chunks:
+//               densify a chunk into a stage of the ring (entries prefetched
+//               four chunks ahead in registers) and start the stage's B copy
 //   warp 12     lane 0 issues the MMAs (two TMEM accumulators, 2 x 256 columns)
 // Stage hand-offs use mbarriers: a_full (producers -> MMA), b_full (bulk copy
 // -> MMA), stage_free (MMA commit -> producers), acc_full (MMA commit ->
 // epilogue), acc_empty (epilogue -> MMA).  Every wait is bounded; a timeout
 // records DPMM_ETIMEOUT and every role leaves its loop at its next barrier.
-constexpr int kStages = 3;
+constexpr int kMaxStages = 4;
 constexpr int kProdWarp0 = 4;
-constexpr int kProdThreads = 256;
+constexpr int kProdGroupThreads = 128;   // two producer groups of 4 warps
 constexpr int kMmaWarp = 12;
 constexpr int kTileThreadsP = 13 * 32;
-constexpr int kBarProd = 1, kBarLabel = 2;
-constexpr int kProdRegs = 8;    // entries per producer thread and chunk held in registers
+constexpr int kBarProd0 = 1, kBarLabel = 2, kBarProd1 = 3;
+constexpr int kProdRegs = 16;   // entries per producer thread and chunk held in registers
 
 __global__ void __launch_bounds__(kTileThreadsP, 1)
 k_assign_tc(TileArgs a) {
@@ -228,27 +237,29 @@ k_assign_tc(TileArgs a) {
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
     const uint32_t t = a.sc->t;
     const uint32_t b_stage = ((uint32_t)Ntot * 128u + 1023u) & ~1023u;
+    // as many ring stages (A lo + hi, B) as shared memory holds, 2 .. 4
+    const int64_t room = a.smem_bytes - (int64_t)(base - smem_raw) - 8192;
+    const int kStages = (int)max((int64_t)2, min((int64_t)kMaxStages, room / (int64_t)(32768 + b_stage)));
     unsigned char* A_base = base;                                    // stage s: lo, then hi
     unsigned char* B_base = base + kStages * 32768;
     unsigned char* small = B_base + kStages * b_stage;
-    uint64_t* a_full = reinterpret_cast<uint64_t*>(small);           // [kStages]
-    uint64_t* b_full = a_full + kStages;                              // [kStages]
-    uint64_t* stage_free = b_full + kStages;                          // [kStages]
-    uint64_t* acc_full = stage_free + kStages;                        // [2]
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(small);           // [kMaxStages]
+    uint64_t* b_full = a_full + kMaxStages;                           // [kMaxStages]
+    uint64_t* stage_free = b_full + kMaxStages;                       // [kMaxStages]
+    uint64_t* acc_full = stage_free + kMaxStages;                     // [2]
     uint64_t* acc_empty = acc_full + 2;                               // [2]
     uint32_t* taddr_s = reinterpret_cast<uint32_t*>(acc_empty + 2);
     volatile int* err = reinterpret_cast<volatile int*>(taddr_s + 1);
-    int* stage_hi = const_cast<int*>(err) + 1;                        // [kStages]
-    int* dirty = stage_hi + kStages;                                  // [kStages]
-    uint32_t* rows_cs = reinterpret_cast<uint32_t*>(dirty + kStages);  // [2][128]
+    int* stage_hi = const_cast<int*>(err) + 1;                        // [kMaxStages]
+    uint32_t* rows_cs = reinterpret_cast<uint32_t*>(stage_hi + kMaxStages);  // [2][128]
     uint32_t* sn = rows_cs + 256;                                     // [2K]
     float* spi = reinterpret_cast<float*>(sn + 2 * kTileMaxK);        // [K]
     float* slw = spi + kTileMaxK;                                     // [4K]
     float* wsq = slw + 4 * kTileMaxK;                                 // [4][K]
     // role-uniform stop decisions: sampled by one thread before a role's
     // barrier, read by every thread of the role after it
-    int* prod_stop = reinterpret_cast<int*>(wsq + 4 * kTileMaxK);
-    int* epi_stop = prod_stop + 1;
+    int* prod_stop = reinterpret_cast<int*>(wsq + 4 * kTileMaxK);     // [2] per group
+    int* epi_stop = prod_stop + 2;
     // the statistics of the new labels come from k_stats_tile, launched after this kernel
     if (!a.dbg && blockIdx.x == 0 && tid == 0) a.sc->stats_fused = 0;
 
@@ -259,13 +270,10 @@ k_assign_tc(TileArgs a) {
         slw[2 * i + 1] = n > 1.0f ? logf(n - 1.0f) : -CUDART_INF_F;
     }
     for (int i = tid; i < 4 * K; i += blockDim.x) wsq[i] = 0.0f;
-    if (tid < kStages) {
-        stage_hi[tid] = 0;
-        dirty[tid] = 1;   // hi-count operands start dirty: their first use zeroes them
-    }
+    if (tid < kMaxStages) stage_hi[tid] = 0;
     if (tid == 0) {
         *err = 0;
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < kMaxStages; ++i) {
             tc::mbar_init(&a_full[i], 1);
             tc::mbar_init(&b_full[i], 1);
             tc::mbar_init(&stage_free[i], 1);
@@ -287,17 +295,17 @@ k_assign_tc(TileArgs a) {
 
     if (warp >= kProdWarp0 && warp < kMmaWarp) {
         // ---------------- producers ----------------
-        const int pt = tid - kProdWarp0 * 32;
-        uint32_t g = 0;
-        // register pipeline: entries of the current chunk and the next two
-        uint32_t e0[kProdRegs], e1[kProdRegs], e2[kProdRegs];
-        // chunk g's entry range [lo, hi); bounds are loaded one iteration before the
-        // entries that need them, entries two iterations before their chunk
+        const int grp = (warp - kProdWarp0) >> 2;                 // chunks g with g % 2 == grp
+        const int pt = tid - (kProdWarp0 + 4 * grp) * 32;         // 0 .. 127
+        const int bar_id = grp ? kBarProd1 : kBarProd0;
+        const uint32_t my_tiles =
+            (int)blockIdx.x < a.T ? (uint32_t)((a.T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1) : 0u;
+        const uint32_t total = my_tiles * (uint32_t)a.C;
         auto bounds = [&](uint32_t gg, int& lo, int& hi) {
-            const uint32_t ti = gg / (uint32_t)a.C, ci = gg - ti * (uint32_t)a.C;
-            const int tile = (int)blockIdx.x + (int)ti * (int)gridDim.x;
             lo = hi = 0;
-            if (tile < a.T) {
+            if (gg < total) {
+                const uint32_t ti = gg / (uint32_t)a.C, ci = gg - ti * (uint32_t)a.C;
+                const int tile = (int)blockIdx.x + (int)ti * (int)gridDim.x;
                 lo = __ldg(a.ptr + tile * a.C + ci);
                 hi = __ldg(a.ptr + tile * a.C + ci + 1);
             }
@@ -305,82 +313,77 @@ k_assign_tc(TileArgs a) {
         auto fetch = [&](uint32_t (&dst)[kProdRegs], int lo, int hi) {
 #pragma unroll
             for (int j = 0; j < kProdRegs; ++j) {
-                const int e = lo + pt + kProdThreads * j;
+                const int e = lo + pt + kProdGroupThreads * j;
                 dst[j] = e < hi ? __ldg(a.ent + e) : 0xFFFFFFFFu;
             }
         };
-        int b1l, b1h, b2l, b2h, bnl, bnh;   // bounds of chunks g + 1, g + 2 and g + 3
-        bounds(0, b1l, b1h);
-        bounds(1, b2l, b2h);
-        fetch(e1, b1l, b1h);
-        fetch(e2, b2l, b2h);
-        bounds(2, bnl, bnh);
-        for (int tile = blockIdx.x; tile < a.T; tile += gridDim.x) {
-            bool stop = false;
-            for (int c = 0; c < a.C; ++c, ++g) {
-                const int st = (int)(g % kStages);
-                const uint32_t n = g / kStages;
-                unsigned char* A_lo = A_base + st * 32768;
-                unsigned char* A_hi = A_lo + 16384;
-                const int p0 = b1l, p1 = b1h;
+        // register pipeline over this group's chunks g, g + 2, g + 4 (entries) and
+        // g + 6, g + 8 (bounds)
+        uint32_t ecur[kProdRegs], eA[kProdRegs], eB[kProdRegs];
+        int aL, aH, bL, bH, cL, cH, dL, dH;
+        bounds((uint32_t)grp, aL, aH);
+        bounds((uint32_t)grp + 2, bL, bH);
+        fetch(eA, aL, aH);
+        fetch(eB, bL, bH);
+        bounds((uint32_t)grp + 4, cL, cH);
+        bounds((uint32_t)grp + 6, dL, dH);
+        for (uint32_t g = (uint32_t)grp; g < total; g += 2) {
+            const uint32_t ti = g / (uint32_t)a.C;
+            const int c = (int)(g - ti * (uint32_t)a.C);
+            const int st = (int)(g % (uint32_t)kStages);
+            const uint32_t n = g / (uint32_t)kStages;
+            unsigned char* A_lo = A_base + st * 32768;
+            unsigned char* A_hi = A_lo + 16384;
+            const int p0 = aL, p1 = aH;
 #pragma unroll
-                for (int j = 0; j < kProdRegs; ++j) {
-                    e0[j] = e1[j];
-                    e1[j] = e2[j];
-                }
-                b1l = b2l;
-                b1h = b2h;
-                b2l = bnl;
-                b2h = bnh;
-                fetch(e2, b2l, b2h);
-                bounds(g + 3, bnl, bnh);
-                if (g >= kStages && !tc::mbar_wait(&stage_free[st], (n - 1) & 1, kWaitLimit))
-                    *err = DPMM_ETIMEOUT;
-                if (pt == 0 && !*err) {
-                    stage_hi[st] = 0;
-                    tc::mbar_arrive_expect_tx(&b_full[st], (uint32_t)Ntot * 128u);
-                    tc::bulk_g2s(B_base + st * b_stage, a.B + (size_t)c * kBChunkBytes,
-                                 (uint32_t)Ntot * 128u, &b_full[st]);
-                }
-                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) reinterpret_cast<uint4*>(A_lo)[pt + kProdThreads * i] = z;
-                if (dirty[st]) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) reinterpret_cast<uint4*>(A_hi)[pt + kProdThreads * i] = z;
-                }
-                tc::named_bar(kBarProd, kProdThreads);
-                int hi = 0;
-                auto put = [&](uint32_t v) {
-                    const uint32_t r = v >> 22, gg = (v >> 16) & 63u, x = v & 0xFFFFu;
-                    const uint32_t off = tc::swz_offset(r, gg);
-                    *reinterpret_cast<uint16_t*>(A_lo + off) = bf16_bits_rn((float)(x & 255u));
-                    if (x >> 8) {
-                        *reinterpret_cast<uint16_t*>(A_hi + off) =
-                            bf16_bits_rn((float)((x >> 8) << 8));
-                        hi = 1;
-                    }
-                };
-#pragma unroll
-                for (int j = 0; j < kProdRegs; ++j)
-                    if (e0[j] != 0xFFFFFFFFu) put(e0[j]);
-                for (int e = p0 + pt + kProdThreads * kProdRegs; e < p1; e += kProdThreads)
-                    put(__ldg(a.ent + e));
-                if (hi) atomicOr(&stage_hi[st], 1);
-                tc::fence_async_smem();
-                if (pt == 0) *prod_stop = *err;
-                tc::named_bar(kBarProd, kProdThreads);
-                const bool halt = *prod_stop != 0;
-                if (pt == 0) {
-                    dirty[st] = stage_hi[st];
-                    if (!halt) tc::mbar_arrive(&a_full[st]);
-                }
-                if (halt) {
-                    stop = true;
-                    break;
-                }
+            for (int j = 0; j < kProdRegs; ++j) {
+                ecur[j] = eA[j];
+                eA[j] = eB[j];
             }
-            if (stop) break;
+            aL = bL;
+            aH = bH;
+            bL = cL;
+            bH = cH;
+            cL = dL;
+            cH = dH;
+            fetch(eB, bL, bH);
+            bounds(g + 8, dL, dH);
+            if (g >= (uint32_t)kStages &&
+                !tc::mbar_wait(&stage_free[st], (n - 1) & 1, kWaitLimit))
+                *err = DPMM_ETIMEOUT;
+            if (pt == 0 && !*err) {
+                stage_hi[st] = 0;
+                tc::mbar_arrive_expect_tx(&b_full[st], (uint32_t)Ntot * 128u);
+                tc::bulk_g2s(B_base + st * b_stage, a.B + (size_t)c * kBChunkBytes,
+                             (uint32_t)Ntot * 128u, &b_full[st]);
+            }
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int i = 0; i < 16; ++i)   // A lo and A hi: 32 KB
+                reinterpret_cast<uint4*>(A_lo)[pt + kProdGroupThreads * i] = z;
+            tc::named_bar(bar_id, kProdGroupThreads);
+            int hi = 0;
+            auto put = [&](uint32_t v) {
+                const uint32_t r = v >> 22, gg = (v >> 16) & 63u, x = v & 0xFFFFu;
+                const uint32_t off = tc::swz_offset(r, gg);
+                *reinterpret_cast<uint16_t*>(A_lo + off) = bf16_bits_rn((float)(x & 255u));
+                if (x >> 8) {
+                    *reinterpret_cast<uint16_t*>(A_hi + off) = bf16_bits_rn((float)((x >> 8) << 8));
+                    hi = 1;
+                }
+            };
+#pragma unroll
+            for (int j = 0; j < kProdRegs; ++j)
+                if (ecur[j] != 0xFFFFFFFFu) put(ecur[j]);
+            for (int e = p0 + pt + kProdGroupThreads * kProdRegs; e < p1; e += kProdGroupThreads)
+                put(__ldg(a.ent + e));
+            if (hi) atomicOr(&stage_hi[st], 1);
+            tc::fence_async_smem();
+            if (pt == 0) prod_stop[grp] = *err;
+            tc::named_bar(bar_id, kProdGroupThreads);
+            const bool halt = prod_stop[grp] != 0;
+            if (pt == 0 && !halt) tc::mbar_arrive(&a_full[st]);
+            if (halt) break;
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issue ----------------
@@ -526,77 +529,77 @@ k_assign_tc(TileArgs a) {
 // segment with the tile's 128 cell states cached in shared memory; counters
 // private to the block in shared memory when 2 K D words fit, else global
 // atomics.  Integer sums, exact.
-constexpr int kStatsTileThreads = 1024;
+// Statistics n-bar[k][r], S-bar[k][r][u] of the labels the dense-tile engine
+// just drew, read from the blocked entries.  Blocks are partitioned by gene
+// chunk: block b takes chunk b % C of every tile t = b / C, b / C + nt, ...
+// (nt tile groups), so its private counters cover only 64 genes ([2K][64]
+// words in shared memory) and its flush adds at most 2K x 64 words.  One warp
+// per (tile, chunk) segment at a time, with the tile's 128 cell states
+// cached in shared memory.  Integer sums, exact.
+constexpr int kStatsTileThreads = 512;
 
-__global__ void __launch_bounds__(kStatsTileThreads, 1)
+__global__ void __launch_bounds__(kStatsTileThreads)
 k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
              const uint32_t* __restrict__ ent, const int32_t* __restrict__ ptr, int32_t T,
              int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ nsub,
-             uint32_t* __restrict__ Ssub, int64_t smem_words) {
-    extern __shared__ __align__(16) uint32_t sm_words[];
+             uint32_t* __restrict__ Ssub) {
+    __shared__ uint32_t cache[kStatsTileThreads / 32][128];
+    __shared__ uint32_t priv[2 * kTileMaxK * 64];
+    __shared__ uint32_t pn[2 * kTileMaxK];
     if (!sc->tile_used) return;
     const int K = sc->K;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t* cache = sm_words;                          // [nw][128]
-    uint32_t* priv = sm_words + nw * 128;                // [2K][D] + [2K]
-    const int64_t words = (int64_t)2 * K * D;
-    const bool use_priv = nw * 128 + words + 2 * K <= smem_words;
-    uint32_t* S = use_priv ? priv : Ssub;
-    uint32_t* n = use_priv ? priv + words : nsub;
-    if (use_priv)
-        for (int64_t i = threadIdx.x; i < words + 2 * K; i += blockDim.x) priv[i] = 0u;
+    const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
+    if (tg >= nt) return;
+    for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) priv[i] = 0u;
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) pn[i] = 0u;
     __syncthreads();
-    uint32_t* my = cache + w * 128;
-    const int segs = T * C;
-    for (int seg = blockIdx.x * nw + w; seg < segs; seg += gridDim.x * nw) {
-        const int tile = seg / C, c = seg - tile * C;
+    uint32_t* my = cache[w];
+    const int gene0 = c * 64;
+    for (int tile = tg + nt * w; tile < T; tile += nt * nw) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t cell = (int64_t)tile * 128 + lane + 32 * j;
             const uint32_t st = cell < N ? state[cell] : 0xFFFFFFFFu;
             my[lane + 32 * j] = st;
-            if (c == 0 && st != 0xFFFFFFFFu) atomicAdd(&n[2 * state_label(st) + state_sub(st)], 1u);
+            if (c == 0 && st != 0xFFFFFFFFu) atomicAdd(&pn[2 * state_label(st) + state_sub(st)], 1u);
         }
         __syncwarp();
+        const int seg = tile * C + c;
         const int p0 = ptr[seg], p1 = ptr[seg + 1];
-        const int gene0 = c * 64;
-        for (int e = p0 + lane; e < p1; e += 128) {
-            uint32_t v[4];
+        for (int e = p0 + lane; e < p1; e += 32 * 16) {
+            uint32_t v[16];   // 16 independent loads in flight per lane
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = e + 32 * j < p1 ? __ldg(ent + e + 32 * j) : 0u;
+            for (int j = 0; j < 16; ++j) v[j] = e + 32 * j < p1 ? __ldg(ent + e + 32 * j) : 0u;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 16; ++j) {
                 const uint32_t x = v[j] & 0xFFFFu;
                 if (!x) continue;
                 const uint32_t st = my[v[j] >> 22];
-                atomicAdd(&S[(size_t)(2 * state_label(st) + state_sub(st)) * D + gene0 +
-                             ((v[j] >> 16) & 63u)],
-                          x);
+                atomicAdd(&priv[(2 * state_label(st) + state_sub(st)) * 64 + ((v[j] >> 16) & 63u)], x);
             }
         }
         __syncwarp();
     }
     __syncthreads();
-    if (use_priv) {
-        for (int64_t i = threadIdx.x; i < words; i += blockDim.x)
-            if (priv[i]) atomicAdd(&Ssub[i], priv[i]);
-        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
-            if (priv[words + i]) atomicAdd(&nsub[i], priv[words + i]);
+    for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) {
+        const int g = i & 63, u = gene0 + g;
+        if (priv[i] && u < D) atomicAdd(&Ssub[(size_t)(i >> 6) * D + u], priv[i]);
     }
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
+        if (pn[i]) atomicAdd(&nsub[i], pn[i]);
 }
 
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
 
 cudaError_t configure_tile(Ctx& c) {
-    cudaError_t e = cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)c.smem_optin);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_stats_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)c.smem_optin);
 }
 
 cudaError_t launch_tile_assign(Ctx& c, float* dbg) {
-    k_build_b<<<c.tile_C, 256, 0, c.stream>>>(c.sc, c.Lc, c.Ls, c.tile_B, c.D, c.kmax);
+    k_build_b<<<dim3(c.tile_C, kNtotMax / 16), 256, 0, c.stream>>>(c.sc, c.Lc, c.Ls, c.tile_B,
+                                                                     c.D, c.kmax);
     TileArgs a;
     a.ent = c.tile_ent;
     a.ptr = c.tile_ptr;
@@ -617,10 +620,12 @@ cudaError_t launch_tile_assign(Ctx& c, float* dbg) {
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
     const int grid = c.tile_T < c.num_sms ? c.tile_T : c.num_sms;
     k_assign_tc<<<grid, kTileThreadsP, c.smem_optin, c.stream>>>(a);
-    if (!dbg)
-        k_stats_tile<<<c.num_sms, kStatsTileThreads, c.smem_optin, c.stream>>>(
+    if (!dbg) {
+        const int nt = max(1, (2 * c.num_sms) / c.tile_C);   // tile groups per gene chunk
+        k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(
             c.sc, c.state, c.tile_ent, c.tile_ptr, c.tile_T, c.tile_C, c.N, c.D, c.acc_nsub,
-            c.acc_Ssub, (int64_t)(c.smem_optin / sizeof(uint32_t)));
+            c.acc_Ssub);
+    }
     return cudaGetLastError();
 }
 
