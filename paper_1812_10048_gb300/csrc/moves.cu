@@ -13,32 +13,102 @@
 //                 new n-bar / sum log q of every surviving cluster
 #include <math_constants.h>
 
+#include <cmath>
+
 #include "common.cuh"
 
 namespace dpmm {
 
 constexpr int kPlanThreads = kMaxKmax;
 
-constexpr int kLgTable = 1024;      // lgamma(beta + S) - lgamma(beta) tabulated for S < this
+constexpr int kLgTable = 65536;     // exact lgamma tables cover arguments below this
+constexpr int kLogTab = 128;        // breakpoints of the table-driven logarithm
 constexpr int kPartialThreads = 128;
+constexpr int kPartialWarps = kPartialThreads / 32;
 constexpr int kMaxPartials = 304;   // = 2 x 152 blocks of the scoring kernel
 
-// lgamma(beta + S) - lgamma(beta), FP64.  Small S from the per-chain table;
-// large S by Stirling's series for lgamma(x), x >= 1024 (Abramowitz & Stegun
-// 6.1.41, truncated after the x^-3 term: the next term is below 1e-18).
-__device__ __forceinline__ double lg_shift(uint32_t S, double beta, double lg_beta,
-                                           const double* __restrict__ tab) {
-    if (S < (uint32_t)kLgTable) return tab[S];
-    const double x = beta + (double)S;
-    const double r = 1.0 / x;
-    const double r2 = r * r;
-    const double half_log_2pi = 0.91893853320467274178;
-    return (x - 0.5) * log(x) - x + half_log_2pi + r * (1.0 / 12.0 - r2 * (1.0 / 360.0)) - lg_beta;
+// Per-chain FP64 tables (one device array; filled once by k_lg_table):
+//   shift[S] = lgamma(beta + S) - lgamma(beta)   S < 65536
+//   cnt[n]   = lgamma(n)                          1 <= n < 65536
+//   tot[T]   = lgamma(D beta + T)                 T < 65536
+//   logc[j]  = log(1 + j / 128), invc[j] = 1 / (1 + j / 128)
+// GB300 issues FP64 arithmetic at a small fraction of its FP32 rate, so the
+// split/merge scores read every lgamma they can from these tables and take
+// the rest from the short Stirling form below.
+struct LgTab {
+    const double* shift;
+    const double* cnt;
+    const double* tot;
+    const double* logc;
+    const double* invc;
+};
+__host__ __device__ inline LgTab lg_tab_view(const double* base) {
+    return LgTab{base, base + kLgTable, base + 2 * kLgTable, base + 3 * kLgTable,
+                 base + 3 * kLgTable + kLogTab};
 }
 
-__global__ void k_lg_table(double* __restrict__ tab, double beta) {
+// Natural logarithm of a positive normal double by table-driven argument
+// reduction (Tang, ACM TOMS 16(4), 1990): x = 2^e m, m in [1, 2), c = the
+// breakpoint 1 + j/128 at or below m, log x = e ln 2 + log c + log(1 + t) with
+// t = (m - c) / c in [0, 2^-7) and log(1 + t) from its Taylor series to t^7
+// (truncation below 2^-59).  ln 2 is split so that e * ln2_hi is exact.
+__device__ __forceinline__ double log_tab(double x, const LgTab& tb) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023;
+    const int j = (int)((b >> 45) & (kLogTab - 1));
+    const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const double t = (m - (1.0 + (double)j * (1.0 / kLogTab))) * __ldg(tb.invc + j);
+    double p = 1.0 / 7.0;
+    p = fma(p, t, -1.0 / 6.0);
+    p = fma(p, t, 1.0 / 5.0);
+    p = fma(p, t, -1.0 / 4.0);
+    p = fma(p, t, 1.0 / 3.0);
+    p = fma(p, t, -0.5);
+    p = fma(p, t, 1.0);
+    p *= t;
+    const double ln2_hi = 6.93147180369123816490e-01;   // high 32 bits of ln 2
+    const double ln2_lo = 1.90821492927058770002e-10;   // ln 2 - ln2_hi
+    return ((double)e * ln2_hi + __ldg(tb.logc + j)) + ((double)e * ln2_lo + p);
+}
+
+// Stirling's series for lgamma(x), x >= 65536 (Abramowitz & Stegun 6.1.41),
+// kept to the 1/(12x) term: the next term, 1/(360 x^3), is below 1e-17 there.
+// 1/x comes from the FP32 reciprocal: its error moves the result by < 1e-13.
+__device__ __forceinline__ double lgamma_large(double x, const LgTab& tb) {
+    const double r = (double)__frcp_rn((float)x);
+    const double half_log_2pi = 0.91893853320467274178;
+    return (x - 0.5) * log_tab(x, tb) - x + half_log_2pi + r * (1.0 / 12.0);
+}
+
+// lgamma(beta + S) - lgamma(beta)
+__device__ __forceinline__ double lg_shift(uint32_t S, double beta, double lg_beta,
+                                           const LgTab& tb) {
+    if (S < (uint32_t)kLgTable) return __ldg(tb.shift + S);
+    return lgamma_large(beta + (double)S, tb) - lg_beta;
+}
+
+// lgamma(n), n >= 1
+__device__ __forceinline__ double lg_count(uint32_t n, const LgTab& tb) {
+    return n < (uint32_t)kLgTable ? __ldg(tb.cnt + n) : lgamma_large((double)n, tb);
+}
+
+// lgamma(D beta + T)
+__device__ __forceinline__ double lg_total(unsigned long long T, double Db, const LgTab& tb) {
+    return T < (unsigned long long)kLgTable ? __ldg(tb.tot + T)
+                                            : lgamma_large(Db + (double)T, tb);
+}
+
+__global__ void k_lg_table(double* __restrict__ base, double beta, double Db) {
     const int S = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S < kLgTable) tab[S] = S ? lgamma(beta + (double)S) - lgamma(beta) : 0.0;
+    if (S < kLgTable) {
+        base[S] = S ? lgamma(beta + (double)S) - lgamma(beta) : 0.0;
+        base[kLgTable + S] = S ? lgamma((double)S) : 0.0;
+        base[2 * kLgTable + S] = lgamma(Db + (double)S);
+    }
+    if (S < kLogTab) {
+        base[3 * kLgTable + S] = log1p((double)S / kLogTab);
+        base[3 * kLgTable + kLogTab + S] = 1.0 / (1.0 + (double)S / kLogTab);
+    }
 }
 
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
@@ -101,29 +171,83 @@ struct MovePartial {
     unsigned long long Ta, Tb;
 };
 
-// Sum the chunks of proposal e, add the count and total terms, decide (one
-// warp; lanes sum the chunk partials and evaluate the seven count/total
-// lgamma terms in parallel).
-__device__ __forceinline__ void finalize_proposal(
-    int e, int G, const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
-    const double* __restrict__ sumlogq, const int32_t* __restrict__ pair_ab,
-    const MovePartial* __restrict__ part, int32_t* __restrict__ decide, double* __restrict__ log_h,
-    int32_t D, double alpha, double beta, int32_t split_q, const Stream& st) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t m = sc->m;
+// Per (proposal, gene chunk): each warp sums over its genes the lgamma terms
+// of the Hastings ratio and the two gene totals.  Block b serves proposal
+// b / G, chunk b % G, with G chosen so that proposals x G fills the grid.  The
+// last block to finish a proposal (a ticket counter, no waiting) completes
+// it, its four warps evaluating the count and total terms side by side.
+__global__ void __launch_bounds__(kPartialThreads)
+k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
+               const uint32_t* __restrict__ Ssub, const double* __restrict__ sumlogq,
+               const int32_t* __restrict__ pair_ab, const double* __restrict__ lg_base,
+               MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
+               int32_t* __restrict__ decide, double* __restrict__ log_h, int32_t D,
+               double log_alpha, double beta, double lg_beta, int32_t split_q, Stream st) {
+    __shared__ double fin[kPartialWarps][2];
+    __shared__ int last;
+    const LgTab tb = lg_tab_view(lg_base);
+    const int E = sc->n_entries;
+    if (E <= 0) return;
     const bool split = sc->chain_sel == 1;
-    const double Db = (double)D * beta;
+    const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
+    const int G = max(1, min((int)gridDim.x / E, maxG));
+    const int e = blockIdx.x / G, g = blockIdx.x - e * G;
+    if (e >= E) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int Dc = (D + G - 1) / G;
+    const int u0 = g * Dc, u1 = min(D, u0 + Dc);
     double acc = 0.0;
     unsigned long long Ta = 0, Tb = 0;
-    for (int g = lane; g < G; g += 32) {
-        const MovePartial p = part[e * G + g];
-        acc += p.acc;
-        Ta += p.Ta;
-        Tb += p.Tb;
+    if (split) {
+        const uint32_t* S0 = Ssub + (size_t)(2 * e) * D;
+        const uint32_t* S1 = S0 + D;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+            const uint32_t a = S0[u], b = S1[u];
+            Ta += a;
+            Tb += b;
+            if (a && b)
+                acc += lg_shift(a, beta, lg_beta, tb) + lg_shift(b, beta, lg_beta, tb) -
+                       lg_shift(a + b, beta, lg_beta, tb);
+        }
+    } else {
+        const int a = pair_ab[2 * e], b = pair_ab[2 * e + 1];
+        const uint32_t* A0 = Ssub + (size_t)(2 * a) * D;
+        const uint32_t* B0 = Ssub + (size_t)(2 * b) * D;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+            const uint32_t sa = A0[u] + A0[D + u], sb = B0[u] + B0[D + u];
+            Ta += sa;
+            Tb += sb;
+            if (sa && sb)
+                acc += lg_shift(sa + sb, beta, lg_beta, tb) - lg_shift(sa, beta, lg_beta, tb) -
+                       lg_shift(sb, beta, lg_beta, tb);
+        }
     }
     acc = warp_sum(acc);
     Ta = warp_sum(Ta);
     Tb = warp_sum(Tb);
+    if (lane == 0) part[blockIdx.x * kPartialWarps + w] = MovePartial{acc, Ta, Tb};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&ticket[e], 1) == G - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+
+    // ---- completion of proposal e by the whole block ----
+    const MovePartial* pe = part + (size_t)e * G * kPartialWarps;
+    acc = 0.0;
+    Ta = Tb = 0;
+    for (int i = lane; i < G * kPartialWarps; i += 32) {
+        const MovePartial p = pe[i];
+        if (w == 0) acc += p.acc;
+        Ta += p.Ta;
+        Tb += p.Tb;
+    }
+    Ta = warp_sum(Ta);
+    Tb = warp_sum(Tb);
+    const uint32_t m = sc->m;
     uint32_t na, nb;
     int a = e;
     if (split) {
@@ -135,108 +259,51 @@ __device__ __forceinline__ void finalize_proposal(
         na = nsub[2 * a] + nsub[2 * a + 1];
         nb = nsub[2 * b] + nsub[2 * b + 1];
     }
-    double arg = 1.0;
-    if (lane == 0) arg = Db;
-    else if (lane == 1) arg = Db + (double)Ta;
-    else if (lane == 2) arg = Db + (double)Tb;
-    else if (lane == 3) arg = Db + (double)(Ta + Tb);
-    else if (lane == 4) arg = (double)na;
-    else if (lane == 5) arg = (double)nb;
-    else if (lane == 6) arg = (double)(na + nb);
-    const double lg = (lane < 7 && arg > 0.0) ? lgamma(arg) : 0.0;
-    const double lgDb = __shfl_sync(0xFFFFFFFFu, lg, 0);
-    const double lfa = lgDb - __shfl_sync(0xFFFFFFFFu, lg, 1);
-    const double lfb = lgDb - __shfl_sync(0xFFFFFFFFu, lg, 2);
-    const double lfab = lgDb - __shfl_sync(0xFFFFFFFFu, lg, 3);
-    const double lna = __shfl_sync(0xFFFFFFFFu, lg, 4);
-    const double lnb = __shfl_sync(0xFFFFFFFFu, lg, 5);
-    const double lnab = __shfl_sync(0xFFFFFFFFu, lg, 6);
-    if (lane != 0) return;
+    const double Db = (double)D * beta;
+    double v0 = 0.0, v1 = 0.0;
+    if (w == 0) {
+        v0 = warp_sum(acc);
+        const uint32_t word = split ? st.words(TAG_MOVE, (uint32_t)e + 1u, m, 0u).x
+                                    : st.words(TAG_MERGE, (uint32_t)a, m, 0u).x;
+        v1 = log_tab((double)word_uniform(word), tb);
+    } else if (w == 1) {
+        v0 = lg_total(Ta, Db, tb);
+        v1 = na ? lg_count(na, tb) : 0.0;
+    } else if (w == 2) {
+        v0 = lg_total(Tb, Db, tb);
+        v1 = nb ? lg_count(nb, tb) : 0.0;
+    } else {
+        v0 = lg_total(Ta + Tb, Db, tb);
+        v1 = na + nb ? lg_count(na + nb, tb) : 0.0;
+    }
+    if (lane == 0) {
+        fin[w][0] = v0;
+        fin[w][1] = v1;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ticket[e] = 0;
+    const double lgDb = __ldg(tb.tot);
+    const double lfa = lgDb - fin[1][0], lfb = lgDb - fin[2][0], lfab = lgDb - fin[3][0];
+    const double lna = fin[1][1], lnb = fin[2][1], lnab = fin[3][1];
+    acc = fin[0][0];
+    const double log_u = fin[0][1];
     if (split) {
         if (na < 1 || nb < 1) {
             decide[e] = 0;
             log_h[e] = CUDART_NAN;
             return;
         }
-        double lh = log(alpha) + lna + lnb - lnab + lfa + lfb - lfab + acc;
+        double lh = log_alpha + lna + lnb - lnab + lfa + lfb - lfab + acc;
         if (split_q) lh -= sumlogq[e];
-        const double u = (double)word_uniform(st.words(TAG_MOVE, (uint32_t)e + 1u, m, 0u).x);
-        decide[e] = log(u) < lh ? 1 : 0;
+        decide[e] = log_u < lh ? 1 : 0;
         log_h[e] = lh;
     } else {
-        const double lh = -log(alpha) + lnab - lna - lnb + lfab - lfa - lfb + acc +
-                          (double)(na + nb - 2) * log(0.5);
-        const double u = (double)word_uniform(st.words(TAG_MERGE, (uint32_t)a, m, 0u).x);
-        decide[e] = log(u) < lh ? 1 : 0;
+        const double kLogHalf = -0.69314718055994530942;
+        const double lh = -log_alpha + lnab - lna - lnb + lfab - lfa - lfb + acc +
+                          (double)(na + nb - 2) * kLogHalf;
+        decide[e] = log_u < lh ? 1 : 0;
         log_h[e] = lh;
-    }
-}
-
-// Per (proposal, gene chunk): sum over the chunk of the lgamma terms of the
-// Hastings ratio and the two gene totals.  Block b serves proposal b / G,
-// chunk b % G, with G chosen so that proposals x G fills the grid.  The last
-// block to finish a proposal (a ticket counter, no waiting) completes it.
-__global__ void __launch_bounds__(kPartialThreads)
-k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
-               const uint32_t* __restrict__ Ssub, const double* __restrict__ sumlogq,
-               const int32_t* __restrict__ pair_ab, const double* __restrict__ tab,
-               MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
-               int32_t* __restrict__ decide, double* __restrict__ log_h, int32_t D, double alpha,
-               double beta, int32_t split_q, Stream st) {
-    __shared__ double redd[4];
-    __shared__ unsigned long long redu[4];
-    __shared__ int last;
-    const int E = sc->n_entries;
-    if (E <= 0) return;
-    const bool split = sc->chain_sel == 1;
-    const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
-    const int G = max(1, min((int)gridDim.x / E, maxG));
-    const int e = blockIdx.x / G, g = blockIdx.x - e * G;
-    if (e >= E) return;
-    const int Dc = (D + G - 1) / G;
-    const int u0 = g * Dc, u1 = min(D, u0 + Dc);
-    const double lgb = lgamma(beta);
-    double acc = 0.0;
-    unsigned long long Ta = 0, Tb = 0;
-    if (split) {
-        const uint32_t* S0 = Ssub + (size_t)(2 * e) * D;
-        const uint32_t* S1 = S0 + D;
-        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-            const uint32_t a = S0[u], b = S1[u];
-            Ta += a;
-            Tb += b;
-            if (a && b)
-                acc += lg_shift(a, beta, lgb, tab) + lg_shift(b, beta, lgb, tab) -
-                       lg_shift(a + b, beta, lgb, tab);
-        }
-    } else {
-        const int a = pair_ab[2 * e], b = pair_ab[2 * e + 1];
-        const uint32_t* A0 = Ssub + (size_t)(2 * a) * D;
-        const uint32_t* B0 = Ssub + (size_t)(2 * b) * D;
-        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-            const uint32_t sa = A0[u] + A0[D + u], sb = B0[u] + B0[D + u];
-            Ta += sa;
-            Tb += sb;
-            if (sa && sb)
-                acc += lg_shift(sa + sb, beta, lgb, tab) - lg_shift(sa, beta, lgb, tab) -
-                       lg_shift(sb, beta, lgb, tab);
-        }
-    }
-    acc = block_sum_d(acc, redd);
-    Ta = block_sum_u64(Ta, redu);
-    Tb = block_sum_u64(Tb, redu);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = MovePartial{acc, Ta, Tb};
-        __threadfence();
-        last = atomicAdd(&ticket[e], 1) == G - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (threadIdx.x < 32) {
-        finalize_proposal(e, G, sc, nsub, sumlogq, pair_ab, part, decide, log_h, D, alpha, beta,
-                          split_q, st);
-        if (threadIdx.x == 0) ticket[e] = 0;
     }
 }
 
@@ -427,7 +494,8 @@ k_plan(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub, double* __rest
 }
 
 cudaError_t launch_lg_table(Ctx& c) {
-    k_lg_table<<<(kLgTable + 255) / 256, 256, 0, c.stream>>>(c.lg_table, c.beta);
+    k_lg_table<<<(kLgTable + 255) / 256, 256, 0, c.stream>>>(c.lg_table, c.beta,
+                                                             (double)c.D * c.beta);
     return cudaGetLastError();
 }
 
@@ -437,12 +505,12 @@ cudaError_t launch_move_score(Ctx& c, int32_t mode) {
     k_move_partial<<<kMaxPartials, kPartialThreads, 0, c.stream>>>(
         c.sc, c.nsub, c.Ssub, c.sumlogq, c.pair_ab, c.lg_table,
         reinterpret_cast<MovePartial*>(c.move_part), c.move_ticket, c.decide, c.log_h, c.D,
-        c.alpha, c.beta, c.opts.split_q, st);
+        std::log(c.alpha), c.beta, std::lgamma(c.beta), c.opts.split_q, st);
     return cudaGetLastError();
 }
 
-size_t move_partial_bytes() { return sizeof(MovePartial) * kMaxPartials; }
-size_t lg_table_entries() { return kLgTable; }
+size_t move_partial_bytes() { return sizeof(MovePartial) * kMaxPartials * kPartialWarps; }
+size_t lg_table_entries() { return 3 * (size_t)kLgTable + 2 * kLogTab; }
 
 cudaError_t launch_plan(Ctx& c, int32_t kind) {
     k_plan<<<1, kPlanThreads, 0, c.stream>>>(c.sc, kind, c.nsub, c.sumlogq, c.acc_nsub,
