@@ -304,32 +304,57 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
                             cudaMemcpyHostToDevice, c.stream));
     }
     if (c.packed && o.engine != DPMM_ENGINE_CSR_FP32) {
-        // blocked copy for the dense-tile engine: entries grouped by (tile, chunk)
+        // blocked copy for the dense-tile engine: entries grouped by segment
+        // (128-cell tile, 64-gene chunk) and, inside a segment, by quarter
+        // (32-cell row block) in cell order; every segment starts on a 16-byte
+        // boundary (padding entries have count 0) so that it moves as one
+        // bulk copy.  tile_ptr[4 s + q] = first entry of quarter q of segment
+        // s; tile_ptr[4 (s + 1)] = end of segment s, padding included.
         c.tile_T = (int32_t)((N + 127) / 128);
         c.tile_C = (D + 63) / 64;
         const size_t TC = (size_t)c.tile_T * c.tile_C;
-        std::vector<int32_t> tptr(TC + 1, 0);
+        std::vector<int64_t> qcount(4 * TC, 0);
         for (int64_t i = 0; i < N; ++i) {
             const size_t tb = (size_t)(i >> 7) * c.tile_C;
-            for (int32_t e = hptr[i]; e < hptr[i + 1]; ++e) tptr[tb + (hidx[e] >> 6) + 1]++;
+            const size_t q = (size_t)((i >> 5) & 3);
+            for (int32_t e = hptr[i]; e < hptr[i + 1]; ++e)
+                qcount[4 * (tb + (size_t)(hidx[e] >> 6)) + q]++;
         }
-        for (size_t j = 0; j < TC; ++j) tptr[j + 1] += tptr[j];
-        std::vector<int32_t> cur(tptr.begin(), tptr.end() - 1);
-        std::vector<uint32_t> tent((size_t)nnz);
+        std::vector<int64_t> qptr(4 * TC + 1, 0);
+        int64_t pos = 0, lmax = 4;
+        for (size_t sgm = 0; sgm < TC; ++sgm) {
+            const int64_t start = pos;
+            for (int q = 0; q < 4; ++q) {
+                qptr[4 * sgm + q] = pos;
+                pos += qcount[4 * sgm + q];
+            }
+            pos = (pos + 3) & ~(int64_t)3;
+            lmax = std::max(lmax, pos - start);
+        }
+        qptr[4 * TC] = pos;
+        if (pos > (int64_t)INT32_MAX)
+            return bail(fail(DPMM_EOVERFLOW, "the dense-tile copy needs %lld entries (> 2^31 - 1)",
+                             (long long)pos));
+        std::vector<int32_t> tptr(4 * TC + 1);
+        for (size_t j = 0; j <= 4 * TC; ++j) tptr[j] = (int32_t)qptr[j];
+        std::vector<int64_t> cur(qptr.begin(), qptr.end() - 1);
+        std::vector<uint32_t> tent((size_t)pos, 0u);
         for (int64_t i = 0; i < N; ++i) {
             const size_t tb = (size_t)(i >> 7) * c.tile_C;
+            const size_t q = (size_t)((i >> 5) & 3);
             const uint32_t r = (uint32_t)(i & 127);
             for (int32_t e = hptr[i]; e < hptr[i + 1]; ++e)
-                tent[cur[tb + (hidx[e] >> 6)]++] =
+                tent[cur[4 * (tb + (size_t)(hidx[e] >> 6)) + q]++] =
                     (r << 22) | ((uint32_t)(hidx[e] & 63) << 16) | (uint32_t)hval[e];
         }
-        CKI(dalloc(&c.tile_ent, (size_t)nnz));
-        CKI(dalloc(&c.tile_ptr, TC + 1));
+        c.tile_Lslot = (int32_t)lmax;
+        CKI(dalloc(&c.tile_ent, (size_t)pos));
+        CKI(dalloc(&c.tile_ptr, 4 * TC + 1));
         CKI(dalloc(&c.tile_B, tile_b_bytes(c.tile_C)));
-        CKI(cudaMemcpyAsync(c.tile_ptr, tptr.data(), sizeof(int32_t) * (TC + 1),
+        CKI(cudaMemcpyAsync(c.tile_ptr, tptr.data(), sizeof(int32_t) * (4 * TC + 1),
                             cudaMemcpyHostToDevice, c.stream));
-        if (nnz)
-            CKI(cudaMemcpyAsync(c.tile_ent, tent.data(), sizeof(uint32_t) * nnz,
+        if (pos)
+            CKI(cudaMemcpyAsync(c.tile_ent, tent.data(), sizeof(uint32_t) * (size_t)pos,
                                 cudaMemcpyHostToDevice, c.stream));
         CKI(cudaStreamSynchronize(c.stream));
         c.tile_enabled = true;

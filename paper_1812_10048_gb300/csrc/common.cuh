@@ -125,7 +125,7 @@ struct Ctx {
     int32_t* decide = nullptr;    // [kmax] split decisions / merge pair decisions
     double* log_h = nullptr;      // [kmax]
     int32_t* pair_ab = nullptr;   // [2 kmax]
-    double* lg_table = nullptr;   // lgamma(beta + S) - lgamma(beta), S < 1024
+    double* lg_table = nullptr;   // exact lgamma tables and log breakpoints (moves.cu)
     unsigned char* move_part = nullptr;  // per-block partial sums of the move scores
     int32_t* move_ticket = nullptr;      // [kmax] finished chunks per proposal (reset to 0)
 
@@ -138,8 +138,9 @@ struct Ctx {
     // dense-tile engine: counts blocked by (128-cell tile, 64-gene chunk)
     bool tile_enabled = false;
     int32_t tile_T = 0, tile_C = 0;
-    uint32_t* tile_ent = nullptr;   // row << 22 | gene-in-chunk << 16 | count
-    int32_t* tile_ptr = nullptr;    // [T * C + 1]
+    int32_t tile_Lslot = 0;         // longest padded segment, entries
+    uint32_t* tile_ent = nullptr;   // row << 22 | gene-in-chunk << 16 | count (0: padding)
+    int32_t* tile_ptr = nullptr;    // [4 T C + 1] quarter starts
     unsigned char* tile_B = nullptr;  // per-sweep BF16 hi/lo table, [C][256 rows][64] swizzled
 
     // CUDA graph of dpmm_step

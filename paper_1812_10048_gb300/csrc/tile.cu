@@ -189,40 +189,51 @@ k_build_b(const DevScalars* __restrict__ sc, const float* __restrict__ Lc,
 
 struct TileArgs {
     const uint32_t* ent;      // blocked entries: row << 22 | gene-in-chunk << 16 | count
-    const int32_t* ptr;       // [T * C + 1] entry offsets per (tile, chunk)
+    const int32_t* ptr;       // [4 T C + 1] quarter starts of every (tile, chunk) segment
     const unsigned char* B;   // [C][kBChunkBytes]
     DevScalars* sc;
     uint32_t* state;
     const uint32_t* nsub;
     const float* logpi;
     double* acc_sumlogq;
-    uint32_t* acc_nsub;
-    uint32_t* acc_Ssub;
     float* dbg;               // optional [N][3K] centred scores; no state/statistics writes
     int64_t N;
     int32_t D, C, T;
+    int32_t Lslot;            // entries per segment slot (longest padded segment)
     int64_t smem_bytes;
     Stream st;
 };
 
-// Warp roles of the pipelined engine (416 threads):
-//   warps 0-3   epilogue: one cell per thread (TMEM lanes 0-127), label and
-//               sub-label
-//   warps 4-11  producers, two groups of 4 warps taking alternate chunks:
-//               densify a chunk into a stage of the ring (entries prefetched
-//               four chunks ahead in registers) and start the stage's B copy
-//   warp 12     lane 0 issues the MMAs (two TMEM accumulators, 2 x 256 columns)
-// Stage hand-offs use mbarriers: a_full (producers -> MMA), b_full (bulk copy
-// -> MMA), stage_free (MMA commit -> producers), acc_full (MMA commit ->
-// epilogue), acc_empty (epilogue -> MMA).  Every wait is bounded; a timeout
-// records DPMM_ETIMEOUT and every role leaves its loop at its next barrier.
-constexpr int kMaxStages = 4;
-constexpr int kProdWarp0 = 4;
-constexpr int kProdGroupThreads = 128;   // two producer groups of 4 warps
-constexpr int kMmaWarp = 12;
-constexpr int kTileThreadsP = 13 * 32;
-constexpr int kBarProd0 = 1, kBarLabel = 2, kBarProd1 = 3;
-constexpr int kProdRegs = 16;   // entries per producer thread and chunk held in registers
+// Warp roles of the pipelined engine (19 warps):
+//   warps 0-7   epilogue, two halves of four warps over the same 128 cells
+//               (warp w reads TMEM lanes 32 (w % 4) ..): each half takes every
+//               other 8-cluster column group of the Gumbel-max; half 1 also
+//               draws the eq. 8 noise, half 0 merges and finishes the cell
+//   warps 8-15  producers, two sets of four warps taking alternate chunks;
+//               warp q of a set densifies rows 32q .. 32q + 31 of its chunk
+//               (the entries of one quarter) from the staged segment, so the
+//               four warps never wait on one another
+//   warp 16     lane 0 issues the MMAs (two TMEM accumulators of 256 columns)
+//   warp 17     segment loader: bulk-copies each chunk's entries into a ring
+//               of slots, reading the segment table a warp-batch ahead
+//   warp 18     lane 0 bulk-copies the B operand of each chunk into its ring
+// Hand-offs are mbarriers: ent_full / ent_free (segment slots), a_full (four
+// producer warps -> MMA) / stage_free (MMA commit -> producers), b_full /
+// b_free (B slots), acc_full (MMA -> epilogue) / acc_empty (epilogue -> MMA).
+// Every wait is bounded; a timeout records DPMM_ETIMEOUT, every role leaves
+// its loop, and each role that issued asynchronous work waits (bounded) for
+// it before the block exits.
+constexpr int kMaxStages = 4;        // A stages (lo + hi), even
+constexpr int kMaxBSlots = 4;
+constexpr int kMaxESlots = 16;
+constexpr int kEpiWarps = 8;
+constexpr int kProdWarp0 = 8;
+constexpr int kMmaWarp = 16;
+constexpr int kELoadWarp = 17;
+constexpr int kBLoadWarp = 18;
+constexpr int kTileThreadsP = 19 * 32;
+constexpr int kBarEpi = 1, kBarLabel = 2;
+constexpr int kSmallBytes = 8192;
 
 __global__ void __launch_bounds__(kTileThreadsP, 1)
 k_assign_tc(TileArgs a) {
@@ -230,38 +241,50 @@ k_assign_tc(TileArgs a) {
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int K = a.sc->K;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool use = tile_usable(K);
     if (!a.dbg && blockIdx.x == 0 && tid == 0) a.sc->tile_used = use ? 1 : 0;
     if (!use) return;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
     const uint32_t t = a.sc->t;
-    const uint32_t b_stage = ((uint32_t)Ntot * 128u + 1023u) & ~1023u;
-    // as many ring stages (A lo + hi, B) as shared memory holds, 2 .. 4
-    const int64_t room = a.smem_bytes - (int64_t)(base - smem_raw) - 8192;
-    const int kStages = (int)max((int64_t)2, min((int64_t)kMaxStages, room / (int64_t)(32768 + b_stage)));
-    unsigned char* A_base = base;                                    // stage s: lo, then hi
-    unsigned char* B_base = base + kStages * 32768;
-    unsigned char* small = B_base + kStages * b_stage;
-    uint64_t* a_full = reinterpret_cast<uint64_t*>(small);           // [kMaxStages]
-    uint64_t* b_full = a_full + kMaxStages;                           // [kMaxStages]
-    uint64_t* stage_free = b_full + kMaxStages;                       // [kMaxStages]
-    uint64_t* acc_full = stage_free + kMaxStages;                     // [2]
-    uint64_t* acc_empty = acc_full + 2;                               // [2]
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    // shared-memory plan (identical in every thread): A stages, B slots,
+    // segment slots, then the small area
+    const int64_t b_slot = ((int64_t)Ntot * 128 + 1023) & ~(int64_t)1023;
+    const int64_t e_slot = (int64_t)a.Lslot * 4;
+    const int64_t avail = a.smem_bytes - (int64_t)(base - smem_raw) - kSmallBytes;
+    const int nS = (int64_t)kMaxStages * 32768 + 2 * b_slot + 2 * e_slot <= avail ? kMaxStages : 2;
+    const int nB = (int)min((int64_t)kMaxBSlots, (avail - nS * 32768 - 2 * e_slot) / b_slot);
+    const int nE = (int)min((int64_t)kMaxESlots,
+                            (avail - nS * 32768 - (int64_t)max(nB, 0) * b_slot) / e_slot);
+    if (nB < 2 || nE < 2) {
+        if (tid == 0) atomicExch(&a.sc->error, DPMM_ECAPACITY);
+        return;
+    }
+    unsigned char* A_base = base;                                  // stage s: lo, then hi
+    unsigned char* B_base = A_base + nS * 32768;
+    unsigned char* E_base = B_base + nB * b_slot;
+    unsigned char* small = E_base + nE * e_slot;
+    small = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(small) + 15) & ~(uintptr_t)15);
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(small);         // [kMaxStages]
+    uint64_t* stage_free = a_full + kMaxStages;                     // [kMaxStages]
+    uint64_t* b_full = stage_free + kMaxStages;                     // [kMaxBSlots]
+    uint64_t* b_free = b_full + kMaxBSlots;                         // [kMaxBSlots]
+    uint64_t* ent_full = b_free + kMaxBSlots;                       // [kMaxESlots]
+    uint64_t* ent_free = ent_full + kMaxESlots;                     // [kMaxESlots]
+    uint64_t* acc_full = ent_free + kMaxESlots;                     // [2]
+    uint64_t* acc_empty = acc_full + 2;                             // [2]
+    int32_t* meta = reinterpret_cast<int32_t*>(acc_empty + 2);      // [kMaxESlots][4]
+    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(meta + 4 * kMaxESlots);
     volatile int* err = reinterpret_cast<volatile int*>(taddr_s + 1);
-    int* stage_hi = const_cast<int*>(err) + 1;                        // [kMaxStages]
-    uint32_t* rows_cs = reinterpret_cast<uint32_t*>(stage_hi + kMaxStages);  // [2][128]
-    uint32_t* sn = rows_cs + 256;                                     // [2K]
-    float* spi = reinterpret_cast<float*>(sn + 2 * kTileMaxK);        // [K]
-    float* slw = spi + kTileMaxK;                                     // [4K]
-    float* wsq = slw + 4 * kTileMaxK;                                 // [4][K]
-    // role-uniform stop decisions: sampled by one thread before a role's
-    // barrier, read by every thread of the role after it
-    int* prod_stop = reinterpret_cast<int*>(wsq + 4 * kTileMaxK);     // [2] per group
-    int* epi_stop = prod_stop + 2;
-    // the statistics of the new labels come from k_stats_tile, launched after this kernel
-    if (!a.dbg && blockIdx.x == 0 && tid == 0) a.sc->stats_fused = 0;
+    int* stop = const_cast<int*>(err) + 1;                          // [2]
+    uint8_t* stage_hib = reinterpret_cast<uint8_t*>(stop + 2);      // [kMaxStages][4]
+    float* spi = reinterpret_cast<float*>(stage_hib + 4 * kMaxStages);  // [K]
+    float* slw = spi + kTileMaxK;                                   // [4K]
+    float* wsq = slw + 4 * kTileMaxK;                               // [4][K]
+    float* xbest = wsq + 4 * kTileMaxK;                             // [2][128] half 1 -> half 0
+    int* xc = reinterpret_cast<int*>(xbest + 256);                  // [2][128]
+    float* xg0 = reinterpret_cast<float*>(xc + 256);                // [2][128]
+    float* xg1 = xg0 + 256;                                         // [2][128]
 
     for (int k = tid; k < K; k += blockDim.x) spi[k] = a.logpi[k];
     for (int i = tid; i < 2 * K; i += blockDim.x) {
@@ -270,13 +293,30 @@ k_assign_tc(TileArgs a) {
         slw[2 * i + 1] = n > 1.0f ? logf(n - 1.0f) : -CUDART_INF_F;
     }
     for (int i = tid; i < 4 * K; i += blockDim.x) wsq[i] = 0.0f;
-    if (tid < kMaxStages) stage_hi[tid] = 0;
+    if (tid < 4 * kMaxStages) stage_hib[tid] = 0;
+    {
+        // the hi halves start clear: a producer warp clears its quarter of a hi
+        // half only after it has written counts above 255 there
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (int s = 0; s < nS; ++s) {
+            uint4* hi = reinterpret_cast<uint4*>(A_base + s * 32768 + 16384);
+            for (int i = tid; i < 1024; i += blockDim.x) hi[i] = z;
+        }
+    }
     if (tid == 0) {
         *err = 0;
+        stop[0] = stop[1] = 0;
         for (int i = 0; i < kMaxStages; ++i) {
-            tc::mbar_init(&a_full[i], 1);
-            tc::mbar_init(&b_full[i], 1);
+            tc::mbar_init(&a_full[i], 4);
             tc::mbar_init(&stage_free[i], 1);
+        }
+        for (int i = 0; i < kMaxBSlots; ++i) {
+            tc::mbar_init(&b_full[i], 1);
+            tc::mbar_init(&b_free[i], 1);
+        }
+        for (int i = 0; i < kMaxESlots; ++i) {
+            tc::mbar_init(&ent_full[i], 1);
+            tc::mbar_init(&ent_free[i], 4);
         }
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&acc_full[i], 1);
@@ -288,106 +328,152 @@ k_assign_tc(TileArgs a) {
         tc::tmem_alloc(taddr_s, 512);
         tc::tmem_relinquish();
     }
+    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *taddr_s;
+    const uint32_t my_tiles =
+        (int)blockIdx.x < a.T ? (uint32_t)((a.T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1) : 0u;
+    const uint32_t total = my_tiles * (uint32_t)a.C;   // chunks of this block
 
     if (warp >= kProdWarp0 && warp < kMmaWarp) {
         // ---------------- producers ----------------
-        const int grp = (warp - kProdWarp0) >> 2;                 // chunks g with g % 2 == grp
-        const int pt = tid - (kProdWarp0 + 4 * grp) * 32;         // 0 .. 127
-        const int bar_id = grp ? kBarProd1 : kBarProd0;
-        const uint32_t my_tiles =
-            (int)blockIdx.x < a.T ? (uint32_t)((a.T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1) : 0u;
-        const uint32_t total = my_tiles * (uint32_t)a.C;
-        auto bounds = [&](uint32_t gg, int& lo, int& hi) {
-            lo = hi = 0;
-            if (gg < total) {
-                const uint32_t ti = gg / (uint32_t)a.C, ci = gg - ti * (uint32_t)a.C;
-                const int tile = (int)blockIdx.x + (int)ti * (int)gridDim.x;
-                lo = __ldg(a.ptr + tile * a.C + ci);
-                hi = __ldg(a.ptr + tile * a.C + ci + 1);
+        const int set = (warp - kProdWarp0) >> 2, q = (warp - kProdWarp0) & 3;
+        uint32_t hi_dirty = 0u;   // stages whose hi quarter this warp left non-zero
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t g = (uint32_t)set; g < total; g += 2) {
+            const int st = (int)(g % (uint32_t)nS);
+            const int es = (int)(g % (uint32_t)nE);
+            bool ok = tc::mbar_wait(&ent_full[es], (g / (uint32_t)nE) & 1u, kWaitLimit);
+            if (ok && g >= (uint32_t)nS)
+                ok = tc::mbar_wait(&stage_free[st], ((g / (uint32_t)nS) - 1u) & 1u, kWaitLimit);
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                if (lane == 0) *err = DPMM_ETIMEOUT;
+                break;
             }
-        };
-        auto fetch = [&](uint32_t (&dst)[kProdRegs], int lo, int hi) {
-#pragma unroll
-            for (int j = 0; j < kProdRegs; ++j) {
-                const int e = lo + pt + kProdGroupThreads * j;
-                dst[j] = e < hi ? __ldg(a.ent + e) : 0xFFFFFFFFu;
-            }
-        };
-        // register pipeline over this group's chunks g, g + 2, g + 4 (entries) and
-        // g + 6, g + 8 (bounds)
-        uint32_t ecur[kProdRegs], eA[kProdRegs], eB[kProdRegs];
-        int aL, aH, bL, bH, cL, cH, dL, dH;
-        bounds((uint32_t)grp, aL, aH);
-        bounds((uint32_t)grp + 2, bL, bH);
-        fetch(eA, aL, aH);
-        fetch(eB, bL, bH);
-        bounds((uint32_t)grp + 4, cL, cH);
-        bounds((uint32_t)grp + 6, dL, dH);
-        for (uint32_t g = (uint32_t)grp; g < total; g += 2) {
-            const uint32_t ti = g / (uint32_t)a.C;
-            const int c = (int)(g - ti * (uint32_t)a.C);
-            const int st = (int)(g % (uint32_t)kStages);
-            const uint32_t n = g / (uint32_t)kStages;
+            if (__any_sync(0xFFFFFFFFu, *err != 0)) break;
             unsigned char* A_lo = A_base + st * 32768;
             unsigned char* A_hi = A_lo + 16384;
-            const int p0 = aL, p1 = aH;
+            uint4* zl = reinterpret_cast<uint4*>(A_lo + q * 4096);
 #pragma unroll
-            for (int j = 0; j < kProdRegs; ++j) {
-                ecur[j] = eA[j];
-                eA[j] = eB[j];
-            }
-            aL = bL;
-            aH = bH;
-            bL = cL;
-            bH = cH;
-            cL = dL;
-            cH = dH;
-            fetch(eB, bL, bH);
-            bounds(g + 8, dL, dH);
-            if (g >= (uint32_t)kStages &&
-                !tc::mbar_wait(&stage_free[st], (n - 1) & 1, kWaitLimit))
-                *err = DPMM_ETIMEOUT;
-            if (pt == 0 && !*err) {
-                stage_hi[st] = 0;
-                tc::mbar_arrive_expect_tx(&b_full[st], (uint32_t)Ntot * 128u);
-                tc::bulk_g2s(B_base + st * b_stage, a.B + (size_t)c * kBChunkBytes,
-                             (uint32_t)Ntot * 128u, &b_full[st]);
-            }
-            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+            for (int i = 0; i < 8; ++i) zl[lane + 32 * i] = z;
+            if ((hi_dirty >> st) & 1u) {
+                uint4* zh = reinterpret_cast<uint4*>(A_hi + q * 4096);
 #pragma unroll
-            for (int i = 0; i < 16; ++i)   // A lo and A hi: 32 KB
-                reinterpret_cast<uint4*>(A_lo)[pt + kProdGroupThreads * i] = z;
-            tc::named_bar(bar_id, kProdGroupThreads);
+                for (int i = 0; i < 8; ++i) zh[lane + 32 * i] = z;
+            }
+            __syncwarp();
+            const int32_t* mt = meta + 4 * es;
+            const int i0 = q ? mt[q - 1] : 0, i1 = mt[q];
+            const uint32_t* ring = reinterpret_cast<const uint32_t*>(E_base + es * e_slot);
             int hi = 0;
-            auto put = [&](uint32_t v) {
-                const uint32_t r = v >> 22, gg = (v >> 16) & 63u, x = v & 0xFFFFu;
-                const uint32_t off = tc::swz_offset(r, gg);
+            for (int i = i0 + lane; i < i1; i += 32) {
+                const uint32_t v = ring[i];
+                const uint32_t x = v & 0xFFFFu;
+                if (!x) continue;
+                const uint32_t off = tc::swz_offset(v >> 22, (v >> 16) & 63u);
                 *reinterpret_cast<uint16_t*>(A_lo + off) = bf16_bits_rn((float)(x & 255u));
                 if (x >> 8) {
                     *reinterpret_cast<uint16_t*>(A_hi + off) = bf16_bits_rn((float)((x >> 8) << 8));
                     hi = 1;
                 }
-            };
-#pragma unroll
-            for (int j = 0; j < kProdRegs; ++j)
-                if (ecur[j] != 0xFFFFFFFFu) put(ecur[j]);
-            for (int e = p0 + pt + kProdGroupThreads * kProdRegs; e < p1; e += kProdGroupThreads)
-                put(__ldg(a.ent + e));
-            if (hi) atomicOr(&stage_hi[st], 1);
+            }
+            hi = __any_sync(0xFFFFFFFFu, hi);
             tc::fence_async_smem();
-            if (pt == 0) prod_stop[grp] = *err;
-            tc::named_bar(bar_id, kProdGroupThreads);
-            const bool halt = prod_stop[grp] != 0;
-            if (pt == 0 && !halt) tc::mbar_arrive(&a_full[st]);
-            if (halt) break;
+            __syncwarp();
+            if (lane == 0) {
+                stage_hib[4 * st + q] = (uint8_t)hi;
+                tc::mbar_arrive(&a_full[st]);
+                tc::mbar_arrive(&ent_free[es]);
+            }
+            hi_dirty = hi ? (hi_dirty | (1u << st)) : (hi_dirty & ~(1u << st));
+        }
+    } else if (warp == kELoadWarp) {
+        // ---------------- segment loader ----------------
+        // lane j holds the five quarter pointers of chunk gb + j
+        auto seg_ptrs = [&](uint32_t g, int32_t (&p)[5]) {
+            if (g < total) {
+                const uint32_t ti = g / (uint32_t)a.C, ci = g - ti * (uint32_t)a.C;
+                const int64_t sgm = ((int64_t)blockIdx.x + (int64_t)ti * gridDim.x) * a.C + ci;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) p[k] = __ldg(a.ptr + 4 * sgm + k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) p[k] = 0;
+            }
+        };
+        int32_t cur[5], nxt[5];
+        seg_ptrs((uint32_t)lane, cur);
+        uint32_t issued = 0;   // chunks whose copy was started
+        for (uint32_t gb = 0; gb < total; gb += 32) {
+            if (__any_sync(0xFFFFFFFFu, *err != 0)) break;
+            seg_ptrs(gb + 32 + (uint32_t)lane, nxt);
+            bool stop_l = false;
+            for (uint32_t j = 0; j < 32 && gb + j < total; ++j) {
+                const uint32_t g = gb + j;
+                const int es = (int)(g % (uint32_t)nE);
+                int32_t p[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) p[k] = __shfl_sync(0xFFFFFFFFu, cur[k], (int)j);
+                bool ok = true;
+                if (lane == 0 && g >= (uint32_t)nE)
+                    ok = tc::mbar_wait(&ent_free[es], ((g / (uint32_t)nE) - 1u) & 1u, kWaitLimit);
+                ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+                if (!ok && lane == 0) *err = DPMM_ETIMEOUT;
+                if (__any_sync(0xFFFFFFFFu, !ok || *err != 0)) {
+                    stop_l = true;
+                    break;
+                }
+                if (lane == 0) {
+                    int32_t* mt = meta + 4 * es;
+                    mt[0] = p[1] - p[0];
+                    mt[1] = p[2] - p[0];
+                    mt[2] = p[3] - p[0];
+                    mt[3] = p[4] - p[0];
+                    const uint32_t bytes = (uint32_t)(p[4] - p[0]) * 4u;
+                    if (bytes) {
+                        tc::mbar_arrive_expect_tx(&ent_full[es], bytes);
+                        tc::bulk_g2s(E_base + es * e_slot, a.ent + p[0], bytes, &ent_full[es]);
+                    } else {
+                        tc::mbar_arrive(&ent_full[es]);
+                    }
+                }
+                issued = g + 1;
+            }
+            if (stop_l) break;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) cur[k] = nxt[k];
+        }
+        // every started copy has landed before the block can exit
+        if (lane == 0)
+            for (uint32_t g = issued > (uint32_t)nE ? issued - (uint32_t)nE : 0u; g < issued; ++g)
+                tc::mbar_wait(&ent_full[g % (uint32_t)nE], (g / (uint32_t)nE) & 1u, kWaitLimit);
+    } else if (warp == kBLoadWarp) {
+        // ---------------- B loader ----------------
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)Ntot * 128u;
+            uint32_t issued = 0;
+            for (uint32_t g = 0; g < total; ++g) {
+                const int bs = (int)(g % (uint32_t)nB);
+                if (g >= (uint32_t)nB &&
+                    !tc::mbar_wait(&b_free[bs], ((g / (uint32_t)nB) - 1u) & 1u, kWaitLimit)) {
+                    *err = DPMM_ETIMEOUT;
+                    break;
+                }
+                if (*err) break;
+                const uint32_t c = g % (uint32_t)a.C;
+                tc::mbar_arrive_expect_tx(&b_full[bs], bytes);
+                tc::bulk_g2s(B_base + bs * b_slot, a.B + (size_t)c * kBChunkBytes, bytes,
+                             &b_full[bs]);
+                issued = g + 1;
+            }
+            for (uint32_t g = issued > (uint32_t)nB ? issued - (uint32_t)nB : 0u; g < issued; ++g)
+                tc::mbar_wait(&b_full[g % (uint32_t)nB], (g / (uint32_t)nB) & 1u, kWaitLimit);
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issue ----------------
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
             uint32_t g = 0, it = 0;
             const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)Ntot);
             for (int tile = blockIdx.x; tile < a.T && !*err; tile += gridDim.x, ++it) {
@@ -398,62 +484,71 @@ k_assign_tc(TileArgs a) {
                 }
                 tc::fence_after_sync();
                 const uint32_t acc = tmem + buf * 256u;
-                for (int c = 0; c < a.C; ++c, ++g) {
-                    const int st = (int)(g % kStages);
-                    const uint32_t n = g / kStages;
-                    if (!tc::mbar_wait(&a_full[st], n & 1, kWaitLimit) ||
-                        !tc::mbar_wait(&b_full[st], n & 1, kWaitLimit)) {
+                for (int c = 0; c < a.C; ++c) {
+                    const int st = (int)(g % (uint32_t)nS), bs = (int)(g % (uint32_t)nB);
+                    if (!tc::mbar_wait(&a_full[st], (g / (uint32_t)nS) & 1u, kWaitLimit) ||
+                        !tc::mbar_wait(&b_full[bs], (g / (uint32_t)nB) & 1u, kWaitLimit)) {
                         *err = DPMM_ETIMEOUT;
                         break;
                     }
                     tc::fence_after_sync();
                     const uint32_t alo = tc::smem_addr(A_base + st * 32768);
-                    const uint32_t bsm = tc::smem_addr(B_base + st * b_stage);
+                    const uint32_t bsm = tc::smem_addr(B_base + bs * b_slot);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         tc::mma_bf16(acc, tc::desc_sw128(alo + 32 * k), tc::desc_sw128(bsm + 32 * k),
                                      idesc, (c | k) != 0);
-                    if (stage_hi[st]) {
+                    if (*reinterpret_cast<volatile uint32_t*>(stage_hib + 4 * st)) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
                             tc::mma_bf16(acc, tc::desc_sw128(alo + 16384 + 32 * k),
                                          tc::desc_sw128(bsm + 32 * k), idesc, 1u);
                     }
                     tc::mma_commit(&stage_free[st]);
+                    tc::mma_commit(&b_free[bs]);
+                    ++g;
                 }
                 if (*err) break;
                 tc::mma_commit(&acc_full[buf]);
             }
+            // the MMAs of the last chunk have completed (and signalled) before exit
+            if (g > 0) {
+                const uint32_t l = g - 1;
+                tc::mbar_wait(&stage_free[l % (uint32_t)nS], (l / (uint32_t)nS) & 1u, kWaitLimit);
+                tc::mbar_wait(&b_free[l % (uint32_t)nB], (l / (uint32_t)nB) & 1u, kWaitLimit);
+            }
         }
     } else {
-        // ---------------- epilogue and statistics (warps 0-3) ----------------
+        // ---------------- epilogue (warps 0-7) ----------------
+        const int h = warp >> 2, qw = warp & 3;
+        const int r = 32 * qw + lane;
         uint32_t it = 0;
         for (int tile = blockIdx.x; tile < a.T; tile += gridDim.x, ++it) {
-            const uint32_t buf = it & 1;
-            uint32_t* rcs = rows_cs + 128 * buf;
-            {
-                if (!tc::mbar_wait(&acc_full[buf], (it >> 1) & 1, kWaitLimit)) *err = DPMM_ETIMEOUT;
-                tc::fence_after_sync();
-                const int r = tid;
-                const int64_t cell = (int64_t)tile * 128 + r;
-                const bool live = cell < a.N && !*err;
-                const uint32_t trow = tmem + buf * 256u + ((uint32_t)(warp * 32) << 16);
-                float best = -CUDART_INF_F;
-                int c = 0;
-                for (int q = 0; q < S0 / 16; ++q) {
+            const uint32_t buf = it & 1, xb = it & 1;
+            const bool ok = tc::mbar_wait(&acc_full[buf], (it >> 1) & 1, kWaitLimit);
+            if (!ok) *err = DPMM_ETIMEOUT;
+            tc::fence_after_sync();
+            const bool okw = __all_sync(0xFFFFFFFFu, ok);
+            const int64_t cell = (int64_t)tile * 128 + r;
+            const bool live = cell < a.N;
+            const uint32_t trow = tmem + buf * 256u + ((uint32_t)(32 * qw) << 16);
+            float best = -CUDART_INF_F;
+            int c = h ? K : 0;   // half 1's "none" loses every tie
+            if (okw) {
+                for (int q = h; q < S0 / 16; q += 2) {
                     float v[16];
                     tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
                     tc::tmem_ld_wait();
-                    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int k = 8 * q + i;
                         if ((i & 3) == 0 && k < K)
-                            w = a.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
+                            w4 = a.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
                         if (k < K) {
                             const float sc = v[2 * i] + v[2 * i + 1];
                             if (a.dbg && live) a.dbg[(size_t)cell * 3 * K + k] = sc;
-                            const float val = (spi[k] + sc) + gumbel(word_of(w, i & 3));
+                            const float val = (spi[k] + sc) + gumbel(word_of(w4, i & 3));
                             if (val > best) {
                                 best = val;
                                 c = k;
@@ -461,53 +556,68 @@ k_assign_tc(TileArgs a) {
                         }
                     }
                 }
-                float t0 = 0.0f, t1 = 0.0f;
-                const int s0 = S0 + 4 * c;
-                for (int q = S0 / 16; q < Ntot / 16; ++q) {
-                    float v[16];
-                    tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
-                    tc::tmem_ld_wait();
-                    if (a.dbg && live) {
-#pragma unroll
-                        for (int i = 0; i < 16; i += 2) {
-                            const int col = 16 * q + i - S0;
-                            if (col < 4 * K)
-                                a.dbg[(size_t)cell * 3 * K + K + (col >> 1)] = v[i] + v[i + 1];
-                        }
-                    }
-                    if ((s0 >> 4) == q) {
-                        const int o = s0 & 15;
-                        if (o == 0) { t0 = v[0] + v[1]; t1 = v[2] + v[3]; }
-                        else if (o == 4) { t0 = v[4] + v[5]; t1 = v[6] + v[7]; }
-                        else if (o == 8) { t0 = v[8] + v[9]; t1 = v[10] + v[11]; }
-                        else { t0 = v[12] + v[13]; t1 = v[14] + v[15]; }
-                    }
-                }
-                tc::fence_before_sync();
-                uint32_t cs = 0xFFFFFFFFu;
-                if (live && !a.dbg) {
-                    const uint32_t old = a.state[cell];
-                    const bool stays = state_label(old) == (uint32_t)c;
-                    const uint32_t so = state_sub(old);
-                    const float lw0 = slw[4 * c + (stays && so == 0 ? 1 : 0)];
-                    const float lw1 = slw[4 * c + 2 + (stays && so == 1 ? 1 : 0)];
-                    const bool both_empty = lw0 == -CUDART_INF_F && lw1 == -CUDART_INF_F;
-                    const float l0 = (both_empty ? 0.0f : lw0) + t0;
-                    const float l1 = (both_empty ? 0.0f : lw1) + t1;
-                    const uint4 hw = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
-                    const uint32_t s = (l1 + gumbel(hw.y) > l0 + gumbel(hw.x)) ? 1u : 0u;
-                    const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
-                    const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
-                    a.state[cell] = pack_state((uint32_t)c, s);
-                    atomicAdd(&wsq[warp * K + c], logq);
-                    cs = pack_state((uint32_t)c, s);
-                }
-                rcs[r] = cs;
-                if (tid == 0) *epi_stop = *err;
-                tc::named_bar(kBarLabel, 128);
-                if (tid == 0 && !*epi_stop) tc::mbar_arrive(&acc_empty[buf]);
             }
-            if (*epi_stop) break;
+            if (h == 1) {
+                xbest[128 * xb + r] = best;
+                xc[128 * xb + r] = c;
+                const uint4 hw = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+                xg0[128 * xb + r] = gumbel(hw.x);
+                xg1[128 * xb + r] = gumbel(hw.y);
+            }
+            tc::fence_before_sync();
+            if (tid == 0) stop[xb] = *err;
+            tc::named_bar(kBarEpi, 32 * kEpiWarps);
+            if (stop[xb]) break;
+            if (h == 1) continue;
+            {
+                const float b1 = xbest[128 * xb + r];
+                const int c1 = xc[128 * xb + r];
+                if (b1 > best || (b1 == best && c1 < c)) {
+                    best = b1;
+                    c = c1;
+                }
+            }
+            float t0 = 0.0f, t1 = 0.0f;
+            const int s0 = S0 + 4 * c;
+            for (int q = S0 / 16; q < Ntot / 16; ++q) {
+                float v[16];
+                tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
+                tc::tmem_ld_wait();
+                if (a.dbg && live) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const int col = 16 * q + i - S0;
+                        if (col < 4 * K)
+                            a.dbg[(size_t)cell * 3 * K + K + (col >> 1)] = v[i] + v[i + 1];
+                    }
+                }
+                if ((s0 >> 4) == q) {
+                    const int o = s0 & 15;
+                    if (o == 0) { t0 = v[0] + v[1]; t1 = v[2] + v[3]; }
+                    else if (o == 4) { t0 = v[4] + v[5]; t1 = v[6] + v[7]; }
+                    else if (o == 8) { t0 = v[8] + v[9]; t1 = v[10] + v[11]; }
+                    else { t0 = v[12] + v[13]; t1 = v[14] + v[15]; }
+                }
+            }
+            tc::fence_before_sync();
+            if (live && !a.dbg) {
+                const uint32_t old = a.state[cell];
+                const bool stays = state_label(old) == (uint32_t)c;
+                const uint32_t so = state_sub(old);
+                const float lw0 = slw[4 * c + (stays && so == 0 ? 1 : 0)];
+                const float lw1 = slw[4 * c + 2 + (stays && so == 1 ? 1 : 0)];
+                const bool both_empty = lw0 == -CUDART_INF_F && lw1 == -CUDART_INF_F;
+                const float l0 = (both_empty ? 0.0f : lw0) + t0;
+                const float l1 = (both_empty ? 0.0f : lw1) + t1;
+                const uint32_t s =
+                    (l1 + xg1[128 * xb + r] > l0 + xg0[128 * xb + r]) ? 1u : 0u;
+                const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
+                const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
+                a.state[cell] = pack_state((uint32_t)c, s);
+                atomicAdd(&wsq[qw * K + c], logq);
+            }
+            tc::named_bar(kBarLabel, 128);
+            if (tid == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
     }
     __syncthreads();
@@ -524,11 +634,6 @@ k_assign_tc(TileArgs a) {
     }
 }
 
-// Statistics n-bar[k][r], S-bar[k][r][u] of the labels the dense-tile engine
-// just drew, read from the blocked entries: one warp per (tile, chunk)
-// segment with the tile's 128 cell states cached in shared memory; counters
-// private to the block in shared memory when 2 K D words fit, else global
-// atomics.  Integer sums, exact.
 // Statistics n-bar[k][r], S-bar[k][r][u] of the labels the dense-tile engine
 // just drew, read from the blocked entries.  Blocks are partitioned by gene
 // chunk: block b takes chunk b % C of every tile t = b / C, b / C + nt, ...
@@ -565,8 +670,8 @@ k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ sta
             if (c == 0 && st != 0xFFFFFFFFu) atomicAdd(&pn[2 * state_label(st) + state_sub(st)], 1u);
         }
         __syncwarp();
-        const int seg = tile * C + c;
-        const int p0 = ptr[seg], p1 = ptr[seg + 1];
+        const int64_t seg = (int64_t)tile * C + c;
+        const int p0 = ptr[4 * seg], p1 = ptr[4 * seg + 4];
         for (int e = p0 + lane; e < p1; e += 32 * 16) {
             uint32_t v[16];   // 16 independent loads in flight per lane
 #pragma unroll
@@ -609,13 +714,12 @@ cudaError_t launch_tile_assign(Ctx& c, float* dbg) {
     a.nsub = c.nsub;
     a.logpi = c.logpi;
     a.acc_sumlogq = c.acc_sumlogq;
-    a.acc_nsub = c.acc_nsub;
-    a.acc_Ssub = c.acc_Ssub;
     a.dbg = dbg;
     a.N = c.N;
     a.D = c.D;
     a.C = c.tile_C;
     a.T = c.tile_T;
+    a.Lslot = c.tile_Lslot;
     a.smem_bytes = (int64_t)c.smem_optin;
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
     const int grid = c.tile_T < c.num_sms ? c.tile_T : c.num_sms;
