@@ -109,14 +109,24 @@ int dpmm_labels(dpmm_ctx* ctx, int32_t* out, int32_t* K_out);
 /*
  * Per-phase CUDA-event timing.  With enable = 1, every sweep and move records
  * events on the context stream (also inside the dpmm_step graph, which is
- * re-captured when the setting changes).  dpmm_phase_times() returns the
- * device time of each phase of the last step in ms (n <= 5 entries):
- * [0] pi/theta draws, [1] label + sub-label draw (the contraction, eq. 4
- * third line and eq. 8), [2] statistics, [3] empty-cluster removal,
- * [4] split/merge move.  dpmm_phase_times synchronises.
+ * re-captured when the setting changes).  dpmm_phase_times()
+ * returns the device time of each phase of the last step in ms (n <= 5
+ * entries): [0] pi/theta draws (+ the dense-tile B operand), [1] the label
+ * kernel (label + sub-label draw: the contraction of eq. 4 third line and
+ * eq. 8), [2] statistics (+ the CSR fallback when the dense-tile engine is
+ * built), [3] empty-cluster removal, [4] split/merge move.  dpmm_phase_times
+ * synchronises.
  */
 int dpmm_profile(dpmm_ctx* ctx, int32_t enable);
 int dpmm_phase_times(dpmm_ctx* ctx, float* ms, int32_t n);
+
+/*
+ * Number of plans applied since dpmm_init: sweep compactions and split/merge
+ * moves that changed some label or statistic (the others end right after
+ * the plan).  Instrumentation only (the paper has no counterpart).
+ * Synchronises.
+ */
+int dpmm_plans_applied(dpmm_ctx* ctx, int64_t* n);
 
 /* Block until all work enqueued on the context's stream is done. */
 int dpmm_sync(dpmm_ctx* ctx);

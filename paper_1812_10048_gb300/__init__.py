@@ -17,7 +17,7 @@ from ._lib import (DpmmError, ENGINE_AUTO, ENGINE_CSR_FP32, ENGINE_TILE_BF16, ch
 __all__ = [
     "DpmmError", "Sampler", "LogML", "dpmm_default_opts", "dpmm_init", "dpmm_free", "dpmm_sweep",
     "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
-    "dpmm_phase_times", "dpmm_get_state",
+    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_get_state",
     "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
     "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_tile_scores", "dpmm_debug_moves", "dpmm_logml_create",
     "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_logml_grad_noalloc",
@@ -78,6 +78,12 @@ def dpmm_labels(ctx, N):
 
 def dpmm_sync(ctx):
     check(lib().dpmm_sync(ctx))
+
+
+def dpmm_plans_applied(ctx):
+    n = ctypes.c_int64(0)
+    check(lib().dpmm_plans_applied(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def dpmm_profile(ctx, enable=True):
@@ -275,6 +281,9 @@ class Sampler:
 
     def sync(self):
         dpmm_sync(self.ctx)
+
+    def plans_applied(self):
+        return dpmm_plans_applied(self.ctx)
 
     @property
     def stream(self):

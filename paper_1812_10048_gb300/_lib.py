@@ -46,6 +46,7 @@ SIGNATURES = {
     "dpmm_step": (ctypes.c_int, [_P, _I32]),
     "dpmm_labels": (ctypes.c_int, [_P, _P, _P]),
     "dpmm_sync": (ctypes.c_int, [_P]),
+    "dpmm_plans_applied": (ctypes.c_int, [_P, _P]),
     "dpmm_profile": (ctypes.c_int, [_P, _I32]),
     "dpmm_phase_times": (ctypes.c_int, [_P, _P, _I32]),
     "dpmm_stream": (_P, [_P]),

@@ -104,7 +104,8 @@ void free_ctx(Ctx& c) {
     void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
                     c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
-                    c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B};
+                    c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B,
+                    c.tile_part, c.tile_ticket, c.gbar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.sc_host) cudaFreeHost(c.sc_host);
@@ -129,33 +130,62 @@ int mark(Ctx& c, int i) {
         if (_rc) return _rc;             \
     } while (0)
 
+// One step is a fixed sequence of kernels (a CUDA graph replays it):
+//   draws; [B operand; dense-tile labels;] CSR labels; statistics; plan +
+//   application of the compaction; move scores; plan + application of the move
+// Branches are decided on the device: a kernel of an untaken branch returns
+// at once (conditional graph nodes were measured slower than these early
+// exits).  Event records bracket the phases when profiling is on: [0] draws
+// (+ the dense-tile B operand), [1] label kernel, [2] statistics (+ the CSR
+// fallback), [3] compaction, [4] move.
+int enqueue_labelling(Ctx& c) {
+    if (c.tile_enabled) {
+        // dense-tile labels (1 <= K <= 40), else CSR labels; statistics of
+        // either from the blocked copy
+        CK(launch_build_b(c, false));
+        MARK(1);
+        CK(launch_tile_label(c, nullptr));
+        MARK(2);
+        CK(launch_assign(c));
+        CK(launch_tile_stats(c));
+    } else {
+        MARK(1);
+        CK(launch_assign(c));
+        MARK(2);
+        CK(launch_sweep_stats(c));
+        CK(launch_csr_commit(c));
+    }
+    MARK(3);
+    return DPMM_OK;
+}
+
+int enqueue_compaction(Ctx& c) {
+    CK(launch_plan_apply(c, PLAN_COMPACT));
+    return DPMM_OK;
+}
+
 int enqueue_sweep(Ctx& c) {
     MARK(0);
     CK(launch_draw_params(c));
-    MARK(1);
-    CK(launch_assign(c));
-    MARK(2);
-    CK(launch_sweep_stats(c));
-    MARK(3);
-    CK(launch_plan(c, PLAN_COMPACT));
-    CK(launch_apply_plan(c, PLAN_COMPACT));
+    int rc = enqueue_labelling(c);
+    if (rc) return rc;
+    rc = enqueue_compaction(c);
+    if (rc) return rc;
     MARK(4);
     return DPMM_OK;
 }
 
 int enqueue_assign_half(Ctx& c) {
-    CK(launch_assign(c));
-    CK(launch_sweep_stats(c));
-    CK(launch_plan(c, PLAN_COMPACT));
-    CK(launch_apply_plan(c, PLAN_COMPACT));
-    return DPMM_OK;
+    CK(launch_select_engine(c));
+    int rc = enqueue_labelling(c);
+    if (rc) return rc;
+    return enqueue_compaction(c);
 }
 
 int enqueue_moves(Ctx& c, int32_t mode) {
     MARK(4);
     CK(launch_move_score(c, mode));
-    CK(launch_plan(c, PLAN_SPLIT));
-    CK(launch_apply_plan(c, PLAN_SPLIT));
+    CK(launch_plan_apply(c, PLAN_SPLIT));
     MARK(5);
     return DPMM_OK;
 }
@@ -164,7 +194,7 @@ int enqueue_moves(Ctx& c, int32_t mode) {
 int recount_all(Ctx& c) {
     CK(cudaMemsetAsync(c.nsub, 0, sizeof(uint32_t) * 2 * c.kmax, c.stream));
     CK(cudaMemsetAsync(c.Ssub, 0, sizeof(uint32_t) * 2 * (size_t)c.kmax * c.D, c.stream));
-    CK(launch_stats(c, nullptr, c.nsub, c.Ssub, nullptr));
+    CK(launch_stats(c, nullptr, c.nsub, c.Ssub));
     return DPMM_OK;
 }
 
@@ -351,6 +381,10 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         CKI(dalloc(&c.tile_ent, (size_t)pos));
         CKI(dalloc(&c.tile_ptr, 4 * TC + 1));
         CKI(dalloc(&c.tile_B, tile_b_bytes(c.tile_C)));
+        c.tile_nt = tile_stat_groups(c);
+        CKI(dalloc(&c.tile_part, tile_part_words(c)));
+        CKI(dalloc(&c.tile_ticket, (size_t)c.tile_C));
+        CKI(cudaMemsetAsync(c.tile_ticket, 0, sizeof(int32_t) * c.tile_C, c.stream));
         CKI(cudaMemcpyAsync(c.tile_ptr, tptr.data(), sizeof(int32_t) * (4 * TC + 1),
                             cudaMemcpyHostToDevice, c.stream));
         if (pos)
@@ -369,6 +403,9 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     c.sc_host->K_new = 1;
     CKI(cudaMemcpyAsync(c.sc, c.sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, c.stream));
     CKI(configure_launches(c));
+    CKI(configure_plan_apply(c));
+    CKI(dalloc(&c.gbar, 1));
+    CKI(cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.stream));
     if (c.tile_enabled) CKI(configure_tile(c));
     CKI(launch_lg_table(c));
     CKI(launch_init_state(c));
@@ -425,7 +462,10 @@ int dpmm_step(dpmm_ctx* ctx, int32_t n) {
         int rc = enqueue_sweep(c);
         if (!rc) rc = enqueue_moves(c, 0);
         cudaError_t e = cudaStreamEndCapture(c.stream, &g);
-        if (rc) return rc;
+        if (rc) {
+            if (!e) cudaGraphDestroy(g);
+            return rc;
+        }
         CK(e);
         e = cudaGraphInstantiate(&c.step_exec, g, 0);
         cudaGraphDestroy(g);
@@ -468,6 +508,15 @@ int dpmm_phase_times(dpmm_ctx* ctx, float* ms, int32_t n) {
     if (!ms || n < 0 || n > 5) return fail(DPMM_EINVAL, "need ms and 0 <= n <= 5");
     CK(cudaStreamSynchronize(c.stream));
     for (int i = 0; i < n; ++i) CK(cudaEventElapsedTime(&ms[i], c.ev[i], c.ev[i + 1]));
+    return DPMM_OK;
+}
+
+int dpmm_plans_applied(dpmm_ctx* ctx, int64_t* n) {
+    CHECK_CTX(ctx);
+    if (!n) return fail(DPMM_EINVAL, "n is NULL");
+    int rc = sync_scalars(ctx->c);
+    if (rc) return rc;
+    *n = (int64_t)ctx->c.sc_host->n_apply;
     return DPMM_OK;
 }
 

@@ -70,13 +70,24 @@ struct DevScalars {
     int32_t n_entries;    // split: K proposals; merge: number of pairs
     int32_t error;        // sticky device error (DPMM_E*)
     int32_t stats_fused;  // the label kernel of this sweep also added the statistics
-    int32_t tile_used;    // the dense-tile engine labelled this sweep's cells
+    int32_t tile_used;    // the dense-tile engine labels this sweep's cells
+    int32_t apply;        // the pending plan changes some label or statistic
+    uint32_t n_apply;     // plans applied so far (sweep compactions and moves)
     int32_t pad;
 };
+
+// The dense-tile engine serves 1 <= K <= kTileMaxK.
+constexpr int kTileMaxK = 40;
 
 // ---------------------------------------------------------------------------
 // The context (owned by the C ABI layer).
 // ---------------------------------------------------------------------------
+// Counters of the grid-wide barrier (zero between uses).
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -142,6 +153,15 @@ struct Ctx {
     uint32_t* tile_ent = nullptr;   // row << 22 | gene-in-chunk << 16 | count (0: padding)
     int32_t* tile_ptr = nullptr;    // [4 T C + 1] quarter starts
     unsigned char* tile_B = nullptr;  // per-sweep BF16 hi/lo table, [C][256 rows][64] swizzled
+
+    uint32_t* tile_part = nullptr;  // per-block partial statistics of the tile engine
+    int32_t* tile_ticket = nullptr; // [C] finished blocks per gene chunk (reset to 0)
+    int32_t tile_nt = 0;            // tile groups per gene chunk in the statistics kernel
+
+    // plan + application kernel (cooperative, one block per SM)
+    GridBar* gbar = nullptr;
+    int apply_blocks = 0;
+    size_t apply_smem = 0;
 
     // CUDA graph of dpmm_step
     cudaGraphExec_t step_exec = nullptr;
@@ -272,16 +292,100 @@ struct Csr {
 inline Csr csr_of(const Ctx& c) { return Csr{c.indptr, c.entries, c.cols, c.counts}; }
 
 // ---------------------------------------------------------------------------
+// Grid-wide barrier for cooperative launches (all blocks co-resident).  The
+// last block to arrive resets the count and advances the generation; the
+// others poll the generation a bounded number of times and report failure
+// (false) if it never moves.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kGridBarLimit = 1u << 22;
+
+__device__ __forceinline__ bool grid_sync(GridBar* b) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = &b->gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            uint32_t i = 0;
+            while (*gen == g) {
+                if (++i > kGridBarLimit) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// n-bar[k][r], S-bar[k][r][u] of the cells of this block's contiguous share
+// of [0, N) whose cluster passes `mask` (all if null), added into nsub / Ssub
+// (K clusters).  Block-private shared-memory counters (spriv, priv_cap words)
+// when 2 K D + 2 K words fit, else direct global atomics.  Integer sums.
+__device__ __forceinline__ void stats_cells(const Csr& csr, const uint32_t* __restrict__ state,
+                                            const uint8_t* __restrict__ mask,
+                                            uint32_t* __restrict__ nsub,
+                                            uint32_t* __restrict__ Ssub, int64_t N, int32_t D,
+                                            int K, uint32_t* spriv, int64_t priv_cap) {
+    const int64_t words = (int64_t)2 * K * D;
+    const bool priv = words + 2 * K <= priv_cap;
+    uint32_t* sS = spriv;
+    uint32_t* sn = spriv + words;
+    if (priv)
+        for (int64_t i = threadIdx.x; i < words + 2 * K; i += blockDim.x) spriv[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * per, c1 = min(N, c0 + per);
+    for (int64_t cell = c0 + (threadIdx.x >> 5); cell < c1; cell += warps) {
+        const uint32_t s = __ldcg(state + cell);
+        const uint32_t c = state_label(s), r = state_sub(s);
+        if (mask && !__ldcg(mask + c)) continue;
+        const int64_t beg = csr.indptr[cell], end = csr.indptr[cell + 1];
+        uint32_t* dst = priv ? sS + (size_t)(2 * c + r) * D : Ssub + (size_t)(2 * c + r) * D;
+        for (int64_t e = beg + lane; e < end; e += 32) {
+            int32_t u, x;
+            csr.get(e, u, x);
+            if (x) atomicAdd(dst + u, (uint32_t)x);
+        }
+        if (lane == 0) atomicAdd(priv ? &sn[2 * c + r] : &nsub[2 * c + r], 1u);
+    }
+    __syncthreads();
+    if (priv) {
+        for (int64_t i = threadIdx.x; i < words; i += blockDim.x) {
+            const uint32_t v = sS[i];
+            if (v) atomicAdd(&Ssub[i], v);
+        }
+        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
+            const uint32_t v = sn[i];
+            if (v) atomicAdd(&nsub[i], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (sweep.cu, moves.cu).
 // ---------------------------------------------------------------------------
 cudaError_t configure_launches(Ctx& c);
 cudaError_t launch_draw_params(Ctx& c);
 cudaError_t launch_assign(Ctx& c);
-cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub,
-                         uint32_t* bump);
+cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub);
 cudaError_t launch_sweep_stats(Ctx& c);
-cudaError_t launch_plan(Ctx& c, int32_t kind);
-cudaError_t launch_apply_plan(Ctx& c, int32_t kind);
+cudaError_t launch_csr_commit(Ctx& c);
+cudaError_t launch_select_engine(Ctx& c);
+cudaError_t launch_plan_apply(Ctx& c, int32_t kind);
+cudaError_t configure_plan_apply(Ctx& c);
 cudaError_t launch_move_score(Ctx& c, int32_t mode);
 cudaError_t launch_lg_table(Ctx& c);
 size_t move_partial_bytes();
@@ -290,7 +394,12 @@ cudaError_t launch_init_state(Ctx& c);
 cudaError_t launch_debug_scores(Ctx& c, const int32_t* cells, int32_t n, float* out);
 cudaError_t configure_tile(Ctx& c);
 cudaError_t launch_tile_assign(Ctx& c, float* dbg);
+cudaError_t launch_build_b(Ctx& c, bool force);
+cudaError_t launch_tile_label(Ctx& c, float* dbg);
+cudaError_t launch_tile_stats(Ctx& c);
 size_t tile_b_bytes(int32_t C);
+int32_t tile_stat_groups(const Ctx& c);
+size_t tile_part_words(const Ctx& c);
 cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, int N, float* C,
                                  int* err);
 

@@ -134,65 +134,72 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return r;
 }
 
-// Chain choice (fair coin on the tag-4 stream unless `mode` fixes it) and, for
-// the merge chain, the random disjoint pairs from sorted tag-5 keys.
-__global__ void __launch_bounds__(kMaxKmax)
-k_move_prep(DevScalars* sc, int32_t* __restrict__ pair_ab, int32_t mode, Stream st) {
-    __shared__ uint32_t keys[kMaxKmax];
-    const int K = sc->K;
-    const uint32_t m = sc->m;
-    int chain = mode;
-    if (mode == 0) chain = word_uniform(st.words(TAG_MOVE, 0u, m, 0u).x) < 0.5f ? 1 : 2;
-    if (threadIdx.x == 0) {
-        sc->chain_sel = chain;
-        sc->n_entries = chain == 1 ? K : K / 2;
-    }
-    if (chain != 2) return;
-    const int k = threadIdx.x;
-    if (k < K) keys[k] = st.words(TAG_PAIR, (uint32_t)k, m, 0u).x;
-    __syncthreads();
-    if (k < K) {
-        int rank = 0;
-        const uint32_t kk = keys[k];
-        for (int j = 0; j < K; ++j) rank += (keys[j] < kk) || (keys[j] == kk && j < k);
-        // rank r joins pair r / 2; the smaller index is a
-        if (rank < 2 * (K / 2)) pair_ab[2 * (rank >> 1) + (rank & 1)] = k;
-    }
-    __syncthreads();
-    if (k < K / 2) {
-        const int x = pair_ab[2 * k], y = pair_ab[2 * k + 1];
-        pair_ab[2 * k] = min(x, y);
-        pair_ab[2 * k + 1] = max(x, y);
-    }
-}
-
 struct MovePartial {
     double acc;
     unsigned long long Ta, Tb;
 };
 
+// Chain choice and proposals of one split/merge call, then their scores.
+//
+// Every block draws the chain (a fair coin on the tag-4 stream unless `mode`
+// fixes it: 1 split, 2 merge); for the merge chain it ranks the K clusters by
+// their tag-5 keys, rank r joining pair r / 2 (the smaller index is a).  Block
+// 0 records the chain, the number of proposals and the pairs for the plan.
+//
 // Per (proposal, gene chunk): each warp sums over its genes the lgamma terms
 // of the Hastings ratio and the two gene totals.  Block b serves proposal
 // b / G, chunk b % G, with G chosen so that proposals x G fills the grid.  The
 // last block to finish a proposal (a ticket counter, no waiting) completes
 // it, its four warps evaluating the count and total terms side by side.
 __global__ void __launch_bounds__(kPartialThreads)
-k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
+k_move_partial(DevScalars* sc, const uint32_t* __restrict__ nsub,
                const uint32_t* __restrict__ Ssub, const double* __restrict__ sumlogq,
-               const int32_t* __restrict__ pair_ab, const double* __restrict__ lg_base,
+               int32_t* __restrict__ pair_ab, const double* __restrict__ lg_base,
                MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
                int32_t* __restrict__ decide, double* __restrict__ log_h, int32_t D,
-               double log_alpha, double beta, double lg_beta, int32_t split_q, Stream st) {
+               double log_alpha, double beta, double lg_beta, int32_t split_q, int32_t mode,
+               Stream st) {
     __shared__ double fin[kPartialWarps][2];
     __shared__ int last;
+    __shared__ uint32_t keys[kMaxKmax];
+    __shared__ int pair_s[2];
     const LgTab tb = lg_tab_view(lg_base);
-    const int E = sc->n_entries;
-    if (E <= 0) return;
-    const bool split = sc->chain_sel == 1;
+    const int K = sc->K;
+    const uint32_t m0 = sc->m;
+    int chain = mode;
+    if (mode == 0) chain = word_uniform(st.words(TAG_MOVE, 0u, m0, 0u).x) < 0.5f ? 1 : 2;
+    const int E = chain == 1 ? K : K / 2;
+    const bool split = chain == 1;
     const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
-    const int G = max(1, min((int)gridDim.x / E, maxG));
+    const int G = E > 0 ? max(1, min((int)gridDim.x / E, maxG)) : 1;
     const int e = blockIdx.x / G, g = blockIdx.x - e * G;
-    if (e >= E) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->chain_sel = chain;
+        sc->n_entries = E;
+    }
+    if (!split && (e < E || blockIdx.x == 0)) {
+        for (int k = threadIdx.x; k < K; k += blockDim.x)
+            keys[k] = st.words(TAG_PAIR, (uint32_t)k, m0, 0u).x;
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            int rank = 0;
+            const uint32_t kk = keys[k];
+            for (int j = 0; j < K; ++j) rank += (keys[j] < kk) || (keys[j] == kk && j < k);
+            if (rank < 2 * E) {
+                if (blockIdx.x == 0) pair_ab[rank] = k;
+                if ((rank >> 1) == e) pair_s[rank & 1] = k;
+            }
+        }
+        __syncthreads();
+        if (blockIdx.x == 0) {
+            for (int p = threadIdx.x; p < E; p += blockDim.x) {
+                const int x = pair_ab[2 * p], y = pair_ab[2 * p + 1];
+                pair_ab[2 * p] = min(x, y);
+                pair_ab[2 * p + 1] = max(x, y);
+            }
+        }
+    }
+    if (E <= 0 || e >= E) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int Dc = (D + G - 1) / G;
     const int u0 = g * Dc, u1 = min(D, u0 + Dc);
@@ -210,7 +217,7 @@ k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ n
                        lg_shift(a + b, beta, lg_beta, tb);
         }
     } else {
-        const int a = pair_ab[2 * e], b = pair_ab[2 * e + 1];
+        const int a = min(pair_s[0], pair_s[1]), b = max(pair_s[0], pair_s[1]);
         const uint32_t* A0 = Ssub + (size_t)(2 * a) * D;
         const uint32_t* B0 = Ssub + (size_t)(2 * b) * D;
         for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
@@ -247,15 +254,15 @@ k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ n
     }
     Ta = warp_sum(Ta);
     Tb = warp_sum(Tb);
-    const uint32_t m = sc->m;
+    const uint32_t m = m0;
     uint32_t na, nb;
     int a = e;
     if (split) {
         na = nsub[2 * e];
         nb = nsub[2 * e + 1];
     } else {
-        a = pair_ab[2 * e];
-        const int b = pair_ab[2 * e + 1];
+        a = min(pair_s[0], pair_s[1]);
+        const int b = max(pair_s[0], pair_s[1]);
         na = nsub[2 * a] + nsub[2 * a + 1];
         nb = nsub[2 * b] + nsub[2 * b + 1];
     }
@@ -307,6 +314,16 @@ k_move_partial(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ n
     }
 }
 
+// Whether the plan must be applied (it changes some label or statistic).  If
+// not, the kernels of the application return at once and the phase is
+// counted here (t or m); otherwise the last of them counts it.
+__device__ __forceinline__ void finish_plan(DevScalars* sc, uint32_t* bump) {
+    const int apply = (sc->any_relabel || sc->any_reinit) ? 1 : 0;
+    sc->apply = apply;
+    if (apply) sc->n_apply += 1u;
+    else *bump += 1u;
+}
+
 // Exclusive prefix sum over the block (blockDim.x = 1024); *total gets the sum.
 __device__ __forceinline__ int block_exclusive_scan(int v, int* tmp, int* total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -335,27 +352,40 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* tmp, int* total)
     return excl;
 }
 
-__global__ void __launch_bounds__(kPlanThreads)
-k_plan(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub, double* __restrict__ sumlogq,
-       uint32_t* __restrict__ acc_nsub, double* __restrict__ acc_sumlogq,
-       const int32_t* __restrict__ decide, const int32_t* __restrict__ pair_ab,
-       uint32_t* __restrict__ lmap, int32_t* __restrict__ desc, uint8_t* __restrict__ reinit,
-       int32_t kmax) {
-    __shared__ int tmp[32];
-    __shared__ uint8_t removed[kMaxKmax];
-    __shared__ int32_t partner[kMaxKmax];
-    __shared__ int32_t into[kMaxKmax];
-    __shared__ int32_t newidx[kMaxKmax];
+// The plan of a sweep's compaction or of a split/merge call (one block of
+// kPlanThreads threads, thread k for cluster k): label map, statistics-gather
+// descriptors and the new n-bar / sum log q of every surviving cluster.
+struct PlanSmem {
+    int tmp[32];
+    uint8_t removed[kMaxKmax];
+    int32_t partner[kMaxKmax];
+    int32_t into[kMaxKmax];
+    int32_t newidx[kMaxKmax];
+};
+
+__device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub,
+                           double* __restrict__ sumlogq, double* __restrict__ acc_sumlogq,
+                           const int32_t* __restrict__ decide,
+                           const int32_t* __restrict__ pair_ab, uint32_t* __restrict__ lmap,
+                           int32_t* __restrict__ desc, uint8_t* __restrict__ reinit,
+                           int32_t kmax, uint32_t* bump, PlanSmem& sm) {
+    int* tmp = sm.tmp;
+    uint8_t* removed = sm.removed;
+    int32_t* partner = sm.partner;
+    int32_t* into = sm.into;
+    int32_t* newidx = sm.newidx;
     const double kLogHalf = -0.69314718055994530942;
     const int K = sc->K;
     const int k = threadIdx.x;
     int total = 0;
     if (kind == PLAN_COMPACT) {
+        // the sweep's counts are in nsub already; compacted in place (every
+        // thread reads its cluster before the scan's first barrier)
         uint32_t n0 = 0, n1 = 0;
         double sq = 0.0;
         if (k < K) {
-            n0 = acc_nsub[2 * k];
-            n1 = acc_nsub[2 * k + 1];
+            n0 = nsub[2 * k];
+            n1 = nsub[2 * k + 1];
             sq = acc_sumlogq[k];
         }
         const bool keep = n0 + n1 > 0;
@@ -363,8 +393,6 @@ k_plan(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub, double* __rest
         const bool reset = keep && n0 + n1 >= 2 && (n0 == 0 || n1 == 0);
         const int any_reset = __syncthreads_or(reset ? 1 : 0);
         if (k < K) {
-            acc_nsub[2 * k] = 0u;
-            acc_nsub[2 * k + 1] = 0u;
             acc_sumlogq[k] = 0.0;
             if (keep) {
                 const uint32_t md = reset ? SUB_COIN : SUB_KEEP;
@@ -384,6 +412,7 @@ k_plan(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub, double* __rest
             sc->K_new = total;
             sc->any_reinit = any_reset;
             sc->any_relabel = (total != K) || any_reset;
+            finish_plan(sc, bump);
         }
         return;
     }
@@ -428,6 +457,7 @@ k_plan(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub, double* __rest
             sc->capacity_rejects += total - A;
             sc->any_reinit = A > 0;
             sc->any_relabel = A > 0;
+            finish_plan(sc, bump);
         }
         return;
     }
@@ -490,8 +520,118 @@ k_plan(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub, double* __rest
         sc->n_accepted = K - total;
         sc->any_reinit = 0;
         sc->any_relabel = total != K;
+        finish_plan(sc, bump);
     }
 }
+
+// Plan and, when it changes something, its application, in one cooperative
+// launch (one block per SM, all co-resident; bounded grid barriers):
+//   block 0 plans (plan_block); barrier; if nothing changes, done (the plan
+//   counted the phase).  Otherwise: main statistics gathered into the
+//   accumulators per the descriptors; barrier; copied back (accumulators
+//   cleared) while each block relabels its contiguous share of the cells
+//   through the label map (SUB_COIN sub-labels are fair coins on the tag-7
+//   stream: step t for a sweep's resets, m after splits); barrier; each block
+//   recounts its share of the cells of re-initialised clusters; block 0
+//   commits K = K_new and counts the phase.
+struct PlanApplyArgs {
+    Csr csr;
+    DevScalars* sc;
+    int32_t kind;
+    uint32_t* nsub;
+    double* sumlogq;
+    double* acc_sumlogq;
+    const int32_t* decide;
+    const int32_t* pair_ab;
+    uint32_t* lmap;
+    int32_t* desc;
+    uint8_t* reinit;
+    uint32_t* Ssub;
+    uint32_t* acc_Ssub;
+    uint32_t* state;
+    GridBar* bar;
+    int64_t N;
+    int32_t D, kmax;
+    int64_t priv_cap;    // words of dynamic shared memory for the recount
+    Stream st;
+};
+
+__global__ void __launch_bounds__(kPlanThreads, 1)
+k_plan_apply(PlanApplyArgs a) {
+    extern __shared__ __align__(16) uint32_t spriv[];
+    __shared__ PlanSmem sm;
+    __shared__ int s_apply, s_Knew;
+    __shared__ uint32_t s_step;
+    const bool compact = a.kind == PLAN_COMPACT;
+    uint32_t* bump = compact ? &a.sc->t : &a.sc->m;
+    if (blockIdx.x == 0)
+        plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq, a.acc_sumlogq,
+                   a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax, bump, sm);
+    if (!grid_sync(a.bar)) {
+        if (threadIdx.x == 0) atomicExch(&a.sc->error, DPMM_ETIMEOUT);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        volatile DevScalars* vs = a.sc;
+        s_apply = vs->apply;
+        s_Knew = vs->K_new;
+        s_step = compact ? vs->t : vs->m;
+    }
+    __syncthreads();
+    if (!s_apply) return;
+    const int Kn = s_Knew;
+    const int D = a.D;
+    const int64_t total = (int64_t)2 * Kn * D;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // (1) rows of the new main statistics, from the old main into the accumulators
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int64_t row = i / D, u = i - row * D;
+        const int32_t d = __ldcg(a.desc + row);
+        const int32_t src = d >> 2, mode = d & 3;
+        uint32_t v = 0u;
+        if (mode == DESC_SUM)
+            v = a.Ssub[(size_t)(2 * src) * D + u] + a.Ssub[(size_t)(2 * src + 1) * D + u];
+        else if (mode != DESC_ZERO)
+            v = a.Ssub[(size_t)(2 * src + mode) * D + u];
+        a.acc_Ssub[i] = v;
+    }
+    if (!grid_sync(a.bar)) {
+        if (threadIdx.x == 0) atomicExch(&a.sc->error, DPMM_ETIMEOUT);
+        return;
+    }
+    // (2) back into main, accumulators cleared; this block's cells relabelled
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        a.Ssub[i] = __ldcg(a.acc_Ssub + i);
+        a.acc_Ssub[i] = 0u;
+    }
+    const uint32_t sub_kind = compact ? SUBINIT_RESET : SUBINIT_SPLIT;
+    const int64_t per = (a.N + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * per, c1 = min(a.N, c0 + per);
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const uint32_t s = a.state[i];
+        const uint32_t e = __ldcg(a.lmap + 2 * state_label(s) + state_sub(s));
+        const uint32_t md = e >> 28;
+        uint32_t sub = state_sub(s);
+        if (md == SUB_SET0) sub = 0u;
+        else if (md == SUB_SET1) sub = 1u;
+        else if (md == SUB_COIN) {
+            const uint4 w = a.st.words(TAG_SUBINIT, (uint32_t)i, s_step, sub_kind);
+            sub = word_uniform(w.x) < 0.5f ? 1u : 0u;
+        }
+        a.state[i] = pack_state(e & 0x0FFFFFFFu, sub);
+    }
+    if (!grid_sync(a.bar)) {
+        if (threadIdx.x == 0) atomicExch(&a.sc->error, DPMM_ETIMEOUT);
+        return;
+    }
+    // (3) re-initialised clusters recounted (their rows were gathered as zeros)
+    stats_cells(a.csr, a.state, a.reinit, a.nsub, a.Ssub, a.N, D, Kn, spriv, a.priv_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.sc->K = Kn;
+        *bump += 1u;
+    }
+}
+
 
 cudaError_t launch_lg_table(Ctx& c) {
     k_lg_table<<<(kLgTable + 255) / 256, 256, 0, c.stream>>>(c.lg_table, c.beta,
@@ -501,22 +641,57 @@ cudaError_t launch_lg_table(Ctx& c) {
 
 cudaError_t launch_move_score(Ctx& c, int32_t mode) {
     const Stream st = make_stream(c.opts.seed, c.opts.chain_id);
-    k_move_prep<<<1, kMaxKmax, 0, c.stream>>>(c.sc, c.pair_ab, mode, st);
     k_move_partial<<<kMaxPartials, kPartialThreads, 0, c.stream>>>(
         c.sc, c.nsub, c.Ssub, c.sumlogq, c.pair_ab, c.lg_table,
         reinterpret_cast<MovePartial*>(c.move_part), c.move_ticket, c.decide, c.log_h, c.D,
-        std::log(c.alpha), c.beta, std::lgamma(c.beta), c.opts.split_q, st);
+        std::log(c.alpha), c.beta, std::lgamma(c.beta), c.opts.split_q, mode, st);
     return cudaGetLastError();
 }
 
 size_t move_partial_bytes() { return sizeof(MovePartial) * kMaxPartials * kPartialWarps; }
 size_t lg_table_entries() { return 3 * (size_t)kLgTable + 2 * kLogTab; }
 
-cudaError_t launch_plan(Ctx& c, int32_t kind) {
-    k_plan<<<1, kPlanThreads, 0, c.stream>>>(c.sc, kind, c.nsub, c.sumlogq, c.acc_nsub,
-                                             c.acc_sumlogq, c.decide, c.pair_ab, c.lmap, c.desc,
-                                             c.reinit, c.kmax);
-    return cudaGetLastError();
+cudaError_t configure_plan_apply(Ctx& c) {
+    // one block per SM, the rest of shared memory for the recount's counters
+    c.apply_blocks = c.num_sms;
+    c.apply_smem = c.smem_optin - sizeof(PlanSmem) - 1024;
+    return cudaFuncSetAttribute(k_plan_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)c.apply_smem);
+}
+
+cudaError_t launch_plan_apply(Ctx& c, int32_t kind) {
+    PlanApplyArgs a;
+    a.csr = csr_of(c);
+    a.sc = c.sc;
+    a.kind = kind;
+    a.nsub = c.nsub;
+    a.sumlogq = c.sumlogq;
+    a.acc_sumlogq = c.acc_sumlogq;
+    a.decide = c.decide;
+    a.pair_ab = c.pair_ab;
+    a.lmap = c.lmap;
+    a.desc = c.desc;
+    a.reinit = c.reinit;
+    a.Ssub = c.Ssub;
+    a.acc_Ssub = c.acc_Ssub;
+    a.state = c.state;
+    a.bar = c.gbar;
+    a.N = c.N;
+    a.D = c.D;
+    a.kmax = c.kmax;
+    a.priv_cap = (int64_t)(c.apply_smem / sizeof(uint32_t));
+    a.st = make_stream(c.opts.seed, c.opts.chain_id);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c.apply_blocks);
+    cfg.blockDim = dim3(kPlanThreads);
+    cfg.dynamicSmemBytes = c.apply_smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_plan_apply, a);
 }
 
 }  // namespace dpmm

@@ -50,16 +50,28 @@ __device__ __forceinline__ float block_reduce_sum(float v, float* red) {
     return r;
 }
 
+// Labelling engine of this sweep: the dense-tile engine when it is built and
+// 1 <= K <= kTileMaxK, else the CSR engine.
+__device__ __forceinline__ void select_engine(DevScalars* sc, int K, int32_t tile_enabled) {
+    sc->tile_used = tile_enabled && K >= 1 && K <= kTileMaxK;
+}
+
+__global__ void k_select_engine(DevScalars* sc, int32_t tile_enabled) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) select_engine(sc, sc->K, tile_enabled);
+}
+
 // Rows 0 .. 3K-1 are theta rows (row 3k + p: cluster k for p = 0, its
 // sub-cluster p - 1 otherwise); row 3K is the pi row.  log G is written to the
 // output slot first, then normalised in place (log theta = log G - logsumexp).
+// Block 0 also selects the labelling engine of the sweep.
 __global__ void __launch_bounds__(kDrawThreads)
-k_draw_params(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ nsub,
+k_draw_params(DevScalars* sc, const uint32_t* __restrict__ nsub,
               const uint32_t* __restrict__ Ssub, float* __restrict__ Lc, float* __restrict__ Ls,
               float* __restrict__ logpi, int32_t D, int32_t kmax, float alpha, float beta,
-              Stream st) {
+              Stream st, int32_t tile_enabled) {
     __shared__ float red[32];
     const int K = sc->K;
+    if (blockIdx.x == 0 && threadIdx.x == 0) select_engine(sc, K, tile_enabled);
     const uint32_t t = sc->t;
     const int rows = 3 * K + 1;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -588,85 +600,26 @@ k_assign(AssignArgs a) {
 // global atomics.  Integer sums: the result is exact and order-independent.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStatsThreads, 1)
-k_stats(Csr csr, const DevScalars* __restrict__ sc_ro, DevScalars* sc_rw,
-        const uint32_t* __restrict__ state, const uint8_t* __restrict__ mask,
-        uint32_t* __restrict__ nsub, uint32_t* __restrict__ Ssub, uint32_t* bump, int64_t N,
-        int32_t D, int64_t priv_cap, int only_if_reinit) {
+k_stats(Csr csr, const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
+        const uint8_t* __restrict__ mask, uint32_t* __restrict__ nsub,
+        uint32_t* __restrict__ Ssub, int64_t N, int32_t D, int64_t priv_cap, int sweep) {
     extern __shared__ __align__(16) uint32_t spriv[];
-    if ((only_if_reinit == 1 && !sc_ro->any_reinit) ||
-        (only_if_reinit == 2 && (sc_ro->stats_fused || sc_ro->tile_used))) {
-        if (bump && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1u;
-        return;
-    }
-    const int K = sc_ro->K;
-    const int64_t words = (int64_t)2 * K * D;
-    const bool priv = words + 2 * K <= priv_cap;
-    uint32_t* sS = spriv;
-    uint32_t* sn = spriv + words;
-    if (priv) {
-        for (int64_t i = threadIdx.x; i < words + 2 * K; i += blockDim.x) spriv[i] = 0u;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int warps = blockDim.x >> 5;
-    // contiguous chunk of cells per block keeps each block's flush sparse
-    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
-    const int64_t c0 = (int64_t)blockIdx.x * per, c1 = min(N, c0 + per);
-    for (int64_t cell = c0 + (threadIdx.x >> 5); cell < c1; cell += warps) {
-        const uint32_t s = state[cell];
-        const uint32_t c = state_label(s), r = state_sub(s);
-        if (mask && !mask[c]) continue;
-        const int64_t beg = csr.indptr[cell], end = csr.indptr[cell + 1];
-        uint32_t* dst = priv ? sS + (size_t)(2 * c + r) * D : Ssub + (size_t)(2 * c + r) * D;
-        for (int64_t e = beg + lane; e < end; e += 32) {
-            int32_t u, x;
-            csr.get(e, u, x);
-            if (x) atomicAdd(dst + u, (uint32_t)x);
-        }
-        if (lane == 0) atomicAdd(priv ? &sn[2 * c + r] : &nsub[2 * c + r], 1u);
-    }
-    __syncthreads();
-    if (priv) {
-        for (int64_t i = threadIdx.x; i < words; i += blockDim.x) {
-            const uint32_t v = sS[i];
-            if (v) atomicAdd(&Ssub[i], v);
-        }
-        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
-            const uint32_t v = sn[i];
-            if (v) atomicAdd(&nsub[i], v);
-        }
-    }
-    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1u;
-    (void)sc_rw;
+    // a sweep's statistics: only when the CSR label kernel did not add them
+    if (sweep && (sc->stats_fused || sc->tile_used)) return;
+    stats_cells(csr, state, mask, nsub, Ssub, N, D, sc->K, spriv, priv_cap);
 }
 
 // ---------------------------------------------------------------------------
-// Plan application.
+// Commit of a CSR-labelled sweep's statistics.
 // ---------------------------------------------------------------------------
-// dst rows (j, r), j < K_new: per desc, from src (single sub-row, sum of both
-// sub-rows of a cluster, or zero).
-__global__ void k_gather_stats(const DevScalars* __restrict__ sc, const int32_t* __restrict__ desc,
-                               const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
-                               int32_t D) {
-    const int64_t total = (int64_t)2 * sc->K_new * D;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = i / D, u = i - row * D;
-        const int32_t d = desc[row];
-        const int32_t s = d >> 2, mode = d & 3;
-        uint32_t v = 0u;
-        if (mode == DESC_SUM)
-            v = src[(size_t)(2 * s) * D + u] + src[(size_t)(2 * s + 1) * D + u];
-        else if (mode != DESC_ZERO)
-            v = src[(size_t)(2 * s + mode) * D + u];
-        dst[i] = v;
-    }
-}
-
-// rows [0, K_rows) of src: copied to dst (if any) and cleared.  K_rows is
-// sc->K (use_new = 0) or sc->K_new (use_new = 1).
+// Rows [0, 2 K_rows) of src (and, if given, the 2 K_rows counts of nsrc):
+// copied to dst / ndst and cleared.  K_rows is sc->K (use_new = 0) or
+// sc->K_new (use_new = 1).  gate 1: only when the pending plan is applied;
+// gate 2: only when the CSR engine labelled the sweep.
 __global__ void k_copy_clear(const DevScalars* __restrict__ sc, uint32_t* __restrict__ src,
-                             uint32_t* __restrict__ dst, int32_t D, int use_new) {
+                             uint32_t* __restrict__ dst, uint32_t* __restrict__ nsrc,
+                             uint32_t* __restrict__ ndst, int32_t D, int use_new, int gate) {
+    if ((gate == 1 && !sc->apply) || (gate == 2 && sc->tile_used)) return;
     const int Kr = use_new ? sc->K_new : sc->K;
     const int64_t total = (int64_t)2 * Kr * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -674,33 +627,11 @@ __global__ void k_copy_clear(const DevScalars* __restrict__ sc, uint32_t* __rest
         if (dst) dst[i] = src[i];
         src[i] = 0u;
     }
-}
-
-// Cell labels through the plan's label map; SUB_COIN sub-labels are fair
-// coins on the tag-7 stream (step t for sweep resets, m after splits).
-// Block 0 commits K = K_new.
-__global__ void k_relabel(DevScalars* sc, const uint32_t* __restrict__ lmap,
-                          uint32_t* __restrict__ state, int64_t N, Stream st, int32_t kind) {
-    const bool work = sc->any_relabel != 0;
-    const uint32_t step = kind == SUBINIT_SPLIT ? sc->m : sc->t;
-    if (work) {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const uint32_t s = state[i];
-            const uint32_t e = lmap[2 * state_label(s) + state_sub(s)];
-            const uint32_t mode = e >> 28;
-            uint32_t sub = state_sub(s);
-            if (mode == SUB_SET0) sub = 0u;
-            else if (mode == SUB_SET1) sub = 1u;
-            else if (mode == SUB_COIN) {
-                const uint4 w = st.words(TAG_SUBINIT, (uint32_t)i, step, (uint32_t)kind);
-                sub = word_uniform(w.x) < 0.5f ? 1u : 0u;
-            }
-            state[i] = pack_state(e & 0x0FFFFFFFu, sub);
+    if (nsrc && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < 2 * Kr; i += blockDim.x) {
+            ndst[i] = nsrc[i];
+            nsrc[i] = 0u;
         }
-    }
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->K = sc->K_new;
 }
 
 __global__ void k_init_state(uint32_t* __restrict__ state, int64_t N, Stream st) {
@@ -783,10 +714,17 @@ cudaError_t launch_draw_params(Ctx& c) {
     const int grid = rows < 2 * c.num_sms ? rows : 2 * c.num_sms;
     k_draw_params<<<grid, kDrawThreads, 0, c.stream>>>(
         c.sc, c.nsub, c.Ssub, c.Lc, c.Ls, c.logpi, c.D, c.kmax, (float)c.alpha, (float)c.beta,
-        make_stream(c.opts.seed, c.opts.chain_id));
+        make_stream(c.opts.seed, c.opts.chain_id), c.tile_enabled ? 1 : 0);
     return cudaGetLastError();
 }
 
+cudaError_t launch_select_engine(Ctx& c) {
+    k_select_engine<<<1, 32, 0, c.stream>>>(c.sc, c.tile_enabled ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// CSR labelling kernel (returns at once when the dense-tile engine labels the
+// sweep); its statistics go to the accumulators, see launch_csr_commit.
 cudaError_t launch_assign(Ctx& c) {
     AssignArgs a;
     a.csr = csr_of(c);
@@ -804,45 +742,31 @@ cudaError_t launch_assign(Ctx& c) {
     a.acc_Ssub = c.acc_Ssub;
     a.smem_bytes = (int64_t)c.assign_smem;
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
-    if (c.tile_enabled) {
-        cudaError_t e = launch_tile_assign(c, nullptr);
-        if (e != cudaSuccess) return e;
-    }
     k_assign<<<c.assign_blocks, kAssignThreads, c.assign_smem, c.stream>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub,
-                         uint32_t* bump) {
+cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub) {
     k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
-        csr_of(c), c.sc, c.sc, c.state, mask, nsub, Ssub, bump, c.N, c.D,
-        (int64_t)(c.stats_smem / sizeof(uint32_t)), mask != nullptr ? 1 : 0);
+        csr_of(c), c.sc, c.state, mask, nsub, Ssub, c.N, c.D,
+        (int64_t)(c.stats_smem / sizeof(uint32_t)), 0);
     return cudaGetLastError();
 }
 
-// Statistics of a sweep's new labels unless the label kernel already added them.
+// Statistics of a CSR-labelled sweep unless the label kernel already added them.
 cudaError_t launch_sweep_stats(Ctx& c) {
     k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
-        csr_of(c), c.sc, c.sc, c.state, nullptr, c.acc_nsub, c.acc_Ssub, nullptr, c.N, c.D,
-        (int64_t)(c.stats_smem / sizeof(uint32_t)), 2);
+        csr_of(c), c.sc, c.state, nullptr, c.acc_nsub, c.acc_Ssub, c.N, c.D,
+        (int64_t)(c.stats_smem / sizeof(uint32_t)), 1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_plan(Ctx& c, int32_t kind) {
-    const int grid = 2 * c.num_sms;
-    const Stream st = make_stream(c.opts.seed, c.opts.chain_id);
-    if (kind == PLAN_COMPACT) {
-        // accumulators -> main (compacted), then clear the accumulators
-        k_gather_stats<<<grid, 256, 0, c.stream>>>(c.sc, c.desc, c.acc_Ssub, c.Ssub, c.D);
-        k_copy_clear<<<grid, 256, 0, c.stream>>>(c.sc, c.acc_Ssub, nullptr, c.D, 0);
-        k_relabel<<<grid, 256, 0, c.stream>>>(c.sc, c.lmap, c.state, c.N, st, SUBINIT_RESET);
-        return launch_stats(c, c.reinit, c.nsub, c.Ssub, &c.sc->t);
-    }
-    // moves: main -> accumulators (rearranged) -> main
-    k_gather_stats<<<grid, 256, 0, c.stream>>>(c.sc, c.desc, c.Ssub, c.acc_Ssub, c.D);
-    k_copy_clear<<<grid, 256, 0, c.stream>>>(c.sc, c.acc_Ssub, c.Ssub, c.D, 1);
-    k_relabel<<<grid, 256, 0, c.stream>>>(c.sc, c.lmap, c.state, c.N, st, SUBINIT_SPLIT);
-    return launch_stats(c, c.reinit, c.nsub, c.Ssub, &c.sc->m);
+// A CSR-labelled sweep's statistics become the main statistics (the dense-tile
+// engine writes them there itself); the accumulators are cleared.
+cudaError_t launch_csr_commit(Ctx& c) {
+    k_copy_clear<<<2 * c.num_sms, 256, 0, c.stream>>>(c.sc, c.acc_Ssub, c.Ssub, c.acc_nsub,
+                                                       c.nsub, c.D, 0, 2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_state(Ctx& c) {

@@ -116,7 +116,6 @@ cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, i
 // ===========================================================================
 
 constexpr int kNtotMax = 256;
-constexpr int kTileMaxK = 40;
 constexpr uint32_t kBChunkBytes = kNtotMax * 128;   // one chunk of B in global memory
 
 __host__ __device__ __forceinline__ bool tile_usable(int K) {
@@ -137,11 +136,12 @@ __device__ __forceinline__ float bf16_value(uint16_t b) {
 // (genes 64c .. 64c + 63); every block of chunk c forms the same m_u.
 __global__ void __launch_bounds__(256)
 k_build_b(const DevScalars* __restrict__ sc, const float* __restrict__ Lc,
-          const float* __restrict__ Ls, unsigned char* __restrict__ B, int32_t D, int32_t kmax) {
+          const float* __restrict__ Ls, unsigned char* __restrict__ B, int32_t D, int32_t kmax,
+          int32_t force) {
     __shared__ float part[4][64];
     __shared__ float m[64];
     const int K = sc->K;
-    if (!tile_usable(K)) return;
+    if (!tile_usable(K) || (!force && !sc->tile_used)) return;
     const int c = blockIdx.x;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
     if ((int)blockIdx.y * 16 >= Ntot) return;
@@ -234,6 +234,7 @@ constexpr int kBLoadWarp = 18;
 constexpr int kTileThreadsP = 19 * 32;
 constexpr int kBarEpi = 1, kBarLabel = 2;
 constexpr int kSmallBytes = 8192;
+constexpr int kScatter = 12;         // entries per producer lane and batch
 
 __global__ void __launch_bounds__(kTileThreadsP, 1)
 k_assign_tc(TileArgs a) {
@@ -242,9 +243,7 @@ k_assign_tc(TileArgs a) {
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int K = a.sc->K;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool use = tile_usable(K);
-    if (!a.dbg && blockIdx.x == 0 && tid == 0) a.sc->tile_used = use ? 1 : 0;
-    if (!use) return;
+    if (!tile_usable(K) || (!a.dbg && !a.sc->tile_used)) return;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
     const uint32_t t = a.sc->t;
     // shared-memory plan (identical in every thread): A stages, B slots,
@@ -367,16 +366,28 @@ k_assign_tc(TileArgs a) {
             const int32_t* mt = meta + 4 * es;
             const int i0 = q ? mt[q - 1] : 0, i1 = mt[q];
             const uint32_t* ring = reinterpret_cast<const uint32_t*>(E_base + es * e_slot);
+            // batches of kScatter entries per lane: all loads first, then the
+            // stores, so that a lane keeps several shared-memory accesses in
+            // flight.  x & 255 and x & 0xFF00 have at most 8 significant bits,
+            // so their FP32 bit patterns truncate exactly to BF16.
             int hi = 0;
-            for (int i = i0 + lane; i < i1; i += 32) {
-                const uint32_t v = ring[i];
-                const uint32_t x = v & 0xFFFFu;
-                if (!x) continue;
-                const uint32_t off = tc::swz_offset(v >> 22, (v >> 16) & 63u);
-                *reinterpret_cast<uint16_t*>(A_lo + off) = bf16_bits_rn((float)(x & 255u));
-                if (x >> 8) {
-                    *reinterpret_cast<uint16_t*>(A_hi + off) = bf16_bits_rn((float)((x >> 8) << 8));
-                    hi = 1;
+            for (int i = i0 + lane; i < i1; i += 32 * kScatter) {
+                uint32_t v[kScatter];
+#pragma unroll
+                for (int u = 0; u < kScatter; ++u) v[u] = i + 32 * u < i1 ? ring[i + 32 * u] : 0u;
+#pragma unroll
+                for (int u = 0; u < kScatter; ++u) {
+                    const uint32_t x = v[u] & 0xFFFFu;
+                    if (x) {
+                        const uint32_t off = tc::swz_offset(v[u] >> 22, (v[u] >> 16) & 63u);
+                        *reinterpret_cast<uint16_t*>(A_lo + off) =
+                            (uint16_t)(__float_as_uint((float)(x & 255u)) >> 16);
+                        if (x >> 8) {
+                            *reinterpret_cast<uint16_t*>(A_hi + off) =
+                                (uint16_t)(__float_as_uint((float)(x & 0xFF00u)) >> 16);
+                            hi = 1;
+                        }
+                    }
                 }
             }
             hi = __any_sync(0xFFFFFFFFu, hi);
@@ -634,33 +645,41 @@ k_assign_tc(TileArgs a) {
     }
 }
 
-// Statistics n-bar[k][r], S-bar[k][r][u] of the labels the dense-tile engine
-// just drew, read from the blocked entries.  Blocks are partitioned by gene
-// chunk: block b takes chunk b % C of every tile t = b / C, b / C + nt, ...
-// (nt tile groups), so its private counters cover only 64 genes ([2K][64]
-// words in shared memory) and its flush adds at most 2K x 64 words.  One warp
-// per (tile, chunk) segment at a time, with the tile's 128 cell states
-// cached in shared memory.  Integer sums, exact.
+// Statistics n-bar[k][r], S-bar[k][r][u] of the sweep's labels (from either
+// engine), read from the blocked entries and STORED as the main statistics
+// (rows 0 .. 2K-1, every gene): nothing needs clearing beforehand.  Blocks are
+// partitioned by gene chunk: block b takes chunk c = b % C of the tiles
+// t = b / C, b / C + nt, ... (nt tile groups), counting into [2K][64] words
+// (one warp per (tile, chunk) segment, the tile's 128 cell states cached):
+// shared memory for K <= kTileMaxK, else the block's own partial slot in
+// global memory.  Each block leaves its counts in its partial slot (pw words);
+// the last block of a chunk to finish (a ticket counter, no waiting) adds the
+// nt partials in a fixed order and stores the chunk's 64 columns.  Integer
+// sums, exact.
 constexpr int kStatsTileThreads = 512;
 
 __global__ void __launch_bounds__(kStatsTileThreads)
 k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
              const uint32_t* __restrict__ ent, const int32_t* __restrict__ ptr, int32_t T,
              int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ nsub,
-             uint32_t* __restrict__ Ssub) {
+             uint32_t* __restrict__ Ssub, uint32_t* __restrict__ part, int64_t pw,
+             int32_t* __restrict__ ticket) {
     __shared__ uint32_t cache[kStatsTileThreads / 32][128];
-    __shared__ uint32_t priv[2 * kTileMaxK * 64];
-    __shared__ uint32_t pn[2 * kTileMaxK];
-    if (!sc->tile_used) return;
+    __shared__ uint32_t spriv[2 * kTileMaxK * 64];
+    __shared__ uint32_t spn[2 * kTileMaxK];
+    __shared__ int last;
     const int K = sc->K;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
     if (tg >= nt) return;
+    uint32_t* mine = part + (size_t)blockIdx.x * pw;
+    const bool in_smem = K <= kTileMaxK;
+    uint32_t* priv = in_smem ? spriv : mine;
+    uint32_t* pn = in_smem ? spn : mine + 2 * K * 64;
     for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) priv[i] = 0u;
     for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) pn[i] = 0u;
     __syncthreads();
     uint32_t* my = cache[w];
-    const int gene0 = c * 64;
     for (int tile = tg + nt * w; tile < T; tile += nt * nw) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -687,12 +706,38 @@ k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ sta
         __syncwarp();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) {
-        const int g = i & 63, u = gene0 + g;
-        if (priv[i] && u < D) atomicAdd(&Ssub[(size_t)(i >> 6) * D + u], priv[i]);
+    if (in_smem) {
+        for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) mine[i] = priv[i];
+        if (c == 0)
+            for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) mine[2 * K * 64 + i] = pn[i];
     }
-    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
-        if (pn[i]) atomicAdd(&nsub[i], pn[i]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ticket[c], 1) == nt - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // partial slots of chunk c: blocks c, c + C, c + 2C, ...
+    for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) {
+        uint32_t v = 0u;
+        for (int g = 0; g < nt; ++g) v += __ldcg(part + (size_t)(c + g * C) * pw + i);
+        const int u = c * 64 + (i & 63);
+        if (u < D) Ssub[(size_t)(i >> 6) * D + u] = v;
+    }
+    if (c == 0)
+        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
+            uint32_t v = 0u;
+            for (int g = 0; g < nt; ++g)
+                v += __ldcg(part + (size_t)(g * C) * pw + 2 * K * 64 + i);
+            nsub[i] = v;
+        }
+    if (threadIdx.x == 0) ticket[c] = 0;
+}
+
+int32_t tile_stat_groups(const Ctx& c) { return max(1, (2 * c.num_sms) / c.tile_C); }
+static int64_t tile_part_slot(const Ctx& c) { return (int64_t)2 * c.kmax * 64 + 2 * c.kmax; }
+size_t tile_part_words(const Ctx& c) {
+    return (size_t)tile_stat_groups(c) * c.tile_C * (size_t)tile_part_slot(c);
 }
 
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
@@ -702,9 +747,13 @@ cudaError_t configure_tile(Ctx& c) {
                                 (int)c.smem_optin);
 }
 
-cudaError_t launch_tile_assign(Ctx& c, float* dbg) {
+cudaError_t launch_build_b(Ctx& c, bool force) {
     k_build_b<<<dim3(c.tile_C, kNtotMax / 16), 256, 0, c.stream>>>(c.sc, c.Lc, c.Ls, c.tile_B,
-                                                                     c.D, c.kmax);
+                                                                     c.D, c.kmax, force ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_label(Ctx& c, float* dbg) {
     TileArgs a;
     a.ent = c.tile_ent;
     a.ptr = c.tile_ptr;
@@ -724,13 +773,24 @@ cudaError_t launch_tile_assign(Ctx& c, float* dbg) {
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
     const int grid = c.tile_T < c.num_sms ? c.tile_T : c.num_sms;
     k_assign_tc<<<grid, kTileThreadsP, c.smem_optin, c.stream>>>(a);
-    if (!dbg) {
-        const int nt = max(1, (2 * c.num_sms) / c.tile_C);   // tile groups per gene chunk
-        k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(
-            c.sc, c.state, c.tile_ent, c.tile_ptr, c.tile_T, c.tile_C, c.N, c.D, c.acc_nsub,
-            c.acc_Ssub);
-    }
     return cudaGetLastError();
+}
+
+cudaError_t launch_tile_stats(Ctx& c) {
+    const int nt = tile_stat_groups(c);   // tile groups per gene chunk
+    k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(
+        c.sc, c.state, c.tile_ent, c.tile_ptr, c.tile_T, c.tile_C, c.N, c.D, c.nsub, c.Ssub,
+        c.tile_part, tile_part_slot(c), c.tile_ticket);
+    return cudaGetLastError();
+}
+
+// The whole dense-tile labelling: B operand, labels, statistics (dbg: scores
+// only, no state or statistics writes).
+cudaError_t launch_tile_assign(Ctx& c, float* dbg) {
+    cudaError_t e = launch_build_b(c, dbg != nullptr);
+    if (e == cudaSuccess) e = launch_tile_label(c, dbg);
+    if (e == cudaSuccess && !dbg) e = launch_tile_stats(c);
+    return e;
 }
 
 }  // namespace dpmm
