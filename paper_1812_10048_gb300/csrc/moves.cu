@@ -525,9 +525,12 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
 }
 
 // Plan and, when it changes something, its application, in one cooperative
-// launch (one block per SM, all co-resident; bounded grid barriers):
-//   block 0 plans (plan_block); barrier; if nothing changes, done (the plan
-//   counted the phase).  Otherwise: main statistics gathered into the
+// launch (one block per SM, all co-resident; bounded grid barriers).  Every
+// block first decides from the same inputs whether the plan changes anything
+// (an empty cluster or a sub-cluster reset; an accepted split with room left;
+// an accepted merge).  If not, block 0 plans (plan_block, which counts the
+// phase) and every other block returns at once.  Otherwise block 0 plans;
+//   barrier; main statistics gathered into the
 //   accumulators per the descriptors; barrier; copied back (accumulators
 //   cleared) while each block relabels its contiguous share of the cells
 //   through the label map (SUB_COIN sub-labels are fair coins on the tag-7
@@ -564,6 +567,28 @@ k_plan_apply(PlanApplyArgs a) {
     __shared__ uint32_t s_step;
     const bool compact = a.kind == PLAN_COMPACT;
     uint32_t* bump = compact ? &a.sc->t : &a.sc->m;
+    {
+        const int K = a.sc->K;
+        int change = 0;
+        if (compact) {
+            for (int k = threadIdx.x; k < K; k += blockDim.x) {
+                const uint32_t n0 = a.nsub[2 * k], n1 = a.nsub[2 * k + 1];
+                change |= (n0 + n1 == 0u) || (n0 + n1 >= 2u && (n0 == 0u || n1 == 0u));
+            }
+        } else if (a.sc->chain_sel == 1) {
+            if (K < a.kmax)
+                for (int k = threadIdx.x; k < K; k += blockDim.x) change |= a.decide[k] != 0;
+        } else {
+            for (int k = threadIdx.x; k < K / 2; k += blockDim.x) change |= a.decide[k] != 0;
+        }
+        if (!__syncthreads_or(change)) {
+            if (blockIdx.x == 0)
+                plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq,
+                           a.acc_sumlogq, a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax,
+                           bump, sm);
+            return;
+        }
+    }
     if (blockIdx.x == 0)
         plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq, a.acc_sumlogq,
                    a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax, bump, sm);

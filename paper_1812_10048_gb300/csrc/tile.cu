@@ -658,28 +658,20 @@ k_assign_tc(TileArgs a) {
 // sums, exact.
 constexpr int kStatsTileThreads = 512;
 
-__global__ void __launch_bounds__(kStatsTileThreads)
-k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
-             const uint32_t* __restrict__ ent, const int32_t* __restrict__ ptr, int32_t T,
-             int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ nsub,
-             uint32_t* __restrict__ Ssub, uint32_t* __restrict__ part, int64_t pw,
-             int32_t* __restrict__ ticket) {
-    __shared__ uint32_t cache[kStatsTileThreads / 32][128];
-    __shared__ uint32_t spriv[2 * kTileMaxK * 64];
-    __shared__ uint32_t spn[2 * kTileMaxK];
-    __shared__ int last;
-    const int K = sc->K;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
-    if (tg >= nt) return;
-    uint32_t* mine = part + (size_t)blockIdx.x * pw;
-    const bool in_smem = K <= kTileMaxK;
-    uint32_t* priv = in_smem ? spriv : mine;
-    uint32_t* pn = in_smem ? spn : mine + 2 * K * 64;
+// Counts of the (tile, chunk c) segments of tile group tg into priv [2K][64]
+// and, for c == 0, the cell counts into pn [2K] (both zeroed here); priv / pn
+// are either shared memory or the block's global partial slot (separate
+// instantiations keep the shared-memory atomics native).
+template <typename T_>
+__device__ __forceinline__ void count_segments(T_* priv, T_* pn, uint32_t* my,
+                                               const uint32_t* __restrict__ state,
+                                               const uint32_t* __restrict__ ent,
+                                               const int32_t* __restrict__ ptr, int32_t T,
+                                               int32_t C, int64_t N, int K, int c, int tg, int nt,
+                                               int lane, int w, int nw) {
     for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) priv[i] = 0u;
     for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) pn[i] = 0u;
     __syncthreads();
-    uint32_t* my = cache[w];
     for (int tile = tg + nt * w; tile < T; tile += nt * nw) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -706,10 +698,31 @@ k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ sta
         __syncwarp();
     }
     __syncthreads();
-    if (in_smem) {
-        for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) mine[i] = priv[i];
+}
+
+__global__ void __launch_bounds__(kStatsTileThreads)
+k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
+             const uint32_t* __restrict__ ent, const int32_t* __restrict__ ptr, int32_t T,
+             int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ nsub,
+             uint32_t* __restrict__ Ssub, uint32_t* __restrict__ part, int64_t pw,
+             int32_t* __restrict__ ticket) {
+    __shared__ uint32_t cache[kStatsTileThreads / 32][128];
+    __shared__ uint32_t spriv[2 * kTileMaxK * 64];
+    __shared__ uint32_t spn[2 * kTileMaxK];
+    __shared__ int last;
+    const int K = sc->K;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
+    if (tg >= nt) return;
+    uint32_t* mine = part + (size_t)blockIdx.x * pw;
+    if (K <= kTileMaxK) {
+        count_segments(spriv, spn, cache[w], state, ent, ptr, T, C, N, K, c, tg, nt, lane, w, nw);
+        for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) mine[i] = spriv[i];
         if (c == 0)
-            for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) mine[2 * K * 64 + i] = pn[i];
+            for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) mine[2 * K * 64 + i] = spn[i];
+    } else {
+        count_segments(mine, mine + 2 * K * 64, cache[w], state, ent, ptr, T, C, N, K, c, tg, nt,
+                       lane, w, nw);
     }
     __threadfence();
     __syncthreads();
@@ -720,6 +733,7 @@ k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ sta
     // partial slots of chunk c: blocks c, c + C, c + 2C, ...
     for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) {
         uint32_t v = 0u;
+#pragma unroll 8
         for (int g = 0; g < nt; ++g) v += __ldcg(part + (size_t)(c + g * C) * pw + i);
         const int u = c * 64 + (i & 63);
         if (u < D) Ssub[(size_t)(i >> 6) * D + u] = v;
@@ -727,6 +741,7 @@ k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ sta
     if (c == 0)
         for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
             uint32_t v = 0u;
+#pragma unroll 8
             for (int g = 0; g < nt; ++g)
                 v += __ldcg(part + (size_t)(g * C) * pw + 2 * K * 64 + i);
             nsub[i] = v;

@@ -355,6 +355,19 @@ def test_assign_parity_across_kernel_variants(P, tiny, K):
     """Every label-kernel variant (lanes per column P = 4..32 with and without spare
     lanes, fused and separate statistics, shared-memory and global tables for K > 32)
     against the oracle from an injected state and injected parameters."""
+    _assign_parity(P, tiny, K, P.ENGINE_CSR_FP32)
+
+
+@pytest.mark.parametrize("K", [41, 57, 120])
+def test_tile_configuration_above_40_clusters(P, tiny, K):
+    """With the dense-tile engine built but K > 40, the CSR kernel labels the cells
+    and the tile statistics kernel counts them from the blocked copy through its
+    global-memory partial slots: labels as in the CSR configuration, statistics
+    exact."""
+    _assign_parity(P, tiny, K, P.ENGINE_AUTO)
+
+
+def _assign_parity(P, tiny, K, engine):
     from oracle.sampler import Sampler as OracleSampler, sufficient_stats
     rng = np.random.default_rng(K)
     labels = rng.integers(0, K, size=tiny.N)
@@ -364,7 +377,7 @@ def test_assign_parity_across_kernel_variants(P, tiny, K):
                       kmax=128)
     o.set_state(labels, sub, K, t=5, m=2)
     g = P.Sampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, kmax=128, seed=17,
-                  engine=P.ENGINE_CSR_FP32)
+                  engine=engine)
     P.dpmm_set_state(g.ctx, o.labels, o.sub, o.K, o.t, o.m, o.sumlogq)
     P.dpmm_draw_params(g.ctx)
     logpi32, logtheta32 = P.dpmm_get_params(g.ctx, K, tiny.D)
