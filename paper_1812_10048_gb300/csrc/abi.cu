@@ -105,7 +105,7 @@ void free_ctx(Ctx& c) {
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
                     c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
                     c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B,
-                    c.tile_part, c.tile_ticket, c.gbar};
+                    c.gbar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.sc_host) cudaFreeHost(c.sc_host);
@@ -381,10 +381,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         CKI(dalloc(&c.tile_ent, (size_t)pos));
         CKI(dalloc(&c.tile_ptr, 4 * TC + 1));
         CKI(dalloc(&c.tile_B, tile_b_bytes(c.tile_C)));
-        c.tile_nt = tile_stat_groups(c);
-        CKI(dalloc(&c.tile_part, tile_part_words(c)));
-        CKI(dalloc(&c.tile_ticket, (size_t)c.tile_C));
-        CKI(cudaMemsetAsync(c.tile_ticket, 0, sizeof(int32_t) * c.tile_C, c.stream));
+
         CKI(cudaMemcpyAsync(c.tile_ptr, tptr.data(), sizeof(int32_t) * (4 * TC + 1),
                             cudaMemcpyHostToDevice, c.stream));
         if (pos)

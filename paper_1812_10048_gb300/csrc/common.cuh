@@ -154,9 +154,6 @@ struct Ctx {
     int32_t* tile_ptr = nullptr;    // [4 T C + 1] quarter starts
     unsigned char* tile_B = nullptr;  // per-sweep BF16 hi/lo table, [C][256 rows][64] swizzled
 
-    uint32_t* tile_part = nullptr;  // per-block partial statistics of the tile engine
-    int32_t* tile_ticket = nullptr; // [C] finished blocks per gene chunk (reset to 0)
-    int32_t tile_nt = 0;            // tile groups per gene chunk in the statistics kernel
 
     // plan + application kernel (cooperative, one block per SM)
     GridBar* gbar = nullptr;
@@ -399,7 +396,6 @@ cudaError_t launch_tile_label(Ctx& c, float* dbg);
 cudaError_t launch_tile_stats(Ctx& c);
 size_t tile_b_bytes(int32_t C);
 int32_t tile_stat_groups(const Ctx& c);
-size_t tile_part_words(const Ctx& c);
 cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, int N, float* C,
                                  int* err);
 

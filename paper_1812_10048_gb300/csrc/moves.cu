@@ -364,7 +364,8 @@ struct PlanSmem {
 };
 
 __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub,
-                           double* __restrict__ sumlogq, double* __restrict__ acc_sumlogq,
+                           double* __restrict__ sumlogq, uint32_t* __restrict__ acc_nsub,
+                           double* __restrict__ acc_sumlogq,
                            const int32_t* __restrict__ decide,
                            const int32_t* __restrict__ pair_ab, uint32_t* __restrict__ lmap,
                            int32_t* __restrict__ desc, uint8_t* __restrict__ reinit,
@@ -379,13 +380,14 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
     const int k = threadIdx.x;
     int total = 0;
     if (kind == PLAN_COMPACT) {
-        // the sweep's counts are in nsub already; compacted in place (every
-        // thread reads its cluster before the scan's first barrier)
+        // the sweep's counts are in the accumulators; the main n-bar gets them
+        // compacted (the accumulators are cleared at the next sweep's start, so
+        // that every block of k_plan_apply reads them unchanged)
         uint32_t n0 = 0, n1 = 0;
         double sq = 0.0;
         if (k < K) {
-            n0 = nsub[2 * k];
-            n1 = nsub[2 * k + 1];
+            n0 = acc_nsub[2 * k];
+            n1 = acc_nsub[2 * k + 1];
             sq = acc_sumlogq[k];
         }
         const bool keep = n0 + n1 > 0;
@@ -393,7 +395,6 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
         const bool reset = keep && n0 + n1 >= 2 && (n0 == 0 || n1 == 0);
         const int any_reset = __syncthreads_or(reset ? 1 : 0);
         if (k < K) {
-            acc_sumlogq[k] = 0.0;
             if (keep) {
                 const uint32_t md = reset ? SUB_COIN : SUB_KEEP;
                 lmap[2 * k] = lmap_entry((uint32_t)j, md);
@@ -543,6 +544,7 @@ struct PlanApplyArgs {
     int32_t kind;
     uint32_t* nsub;
     double* sumlogq;
+    uint32_t* acc_nsub;
     double* acc_sumlogq;
     const int32_t* decide;
     const int32_t* pair_ab;
@@ -572,7 +574,7 @@ k_plan_apply(PlanApplyArgs a) {
         int change = 0;
         if (compact) {
             for (int k = threadIdx.x; k < K; k += blockDim.x) {
-                const uint32_t n0 = a.nsub[2 * k], n1 = a.nsub[2 * k + 1];
+                const uint32_t n0 = a.acc_nsub[2 * k], n1 = a.acc_nsub[2 * k + 1];
                 change |= (n0 + n1 == 0u) || (n0 + n1 >= 2u && (n0 == 0u || n1 == 0u));
             }
         } else if (a.sc->chain_sel == 1) {
@@ -584,13 +586,14 @@ k_plan_apply(PlanApplyArgs a) {
         if (!__syncthreads_or(change)) {
             if (blockIdx.x == 0)
                 plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq,
-                           a.acc_sumlogq, a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax,
+                           a.acc_nsub, a.acc_sumlogq, a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax,
                            bump, sm);
             return;
         }
     }
     if (blockIdx.x == 0)
-        plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq, a.acc_sumlogq,
+        plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq, a.acc_nsub,
+                   a.acc_sumlogq,
                    a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax, bump, sm);
     if (!grid_sync(a.bar)) {
         if (threadIdx.x == 0) atomicExch(&a.sc->error, DPMM_ETIMEOUT);
@@ -691,6 +694,7 @@ cudaError_t launch_plan_apply(Ctx& c, int32_t kind) {
     a.kind = kind;
     a.nsub = c.nsub;
     a.sumlogq = c.sumlogq;
+    a.acc_nsub = c.acc_nsub;
     a.acc_sumlogq = c.acc_sumlogq;
     a.decide = c.decide;
     a.pair_ab = c.pair_ab;

@@ -56,22 +56,38 @@ __device__ __forceinline__ void select_engine(DevScalars* sc, int K, int32_t til
     sc->tile_used = tile_enabled && K >= 1 && K <= kTileMaxK;
 }
 
-__global__ void k_select_engine(DevScalars* sc, int32_t tile_enabled) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) select_engine(sc, sc->K, tile_enabled);
+// The sweep's n-bar and sum log q accumulators start at zero (they are added
+// into by the label and statistics kernels and read by the compaction).
+__device__ __forceinline__ void clear_accumulators(int K, uint32_t* acc_nsub,
+                                                   double* acc_sumlogq) {
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) acc_nsub[i] = 0u;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) acc_sumlogq[i] = 0.0;
+}
+
+__global__ void k_select_engine(DevScalars* sc, int32_t tile_enabled, uint32_t* acc_nsub,
+                                double* acc_sumlogq) {
+    const int K = sc->K;
+    if (threadIdx.x == 0) select_engine(sc, K, tile_enabled);
+    clear_accumulators(K, acc_nsub, acc_sumlogq);
 }
 
 // Rows 0 .. 3K-1 are theta rows (row 3k + p: cluster k for p = 0, its
 // sub-cluster p - 1 otherwise); row 3K is the pi row.  log G is written to the
 // output slot first, then normalised in place (log theta = log G - logsumexp).
-// Block 0 also selects the labelling engine of the sweep.
+// Block 0 also selects the labelling engine of the sweep and clears the
+// accumulators of n-bar and sum log q.
 __global__ void __launch_bounds__(kDrawThreads)
 k_draw_params(DevScalars* sc, const uint32_t* __restrict__ nsub,
               const uint32_t* __restrict__ Ssub, float* __restrict__ Lc, float* __restrict__ Ls,
               float* __restrict__ logpi, int32_t D, int32_t kmax, float alpha, float beta,
-              Stream st, int32_t tile_enabled) {
+              Stream st, int32_t tile_enabled, uint32_t* __restrict__ acc_nsub,
+              double* __restrict__ acc_sumlogq) {
     __shared__ float red[32];
     const int K = sc->K;
-    if (blockIdx.x == 0 && threadIdx.x == 0) select_engine(sc, K, tile_enabled);
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) select_engine(sc, K, tile_enabled);
+        clear_accumulators(K, acc_nsub, acc_sumlogq);
+    }
     const uint32_t t = sc->t;
     const int rows = 3 * K + 1;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -714,12 +730,14 @@ cudaError_t launch_draw_params(Ctx& c) {
     const int grid = rows < 2 * c.num_sms ? rows : 2 * c.num_sms;
     k_draw_params<<<grid, kDrawThreads, 0, c.stream>>>(
         c.sc, c.nsub, c.Ssub, c.Lc, c.Ls, c.logpi, c.D, c.kmax, (float)c.alpha, (float)c.beta,
-        make_stream(c.opts.seed, c.opts.chain_id), c.tile_enabled ? 1 : 0);
+        make_stream(c.opts.seed, c.opts.chain_id), c.tile_enabled ? 1 : 0, c.acc_nsub,
+        c.acc_sumlogq);
     return cudaGetLastError();
 }
 
 cudaError_t launch_select_engine(Ctx& c) {
-    k_select_engine<<<1, 32, 0, c.stream>>>(c.sc, c.tile_enabled ? 1 : 0);
+    k_select_engine<<<1, 256, 0, c.stream>>>(c.sc, c.tile_enabled ? 1 : 0, c.acc_nsub,
+                                              c.acc_sumlogq);
     return cudaGetLastError();
 }
 
@@ -761,11 +779,12 @@ cudaError_t launch_sweep_stats(Ctx& c) {
     return cudaGetLastError();
 }
 
-// A CSR-labelled sweep's statistics become the main statistics (the dense-tile
-// engine writes them there itself); the accumulators are cleared.
+// A CSR-labelled sweep's S-bar becomes the main S-bar (the dense-tile
+// configuration adds it there itself); the accumulator is cleared.  n-bar stays
+// in the accumulator for the compaction.
 cudaError_t launch_csr_commit(Ctx& c) {
-    k_copy_clear<<<2 * c.num_sms, 256, 0, c.stream>>>(c.sc, c.acc_Ssub, c.Ssub, c.acc_nsub,
-                                                       c.nsub, c.D, 0, 2);
+    k_copy_clear<<<2 * c.num_sms, 256, 0, c.stream>>>(c.sc, c.acc_Ssub, c.Ssub, nullptr,
+                                                       nullptr, c.D, 0, 2);
     return cudaGetLastError();
 }
 

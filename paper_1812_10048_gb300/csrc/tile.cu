@@ -133,14 +133,24 @@ __device__ __forceinline__ float bf16_value(uint16_t b) {
 }
 
 // B operand of one sweep: block (c, q) fills rows 16q .. 16q + 15 of chunk c
-// (genes 64c .. 64c + 63); every block of chunk c forms the same m_u.
+// (genes 64c .. 64c + 63); every block of chunk c forms the same m_u.  In a
+// step (force = 0) the blocks first clear the main S-bar rows.
 __global__ void __launch_bounds__(256)
 k_build_b(const DevScalars* __restrict__ sc, const float* __restrict__ Lc,
           const float* __restrict__ Ls, unsigned char* __restrict__ B, int32_t D, int32_t kmax,
-          int32_t force) {
+          uint32_t* __restrict__ Ssub, int32_t force) {
     __shared__ float part[4][64];
     __shared__ float m[64];
     const int K = sc->K;
+    if (!force) {
+        // the main S-bar rows are dead from here until the statistics kernel
+        // adds this sweep's counts into them: clear rows 0 .. 2K-1
+        const int64_t words = (int64_t)2 * K * D;
+        const int64_t nthr = (int64_t)gridDim.x * gridDim.y * blockDim.x;
+        for (int64_t i = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+             i < words; i += nthr)
+            Ssub[i] = 0u;
+    }
     if (!tile_usable(K) || (!force && !sc->tile_used)) return;
     const int c = blockIdx.x;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
@@ -646,32 +656,23 @@ k_assign_tc(TileArgs a) {
 }
 
 // Statistics n-bar[k][r], S-bar[k][r][u] of the sweep's labels (from either
-// engine), read from the blocked entries and STORED as the main statistics
-// (rows 0 .. 2K-1, every gene): nothing needs clearing beforehand.  Blocks are
-// partitioned by gene chunk: block b takes chunk c = b % C of the tiles
-// t = b / C, b / C + nt, ... (nt tile groups), counting into [2K][64] words
-// (one warp per (tile, chunk) segment, the tile's 128 cell states cached):
-// shared memory for K <= kTileMaxK, else the block's own partial slot in
-// global memory.  Each block leaves its counts in its partial slot (pw words);
-// the last block of a chunk to finish (a ticket counter, no waiting) adds the
-// nt partials in a fixed order and stores the chunk's 64 columns.  Integer
-// sums, exact.
+// engine), read from the blocked entries: S-bar added into the main rows
+// (cleared by k_build_b), n-bar into the accumulator nsub (the compaction
+// moves it into the main one).  Blocks are partitioned by gene chunk: block b
+// takes chunk c = b % C of the tiles t = b / C, b / C + nt, ... (nt tile
+// groups), so its private counters cover only 64 genes ([2K][64] words in
+// shared memory; K > kTileMaxK counts straight into global memory) and its
+// flush adds at most 2K x 64 words.  One warp per (tile, chunk) segment at a
+// time, with the tile's 128 cell states cached.  Integer sums, exact.
 constexpr int kStatsTileThreads = 512;
 
-// Counts of the (tile, chunk c) segments of tile group tg into priv [2K][64]
-// and, for c == 0, the cell counts into pn [2K] (both zeroed here); priv / pn
-// are either shared memory or the block's global partial slot (separate
-// instantiations keep the shared-memory atomics native).
 template <typename T_>
-__device__ __forceinline__ void count_segments(T_* priv, T_* pn, uint32_t* my,
+__device__ __forceinline__ void count_segments(T_* priv, int ld, uint32_t* pn, uint32_t* my,
                                                const uint32_t* __restrict__ state,
                                                const uint32_t* __restrict__ ent,
                                                const int32_t* __restrict__ ptr, int32_t T,
-                                               int32_t C, int64_t N, int K, int c, int tg, int nt,
+                                               int32_t C, int64_t N, int c, int tg, int nt,
                                                int lane, int w, int nw) {
-    for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) priv[i] = 0u;
-    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) pn[i] = 0u;
-    __syncthreads();
     for (int tile = tg + nt * w; tile < T; tile += nt * nw) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -692,68 +693,49 @@ __device__ __forceinline__ void count_segments(T_* priv, T_* pn, uint32_t* my,
                 const uint32_t x = v[j] & 0xFFFFu;
                 if (!x) continue;
                 const uint32_t st = my[v[j] >> 22];
-                atomicAdd(&priv[(2 * state_label(st) + state_sub(st)) * 64 + ((v[j] >> 16) & 63u)], x);
+                atomicAdd(&priv[(size_t)(2 * state_label(st) + state_sub(st)) * ld +
+                                ((v[j] >> 16) & 63u)],
+                          x);
             }
         }
         __syncwarp();
     }
-    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kStatsTileThreads)
 k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
              const uint32_t* __restrict__ ent, const int32_t* __restrict__ ptr, int32_t T,
-             int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ nsub,
-             uint32_t* __restrict__ Ssub, uint32_t* __restrict__ part, int64_t pw,
-             int32_t* __restrict__ ticket) {
+             int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ acc_nsub,
+             uint32_t* __restrict__ Ssub) {
     __shared__ uint32_t cache[kStatsTileThreads / 32][128];
-    __shared__ uint32_t spriv[2 * kTileMaxK * 64];
-    __shared__ uint32_t spn[2 * kTileMaxK];
-    __shared__ int last;
+    __shared__ uint32_t priv[2 * kTileMaxK * 64];
+    __shared__ uint32_t pn[2 * kTileMaxK];
     const int K = sc->K;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
     if (tg >= nt) return;
-    uint32_t* mine = part + (size_t)blockIdx.x * pw;
-    if (K <= kTileMaxK) {
-        count_segments(spriv, spn, cache[w], state, ent, ptr, T, C, N, K, c, tg, nt, lane, w, nw);
-        for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) mine[i] = spriv[i];
-        if (c == 0)
-            for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) mine[2 * K * 64 + i] = spn[i];
-    } else {
-        count_segments(mine, mine + 2 * K * 64, cache[w], state, ent, ptr, T, C, N, K, c, tg, nt,
+    const int gene0 = c * 64;
+    if (K > kTileMaxK) {
+        // counts straight into the main rows (global atomics)
+        count_segments(Ssub + gene0, D, acc_nsub, cache[w], state, ent, ptr, T, C, N, c, tg, nt,
                        lane, w, nw);
+        return;
     }
-    __threadfence();
+    for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) priv[i] = 0u;
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) pn[i] = 0u;
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&ticket[c], 1) == nt - 1;
+    count_segments(priv, 64, pn, cache[w], state, ent, ptr, T, C, N, c, tg, nt, lane, w, nw);
     __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // partial slots of chunk c: blocks c, c + C, c + 2C, ...
     for (int i = threadIdx.x; i < 2 * K * 64; i += blockDim.x) {
-        uint32_t v = 0u;
-#pragma unroll 8
-        for (int g = 0; g < nt; ++g) v += __ldcg(part + (size_t)(c + g * C) * pw + i);
-        const int u = c * 64 + (i & 63);
-        if (u < D) Ssub[(size_t)(i >> 6) * D + u] = v;
+        const int u = gene0 + (i & 63);
+        if (priv[i] && u < D) atomicAdd(&Ssub[(size_t)(i >> 6) * D + u], priv[i]);
     }
     if (c == 0)
-        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
-            uint32_t v = 0u;
-#pragma unroll 8
-            for (int g = 0; g < nt; ++g)
-                v += __ldcg(part + (size_t)(g * C) * pw + 2 * K * 64 + i);
-            nsub[i] = v;
-        }
-    if (threadIdx.x == 0) ticket[c] = 0;
+        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x)
+            if (pn[i]) atomicAdd(&acc_nsub[i], pn[i]);
 }
 
 int32_t tile_stat_groups(const Ctx& c) { return max(1, (2 * c.num_sms) / c.tile_C); }
-static int64_t tile_part_slot(const Ctx& c) { return (int64_t)2 * c.kmax * 64 + 2 * c.kmax; }
-size_t tile_part_words(const Ctx& c) {
-    return (size_t)tile_stat_groups(c) * c.tile_C * (size_t)tile_part_slot(c);
-}
 
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
 
@@ -763,8 +745,8 @@ cudaError_t configure_tile(Ctx& c) {
 }
 
 cudaError_t launch_build_b(Ctx& c, bool force) {
-    k_build_b<<<dim3(c.tile_C, kNtotMax / 16), 256, 0, c.stream>>>(c.sc, c.Lc, c.Ls, c.tile_B,
-                                                                     c.D, c.kmax, force ? 1 : 0);
+    k_build_b<<<dim3(c.tile_C, kNtotMax / 16), 256, 0, c.stream>>>(
+        c.sc, c.Lc, c.Ls, c.tile_B, c.D, c.kmax, c.Ssub, force ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -794,8 +776,7 @@ cudaError_t launch_tile_label(Ctx& c, float* dbg) {
 cudaError_t launch_tile_stats(Ctx& c) {
     const int nt = tile_stat_groups(c);   // tile groups per gene chunk
     k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(
-        c.sc, c.state, c.tile_ent, c.tile_ptr, c.tile_T, c.tile_C, c.N, c.D, c.nsub, c.Ssub,
-        c.tile_part, tile_part_slot(c), c.tile_ticket);
+        c.sc, c.state, c.tile_ent, c.tile_ptr, c.tile_T, c.tile_C, c.N, c.D, c.acc_nsub, c.Ssub);
     return cudaGetLastError();
 }
 
