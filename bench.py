@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--engine", default="both", choices=["both", "csr_fp32"])
+    ap.add_argument("--engine", default="both", choices=["both", "bf16", "csr_fp32"],
+                    help="forms to time (profiling runs use one)")
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -284,6 +285,8 @@ def run_ours(args, rank, world, local):
     engines = {"bf16": P.ENGINE_AUTO, "fp32": P.ENGINE_CSR_FP32}
     if args.engine == "csr_fp32":
         engines = {"fp32": P.ENGINE_CSR_FP32}
+    elif args.engine == "bf16":
+        engines = {"bf16": P.ENGINE_AUTO}
     res = {}
     for name, eng in engines.items():
         if world > 1:
