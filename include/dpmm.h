@@ -243,6 +243,21 @@ int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
                         double* grad_log_alpha, float* grad_log_beta);
 
 /*
+ * The collapsed log marginal likelihood of dpmm_logml_forward and its
+ * gradient (dpmm_logml_backward) for a sampler's data (derived from eq. 10
+ * and eq. 12 with gene-wise beta, generalising the symmetric lambda):
+ * labels == NULL takes the chain's current partition (its statistics, no
+ * pass over the counts); otherwise labels is int32[N] (host or device) in
+ * [0, K_labels).  log_beta float[D] (host or device).  Any output may be
+ * NULL; logml and grad_log_alpha are host doubles, grad_log_beta float[D]
+ * host or device.  Scratch is allocated on the first call and kept with the
+ * context.  Synchronises.
+ */
+int dpmm_logml_grad(dpmm_ctx* ctx, const int32_t* labels, int32_t K_labels, double log_alpha,
+                    const float* log_beta, double* logml, double* grad_log_alpha,
+                    float* grad_log_beta);
+
+/*
  * Allocation-free variant of dpmm_logml_create + dpmm_logml_forward +
  * dpmm_logml_backward, for callers that cannot allocate device memory (for
  * example a framework whose caching allocator owns the GPU's memory, or

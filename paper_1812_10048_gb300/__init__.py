@@ -17,7 +17,7 @@ from ._lib import (DpmmError, ENGINE_AUTO, ENGINE_CSR_FP32, ENGINE_TILE_BF16, ch
 __all__ = [
     "DpmmError", "Sampler", "LogML", "dpmm_default_opts", "dpmm_init", "dpmm_free", "dpmm_sweep",
     "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
-    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_get_state",
+    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_get_state",
     "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
     "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_tile_scores", "dpmm_debug_moves", "dpmm_logml_create",
     "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_logml_grad_noalloc",
@@ -84,6 +84,26 @@ def dpmm_plans_applied(ctx):
     n = ctypes.c_int64(0)
     check(lib().dpmm_plans_applied(ctx, ctypes.byref(n)))
     return n.value
+
+
+def dpmm_logml_grad(ctx, log_alpha, log_beta, labels=None, K=0, grad=True):
+    """Collapsed log marginal likelihood of a sampler's data and its gradient
+    w.r.t. (log alpha, log beta): the chain's current partition when labels is
+    None, else labels (int32[N], host array or CUDA tensor) in [0, K).
+    log_beta: float32[D] host array or CUDA tensor.  Returns
+    (logml, d/d log alpha, d/d log beta as float32[D]) or just logml."""
+    lb = log_beta if hasattr(log_beta, "data_ptr") else np.ascontiguousarray(log_beta, np.float32)
+    lab = None
+    if labels is not None:
+        lab = labels if hasattr(labels, "data_ptr") else np.ascontiguousarray(labels, np.int32)
+    out = ctypes.c_double(0.0)
+    ga = ctypes.c_double(0.0)
+    D = lb.numel() if hasattr(lb, "numel") else lb.size
+    gb = np.zeros(int(D), dtype=np.float32)
+    check(lib().dpmm_logml_grad(ctx, ptr(lab) if lab is not None else None, int(K),
+                                float(log_alpha), ptr(lb), ctypes.byref(out),
+                                ctypes.byref(ga) if grad else None, ptr(gb) if grad else None))
+    return (out.value, ga.value, gb) if grad else out.value
 
 
 def dpmm_profile(ctx, enable=True):

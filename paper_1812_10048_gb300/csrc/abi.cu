@@ -109,6 +109,14 @@ void free_ctx(Ctx& c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.sc_host) cudaFreeHost(c.sc_host);
+    if (c.lml) {
+        void* lp[] = {c.lml->labels, c.lml->n, c.lml->S, c.lml->T, c.lml->common, c.lml->out,
+                      c.lml->grad, c.lml->beta_stage};
+        for (void* q : lp)
+            if (q) cudaFree(q);
+        delete c.lml;
+        c.lml = nullptr;
+    }
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
 }
 
@@ -844,6 +852,75 @@ int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
     } else if (!dev_out) {
         CK(cudaStreamSynchronize(p.stream));
     }
+    return DPMM_OK;
+}
+
+int dpmm_logml_grad(dpmm_ctx* ctx, const int32_t* labels, int32_t K_labels, double log_alpha,
+                    const float* log_beta, double* logml, double* grad_log_alpha,
+                    float* grad_log_beta) {
+    CHECK_CTX(ctx);
+    Ctx& c = ctx->c;
+    if (!log_beta) return fail(DPMM_EINVAL, "log_beta is null");
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    int32_t K = c.sc_host->K;
+    if (labels) {
+        if (K_labels < 1 || K_labels > c.kmax)
+            return fail(DPMM_EINVAL, "K_labels = %d outside [1, %d]", K_labels, c.kmax);
+        K = K_labels;
+    }
+    if (!c.lml) {
+        LmlPlan* p = new (std::nothrow) LmlPlan();
+        if (!p) return fail(DPMM_ENOMEM, "host allocation failed");
+        p->stream = c.stream;
+        p->num_sms = c.num_sms;
+        p->N = c.N;
+        p->D = c.D;
+        cudaError_t e;
+        if ((e = dalloc(&p->labels, (size_t)c.N)) || (e = dalloc(&p->n, (size_t)c.kmax)) ||
+            (e = dalloc(&p->S, (size_t)c.kmax * c.D)) || (e = dalloc(&p->T, (size_t)c.kmax)) ||
+            (e = dalloc(&p->common, 1)) || (e = dalloc(&p->out, 2)) ||
+            (e = dalloc(&p->grad, (size_t)c.D)) || (e = dalloc(&p->beta_stage, (size_t)c.D))) {
+            p->own_stream = false;
+            free_lml(*p);
+            delete p;
+            return fail(e == cudaErrorMemoryAllocation ? DPMM_ENOMEM : DPMM_ECUDA,
+                        "log-ML scratch: %s", cudaGetErrorString(e));
+        }
+        c.lml = p;
+    }
+    LmlPlan& p = *c.lml;
+    p.K = K;
+    if (labels) {
+        std::vector<int32_t> hl;
+        if ((rc = fetch(hl, labels, (size_t)c.N))) return rc;
+        for (int64_t i = 0; i < c.N; ++i)
+            if (hl[i] < 0 || hl[i] >= K)
+                return fail(DPMM_EINVAL, "label %d of cell %lld outside [0, %d)", hl[i],
+                            (long long)i, K);
+        CK(cudaMemcpyAsync(p.labels, hl.data(), sizeof(int32_t) * c.N, cudaMemcpyHostToDevice,
+                           c.stream));
+        CK(lml_stats_from_csr(p, csr_of(c), p.labels));
+    } else {
+        CK(lml_stats_from_chain(p, c.nsub, c.Ssub));
+    }
+    const float* lb;
+    if ((rc = stage_beta(p, log_beta, &lb))) return rc;
+    if (logml) {
+        CK(lml_forward(p, log_alpha, lb, p.out));
+        CK(cudaMemcpyAsync(logml, p.out, sizeof(double), cudaMemcpyDefault, c.stream));
+    }
+    if (grad_log_alpha || grad_log_beta) {
+        const bool dev_out = grad_log_beta && is_device_ptr(grad_log_beta);
+        CK(lml_backward(p, log_alpha, lb, dev_out ? grad_log_beta : p.grad, p.out + 1));
+        if (grad_log_beta && !dev_out)
+            CK(cudaMemcpyAsync(grad_log_beta, p.grad, sizeof(float) * c.D,
+                               cudaMemcpyDeviceToHost, c.stream));
+        if (grad_log_alpha)
+            CK(cudaMemcpyAsync(grad_log_alpha, p.out + 1, sizeof(double), cudaMemcpyDefault,
+                               c.stream));
+    }
+    CK(cudaStreamSynchronize(c.stream));
     return DPMM_OK;
 }
 

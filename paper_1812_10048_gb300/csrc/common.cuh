@@ -160,6 +160,9 @@ struct Ctx {
     int apply_blocks = 0;
     size_t apply_smem = 0;
 
+    // scratch of dpmm_logml_grad (allocated on first use)
+    struct LmlPlan* lml = nullptr;
+
     // CUDA graph of dpmm_step
     cudaGraphExec_t step_exec = nullptr;
 

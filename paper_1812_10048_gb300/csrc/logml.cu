@@ -131,6 +131,77 @@ k_lml_backward(const uint32_t* __restrict__ n, const uint32_t* __restrict__ S,
     grad[u] = b * acc;
 }
 
+// Cluster statistics of a sampler's current state from its sub-cluster
+// statistics: n_k = n-bar_k0 + n-bar_k1, S_ku = S-bar_k0u + S-bar_k1u,
+// T_k = sum_u S_ku.  One block per cluster.
+__global__ void k_lml_from_chain(const uint32_t* __restrict__ nsub,
+                                 const uint32_t* __restrict__ Ssub, int32_t D,
+                                 uint32_t* __restrict__ n, uint32_t* __restrict__ S,
+                                 unsigned long long* __restrict__ T) {
+    __shared__ unsigned long long red[32];
+    const int k = blockIdx.x;
+    const uint32_t* S0 = Ssub + (size_t)(2 * k) * D;
+    const uint32_t* S1 = S0 + D;
+    unsigned long long t = 0;
+    for (int u = threadIdx.x; u < D; u += blockDim.x) {
+        const uint32_t v = S0[u] + S1[u];
+        S[(size_t)k * D + u] = v;
+        t += v;
+    }
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        T[k] = s;
+        n[k] = nsub[2 * k] + nsub[2 * k + 1];
+    }
+}
+
+// Cluster statistics of given labels over a sampler's own CSR copy.
+__global__ void k_lml_csr_stats(Csr csr, const int32_t* __restrict__ labels, int64_t N,
+                                int32_t D, int32_t K, uint32_t* __restrict__ n,
+                                uint32_t* __restrict__ S, unsigned long long* __restrict__ T) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t cell = w0; cell < N; cell += nw) {
+        const int32_t k = labels[cell];
+        if (k < 0 || k >= K) continue;
+        const int64_t beg = csr.indptr[cell], end = csr.indptr[cell + 1];
+        unsigned long long rowsum = 0;
+        for (int64_t e = beg + lane; e < end; e += 32) {
+            int32_t u, x;
+            csr.get(e, u, x);
+            if (x) {
+                atomicAdd(&S[(size_t)k * D + u], (uint32_t)x);
+                rowsum += (unsigned long long)x;
+            }
+        }
+        rowsum = warp_sum(rowsum);
+        if (lane == 0) {
+            atomicAdd(&n[k], 1u);
+            if (rowsum) atomicAdd(&T[k], rowsum);
+        }
+    }
+}
+
+cudaError_t lml_stats_from_chain(LmlPlan& p, const uint32_t* nsub, const uint32_t* Ssub) {
+    k_lml_from_chain<<<p.K, kLmlThreads, 0, p.stream>>>(nsub, Ssub, p.D, p.n, p.S, p.T);
+    return cudaGetLastError();
+}
+
+cudaError_t lml_stats_from_csr(LmlPlan& p, const Csr& csr, const int32_t* labels) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p.n, 0, sizeof(uint32_t) * p.K, p.stream))) return e;
+    if ((e = cudaMemsetAsync(p.S, 0, sizeof(uint32_t) * (size_t)p.K * p.D, p.stream))) return e;
+    if ((e = cudaMemsetAsync(p.T, 0, sizeof(unsigned long long) * p.K, p.stream))) return e;
+    k_lml_csr_stats<<<p.num_sms * 4, 256, 0, p.stream>>>(csr, labels, p.N, p.D, p.K, p.n, p.S,
+                                                         p.T);
+    return cudaGetLastError();
+}
+
 cudaError_t lml_compute_stats(LmlPlan& p) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(p.n, 0, sizeof(uint32_t) * p.K, p.stream))) return e;

@@ -28,6 +28,8 @@ struct LmlPlan {
 };
 
 cudaError_t lml_compute_stats(LmlPlan& p);
+cudaError_t lml_stats_from_chain(LmlPlan& p, const uint32_t* nsub, const uint32_t* Ssub);
+cudaError_t lml_stats_from_csr(LmlPlan& p, const Csr& csr, const int32_t* labels);
 cudaError_t lml_forward(LmlPlan& p, double log_alpha, const float* log_beta, double* out_dev);
 cudaError_t lml_backward(LmlPlan& p, double log_alpha, const float* log_beta, float* grad_dev,
                          double* grad_alpha_dev);

@@ -65,3 +65,33 @@ def test_autograd_function_matches_finite_differences(P):
         assert abs(lbt.grad[u].item() - fd) <= 2e-3 * max(1.0, abs(fd))
     fa = (model.forward(0.1 + 1e-6, lbt.detach()) - model.forward(0.1 - 1e-6, lbt.detach())) / 2e-6
     assert abs(la.grad.item() - fa) <= 1e-5 * max(1.0, abs(fa))
+
+
+def test_chain_bound_logml_grad_matches_oracle(P):
+    """dpmm_logml_grad on a sampler: the current partition (from the chain's
+    statistics) and explicit labels (through the chain's own CSR copy), host
+    and device buffers, against the FP64 oracle."""
+    import torch
+    from oracle.logml import cluster_stats, log_ml, log_ml_grad
+    ds, lb = problem(seed=3, N=2500, D=200, K=6)
+    s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, kmax=32, seed=5)
+    s.step(6)
+    labels, K = s.labels()
+    la = -0.2
+    for lab, k, arg in [(labels, K, None), (ds.labels, int(ds.labels.max()) + 1, ds.labels)]:
+        n, S = cluster_stats(ds.indptr, ds.indices, ds.data, ds.N, ds.D, lab, k)
+        ref = log_ml(n, S, la, lb.astype(np.float64))
+        ga_ref, gb_ref = log_ml_grad(n, S, la, lb.astype(np.float64))
+        val, ga, gb = P.dpmm_logml_grad(s.ctx, la, lb, labels=arg, K=k)
+        assert abs(val - ref) <= 1e-10 * abs(ref)
+        assert abs(ga - ga_ref) <= 1e-9 * max(1.0, abs(ga_ref))
+        np.testing.assert_allclose(gb, gb_ref, rtol=2e-4, atol=1e-3)
+        lbt = torch.from_numpy(lb).cuda()
+        argt = None if arg is None else torch.from_numpy(np.ascontiguousarray(arg, np.int32)).cuda()
+        val2, ga2, gb2 = P.dpmm_logml_grad(s.ctx, la, lbt, labels=argt, K=k)
+        assert val2 == val and ga2 == ga
+        np.testing.assert_array_equal(gb2, gb)
+    # the chain itself is untouched
+    labels2, K2 = s.labels()
+    assert K2 == K and np.array_equal(labels2, labels)
+    s.close()
