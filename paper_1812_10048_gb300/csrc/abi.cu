@@ -105,10 +105,12 @@ void free_ctx(Ctx& c) {
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
                     c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
                     c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B,
-                    c.gbar};
+                    c.gbar, c.d_chains};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c.sc_host) cudaFreeHost(c.sc_host);
+    delete c.h_chain0;
+    c.h_chain0 = nullptr;
     if (c.lml) {
         void* lp[] = {c.lml->labels, c.lml->n, c.lml->S, c.lml->T, c.lml->common, c.lml->out,
                       c.lml->grad, c.lml->beta_stage};
@@ -119,6 +121,53 @@ void free_ctx(Ctx& c) {
     }
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
 }
+
+}  // namespace
+
+ChainArgs dpmm::chain_args(const Ctx& c) {
+    ChainArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.csr = csr_of(c);
+    a.N = c.N;
+    a.D = c.D;
+    a.kmax = c.kmax;
+    a.sc = c.sc;
+    a.state = c.state;
+    a.nsub = c.nsub;
+    a.Ssub = c.Ssub;
+    a.sumlogq = c.sumlogq;
+    a.acc_nsub = c.acc_nsub;
+    a.acc_Ssub = c.acc_Ssub;
+    a.acc_sumlogq = c.acc_sumlogq;
+    a.logpi = c.logpi;
+    a.Lc = c.Lc;
+    a.Ls = c.Ls;
+    a.lmap = c.lmap;
+    a.desc = c.desc;
+    a.reinit = c.reinit;
+    a.decide = c.decide;
+    a.log_h = c.log_h;
+    a.pair_ab = c.pair_ab;
+    a.lg_table = c.lg_table;
+    a.move_part = c.move_part;
+    a.move_ticket = c.move_ticket;
+    a.tile_enabled = c.tile_enabled ? 1 : 0;
+    a.tile_C = c.tile_C;
+    a.tile_T = c.tile_T;
+    a.tile_Lslot = c.tile_Lslot;
+    a.tile_ent = c.tile_ent;
+    a.tile_ptr = c.tile_ptr;
+    a.tile_B = c.tile_B;
+    a.alpha = c.alpha;
+    a.beta = c.beta;
+    a.log_alpha = std::log(c.alpha);
+    a.lg_beta = std::lgamma(c.beta);
+    a.split_q = c.opts.split_q;
+    a.st = make_stream(c.opts.seed, c.opts.chain_id);
+    return a;
+}
+
+namespace {
 
 // Inside a stream capture the event becomes an event-record node of the graph
 // (external record); outside a capture it is an ordinary record.
@@ -202,7 +251,7 @@ int enqueue_moves(Ctx& c, int32_t mode) {
 int recount_all(Ctx& c) {
     CK(cudaMemsetAsync(c.nsub, 0, sizeof(uint32_t) * 2 * c.kmax, c.stream));
     CK(cudaMemsetAsync(c.Ssub, 0, sizeof(uint32_t) * 2 * (size_t)c.kmax * c.D, c.stream));
-    CK(launch_stats(c, nullptr, c.nsub, c.Ssub));
+    CK(launch_recount(c));
     return DPMM_OK;
 }
 
@@ -411,6 +460,16 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     CKI(configure_plan_apply(c));
     CKI(dalloc(&c.gbar, 1));
     CKI(cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.stream));
+    {
+        // this context's chain table: itself
+        c.h_chain0 = new (std::nothrow) ChainArgs(chain_args(c));
+        if (!c.h_chain0) return bail(fail(DPMM_ENOMEM, "host allocation failed"));
+        CKI(dalloc(&c.d_chains, 1));
+        CKI(cudaMemcpyAsync(c.d_chains, c.h_chain0, sizeof(ChainArgs), cudaMemcpyHostToDevice,
+                            c.stream));
+        c.nchains = 1;
+        c.max_Lslot = c.tile_Lslot;
+    }
     if (c.tile_enabled) CKI(configure_tile(c));
     CKI(launch_lg_table(c));
     CKI(launch_init_state(c));

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include <string>
 
 #include "dpmm.h"
@@ -155,6 +157,15 @@ struct Ctx {
     unsigned char* tile_B = nullptr;  // per-sweep BF16 hi/lo table, [C][256 rows][64] swizzled
 
 
+    // chains this context's launches walk: itself (nchains = 1) or, for a
+    // batch, its members (each a full context sharing this stream)
+    struct ChainArgs* d_chains = nullptr;
+    int32_t nchains = 0;
+    struct ChainArgs* h_chain0 = nullptr;   // host copy of the single chain (nchains == 1)
+    std::vector<Ctx*> members;       // owned by a batch context
+    bool is_member = false;          // a chain of a batch (its stream is the batch's)
+    int32_t max_Lslot = 0;           // longest segment slot over the chains
+
     // plan + application kernel (cooperative, one block per SM)
     GridBar* gbar = nullptr;
     int apply_blocks = 0;
@@ -292,6 +303,64 @@ struct Csr {
 inline Csr csr_of(const Ctx& c) { return Csr{c.indptr, c.entries, c.cols, c.counts}; }
 
 // ---------------------------------------------------------------------------
+// Per-chain view passed to every step kernel: a step launches each kernel
+// once for a table of chains (one chain, or a batch of independent chains)
+// and the kernel walks the table.
+// ---------------------------------------------------------------------------
+struct ChainArgs {
+    Csr csr;
+    int64_t N;
+    int32_t D, kmax;
+    DevScalars* sc;
+    uint32_t* state;
+    uint32_t* nsub;
+    uint32_t* Ssub;
+    double* sumlogq;
+    uint32_t* acc_nsub;
+    uint32_t* acc_Ssub;
+    double* acc_sumlogq;
+    float* logpi;
+    float* Lc;
+    float* Ls;
+    uint32_t* lmap;
+    int32_t* desc;
+    uint8_t* reinit;
+    int32_t* decide;
+    double* log_h;
+    int32_t* pair_ab;
+    double* lg_table;
+    unsigned char* move_part;
+    int32_t* move_ticket;
+    // dense-tile engine (tile_enabled = 0: not built for this chain)
+    int32_t tile_enabled, tile_C, tile_T, tile_Lslot;
+    uint32_t* tile_ent;
+    int32_t* tile_ptr;
+    unsigned char* tile_B;
+    // hyper-parameters and random stream
+    double alpha, beta, log_alpha, lg_beta;
+    int32_t split_q;
+    int32_t pad;
+    Stream st;
+};
+
+ChainArgs chain_args(const Ctx& c);
+
+// The two forms of chain table a step kernel takes (as a __grid_constant__
+// parameter): one chain by value (its fields stay in the parameter bank, as
+// for a plain kernel) or a device array of chains (a batch).
+struct TabV {
+    ChainArgs c0;
+    __device__ __forceinline__ int n() const { return 1; }
+    __device__ __forceinline__ const ChainArgs& operator[](int) const { return c0; }
+};
+struct TabP {
+    const ChainArgs* p;
+    int32_t cnt;
+    __device__ __forceinline__ int n() const { return cnt; }
+    __device__ __forceinline__ const ChainArgs& operator[](int b) const { return p[b]; }
+};
+
+// ---------------------------------------------------------------------------
 // Grid-wide barrier for cooperative launches (all blocks co-resident).  The
 // last block to arrive resets the count and advances the generation; the
 // others poll the generation a bounded number of times and report failure
@@ -374,13 +443,20 @@ __device__ __forceinline__ void stats_cells(const Csr& csr, const uint32_t* __re
     }
 }
 
+// Calls launch(table) with the context's chains in the fitting table form.
+template <class F>
+cudaError_t with_table(const Ctx& c, F launch) {
+    if (c.nchains == 1) return launch(TabV{*c.h_chain0});
+    return launch(TabP{c.d_chains, c.nchains});
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (sweep.cu, moves.cu).
 // ---------------------------------------------------------------------------
 cudaError_t configure_launches(Ctx& c);
 cudaError_t launch_draw_params(Ctx& c);
 cudaError_t launch_assign(Ctx& c);
-cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub);
+cudaError_t launch_recount(Ctx& c);
 cudaError_t launch_sweep_stats(Ctx& c);
 cudaError_t launch_csr_commit(Ctx& c);
 cudaError_t launch_select_engine(Ctx& c);

@@ -151,8 +151,7 @@ struct MovePartial {
 // b / G, chunk b % G, with G chosen so that proposals x G fills the grid.  The
 // last block to finish a proposal (a ticket counter, no waiting) completes
 // it, its four warps evaluating the count and total terms side by side.
-__global__ void __launch_bounds__(kPartialThreads)
-k_move_partial(DevScalars* sc, const uint32_t* __restrict__ nsub,
+__device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __restrict__ nsub,
                const uint32_t* __restrict__ Ssub, const double* __restrict__ sumlogq,
                int32_t* __restrict__ pair_ab, const double* __restrict__ lg_base,
                MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
@@ -311,6 +310,19 @@ k_move_partial(DevScalars* sc, const uint32_t* __restrict__ nsub,
                           (double)(na + nb - 2) * kLogHalf;
         decide[e] = log_u < lh ? 1 : 0;
         log_h[e] = lh;
+    }
+}
+
+// Every chain of the table in turn, each with the whole grid.
+template <class Tab>
+__global__ void __launch_bounds__(kPartialThreads)
+k_move_partial(const __grid_constant__ Tab tab, int32_t mode) {
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        move_chain(ch.sc, ch.nsub, ch.Ssub, ch.sumlogq, ch.pair_ab, ch.lg_table,
+                   reinterpret_cast<MovePartial*>(ch.move_part), ch.move_ticket, ch.decide,
+                   ch.log_h, ch.D, ch.log_alpha, ch.beta, ch.lg_beta, ch.split_q, mode, ch.st);
+        __syncthreads();
     }
 }
 
@@ -538,128 +550,129 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
 //   stream: step t for a sweep's resets, m after splits); barrier; each block
 //   recounts its share of the cells of re-initialised clusters; block 0
 //   commits K = K_new and counts the phase.
-struct PlanApplyArgs {
-    Csr csr;
-    DevScalars* sc;
-    int32_t kind;
-    uint32_t* nsub;
-    double* sumlogq;
-    uint32_t* acc_nsub;
-    double* acc_sumlogq;
-    const int32_t* decide;
-    const int32_t* pair_ab;
-    uint32_t* lmap;
-    int32_t* desc;
-    uint8_t* reinit;
-    uint32_t* Ssub;
-    uint32_t* acc_Ssub;
-    uint32_t* state;
-    GridBar* bar;
-    int64_t N;
-    int32_t D, kmax;
-    int64_t priv_cap;    // words of dynamic shared memory for the recount
-    Stream st;
-};
 
+// Does chain ch's pending plan change anything?  (block-wide; same answer in
+// every block: an empty cluster or a sub-cluster reset; an accepted split
+// with room left; an accepted merge)
+__device__ __forceinline__ int plan_changes(const ChainArgs& ch, bool compact) {
+    const int K = ch.sc->K;
+    int change = 0;
+    if (compact) {
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const uint32_t n0 = ch.acc_nsub[2 * k], n1 = ch.acc_nsub[2 * k + 1];
+            change |= (n0 + n1 == 0u) || (n0 + n1 >= 2u && (n0 == 0u || n1 == 0u));
+        }
+    } else if (ch.sc->chain_sel == 1) {
+        if (K < ch.kmax)
+            for (int k = threadIdx.x; k < K; k += blockDim.x) change |= ch.decide[k] != 0;
+    } else {
+        for (int k = threadIdx.x; k < K / 2; k += blockDim.x) change |= ch.decide[k] != 0;
+    }
+    return __syncthreads_or(change);
+}
+
+__device__ __forceinline__ void plan_chain(const ChainArgs& ch, bool compact, PlanSmem& sm) {
+    plan_block(ch.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, ch.nsub, ch.sumlogq, ch.acc_nsub,
+               ch.acc_sumlogq, ch.decide, ch.pair_ab, ch.lmap, ch.desc, ch.reinit, ch.kmax,
+               compact ? &ch.sc->t : &ch.sc->m, sm);
+}
+
+// priv_cap: words of dynamic shared memory for the recount.
+template <class Tab>
 __global__ void __launch_bounds__(kPlanThreads, 1)
-k_plan_apply(PlanApplyArgs a) {
+k_plan_apply(const __grid_constant__ Tab tab, int32_t kind, GridBar* bar, int64_t priv_cap) {
     extern __shared__ __align__(16) uint32_t spriv[];
     __shared__ PlanSmem sm;
-    __shared__ int s_apply, s_Knew;
-    __shared__ uint32_t s_step;
-    const bool compact = a.kind == PLAN_COMPACT;
-    uint32_t* bump = compact ? &a.sc->t : &a.sc->m;
-    {
-        const int K = a.sc->K;
-        int change = 0;
-        if (compact) {
-            for (int k = threadIdx.x; k < K; k += blockDim.x) {
-                const uint32_t n0 = a.acc_nsub[2 * k], n1 = a.acc_nsub[2 * k + 1];
-                change |= (n0 + n1 == 0u) || (n0 + n1 >= 2u && (n0 == 0u || n1 == 0u));
-            }
-        } else if (a.sc->chain_sel == 1) {
-            if (K < a.kmax)
-                for (int k = threadIdx.x; k < K; k += blockDim.x) change |= a.decide[k] != 0;
-        } else {
-            for (int k = threadIdx.x; k < K / 2; k += blockDim.x) change |= a.decide[k] != 0;
-        }
-        if (!__syncthreads_or(change)) {
-            if (blockIdx.x == 0)
-                plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq,
-                           a.acc_nsub, a.acc_sumlogq, a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax,
-                           bump, sm);
-            return;
-        }
+    const bool compact = kind == PLAN_COMPACT;
+    int any = 0;
+    for (int b = 0; b < tab.n(); ++b) any |= plan_changes(tab[b], compact);
+    // chain b is planned by block b % gridDim.x
+    for (int b = blockIdx.x; b < tab.n(); b += gridDim.x) {
+        plan_chain(tab[b], compact, sm);
+        __syncthreads();
     }
-    if (blockIdx.x == 0)
-        plan_block(a.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, a.nsub, a.sumlogq, a.acc_nsub,
-                   a.acc_sumlogq,
-                   a.decide, a.pair_ab, a.lmap, a.desc, a.reinit, a.kmax, bump, sm);
-    if (!grid_sync(a.bar)) {
-        if (threadIdx.x == 0) atomicExch(&a.sc->error, DPMM_ETIMEOUT);
+    if (!any) return;
+    if (!grid_sync(bar)) {
+        if (threadIdx.x == 0) atomicExch(&tab[0].sc->error, DPMM_ETIMEOUT);
         return;
     }
-    if (threadIdx.x == 0) {
-        volatile DevScalars* vs = a.sc;
-        s_apply = vs->apply;
-        s_Knew = vs->K_new;
-        s_step = compact ? vs->t : vs->m;
-    }
-    __syncthreads();
-    if (!s_apply) return;
-    const int Kn = s_Knew;
-    const int D = a.D;
-    const int64_t total = (int64_t)2 * Kn * D;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // (1) rows of the new main statistics, from the old main into the accumulators
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int64_t row = i / D, u = i - row * D;
-        const int32_t d = __ldcg(a.desc + row);
-        const int32_t src = d >> 2, mode = d & 3;
-        uint32_t v = 0u;
-        if (mode == DESC_SUM)
-            v = a.Ssub[(size_t)(2 * src) * D + u] + a.Ssub[(size_t)(2 * src + 1) * D + u];
-        else if (mode != DESC_ZERO)
-            v = a.Ssub[(size_t)(2 * src + mode) * D + u];
-        a.acc_Ssub[i] = v;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // (1) rows of each changed chain's new main statistics, from the old main
+    //     into the accumulators
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        volatile DevScalars* vs = ch.sc;
+        if (!vs->apply) continue;
+        const int D = ch.D;
+        const int64_t total = (int64_t)2 * vs->K_new * D;
+        for (int64_t i = tid; i < total; i += stride) {
+            const int64_t row = i / D, u = i - row * D;
+            const int32_t d = __ldcg(ch.desc + row);
+            const int32_t src = d >> 2, mode = d & 3;
+            uint32_t v = 0u;
+            if (mode == DESC_SUM)
+                v = ch.Ssub[(size_t)(2 * src) * D + u] + ch.Ssub[(size_t)(2 * src + 1) * D + u];
+            else if (mode != DESC_ZERO)
+                v = ch.Ssub[(size_t)(2 * src + mode) * D + u];
+            ch.acc_Ssub[i] = v;
+        }
     }
-    if (!grid_sync(a.bar)) {
-        if (threadIdx.x == 0) atomicExch(&a.sc->error, DPMM_ETIMEOUT);
+    if (!grid_sync(bar)) {
+        if (threadIdx.x == 0) atomicExch(&tab[0].sc->error, DPMM_ETIMEOUT);
         return;
     }
     // (2) back into main, accumulators cleared; this block's cells relabelled
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        a.Ssub[i] = __ldcg(a.acc_Ssub + i);
-        a.acc_Ssub[i] = 0u;
-    }
+    //     (SUB_COIN sub-labels: fair coins on the tag-7 stream, step t for a
+    //     sweep's resets, m after splits)
     const uint32_t sub_kind = compact ? SUBINIT_RESET : SUBINIT_SPLIT;
-    const int64_t per = (a.N + gridDim.x - 1) / gridDim.x;
-    const int64_t c0 = (int64_t)blockIdx.x * per, c1 = min(a.N, c0 + per);
-    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-        const uint32_t s = a.state[i];
-        const uint32_t e = __ldcg(a.lmap + 2 * state_label(s) + state_sub(s));
-        const uint32_t md = e >> 28;
-        uint32_t sub = state_sub(s);
-        if (md == SUB_SET0) sub = 0u;
-        else if (md == SUB_SET1) sub = 1u;
-        else if (md == SUB_COIN) {
-            const uint4 w = a.st.words(TAG_SUBINIT, (uint32_t)i, s_step, sub_kind);
-            sub = word_uniform(w.x) < 0.5f ? 1u : 0u;
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        volatile DevScalars* vs = ch.sc;
+        if (!vs->apply) continue;
+        const int64_t total = (int64_t)2 * vs->K_new * ch.D;
+        for (int64_t i = tid; i < total; i += stride) {
+            ch.Ssub[i] = __ldcg(ch.acc_Ssub + i);
+            ch.acc_Ssub[i] = 0u;
         }
-        a.state[i] = pack_state(e & 0x0FFFFFFFu, sub);
+        const uint32_t step = compact ? vs->t : vs->m;
+        const int64_t per = (ch.N + gridDim.x - 1) / gridDim.x;
+        const int64_t c0 = (int64_t)blockIdx.x * per, c1 = min(ch.N, c0 + per);
+        for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+            const uint32_t s = ch.state[i];
+            const uint32_t e = __ldcg(ch.lmap + 2 * state_label(s) + state_sub(s));
+            const uint32_t md = e >> 28;
+            uint32_t sub = state_sub(s);
+            if (md == SUB_SET0) sub = 0u;
+            else if (md == SUB_SET1) sub = 1u;
+            else if (md == SUB_COIN) {
+                const uint4 w = ch.st.words(TAG_SUBINIT, (uint32_t)i, step, sub_kind);
+                sub = word_uniform(w.x) < 0.5f ? 1u : 0u;
+            }
+            ch.state[i] = pack_state(e & 0x0FFFFFFFu, sub);
+        }
     }
-    if (!grid_sync(a.bar)) {
-        if (threadIdx.x == 0) atomicExch(&a.sc->error, DPMM_ETIMEOUT);
+    if (!grid_sync(bar)) {
+        if (threadIdx.x == 0) atomicExch(&tab[0].sc->error, DPMM_ETIMEOUT);
         return;
     }
-    // (3) re-initialised clusters recounted (their rows were gathered as zeros)
-    stats_cells(a.csr, a.state, a.reinit, a.nsub, a.Ssub, a.N, D, Kn, spriv, a.priv_cap);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.sc->K = Kn;
-        *bump += 1u;
+    // (3) re-initialised clusters recounted (their rows were gathered as zeros);
+    //     then block 0 commits K = K_new and counts the phase
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        volatile DevScalars* vs = ch.sc;
+        if (!vs->apply) continue;
+        const int Kn = vs->K_new;
+        stats_cells(ch.csr, ch.state, ch.reinit, ch.nsub, ch.Ssub, ch.N, ch.D, Kn, spriv,
+                    priv_cap);
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ch.sc->K = Kn;
+            if (compact) ch.sc->t += 1u;
+            else ch.sc->m += 1u;
+        }
     }
 }
-
 
 cudaError_t launch_lg_table(Ctx& c) {
     k_lg_table<<<(kLgTable + 255) / 256, 256, 0, c.stream>>>(c.lg_table, c.beta,
@@ -668,12 +681,10 @@ cudaError_t launch_lg_table(Ctx& c) {
 }
 
 cudaError_t launch_move_score(Ctx& c, int32_t mode) {
-    const Stream st = make_stream(c.opts.seed, c.opts.chain_id);
-    k_move_partial<<<kMaxPartials, kPartialThreads, 0, c.stream>>>(
-        c.sc, c.nsub, c.Ssub, c.sumlogq, c.pair_ab, c.lg_table,
-        reinterpret_cast<MovePartial*>(c.move_part), c.move_ticket, c.decide, c.log_h, c.D,
-        std::log(c.alpha), c.beta, std::lgamma(c.beta), c.opts.split_q, mode, st);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_move_partial<<<kMaxPartials, kPartialThreads, 0, c.stream>>>(tab, mode);
+        return cudaGetLastError();
+    });
 }
 
 size_t move_partial_bytes() { return sizeof(MovePartial) * kMaxPartials * kPartialWarps; }
@@ -683,44 +694,29 @@ cudaError_t configure_plan_apply(Ctx& c) {
     // one block per SM, the rest of shared memory for the recount's counters
     c.apply_blocks = c.num_sms;
     c.apply_smem = c.smem_optin - sizeof(PlanSmem) - 1024;
-    return cudaFuncSetAttribute(k_plan_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_plan_apply<TabV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)c.apply_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_plan_apply<TabP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)c.apply_smem);
 }
 
 cudaError_t launch_plan_apply(Ctx& c, int32_t kind) {
-    PlanApplyArgs a;
-    a.csr = csr_of(c);
-    a.sc = c.sc;
-    a.kind = kind;
-    a.nsub = c.nsub;
-    a.sumlogq = c.sumlogq;
-    a.acc_nsub = c.acc_nsub;
-    a.acc_sumlogq = c.acc_sumlogq;
-    a.decide = c.decide;
-    a.pair_ab = c.pair_ab;
-    a.lmap = c.lmap;
-    a.desc = c.desc;
-    a.reinit = c.reinit;
-    a.Ssub = c.Ssub;
-    a.acc_Ssub = c.acc_Ssub;
-    a.state = c.state;
-    a.bar = c.gbar;
-    a.N = c.N;
-    a.D = c.D;
-    a.kmax = c.kmax;
-    a.priv_cap = (int64_t)(c.apply_smem / sizeof(uint32_t));
-    a.st = make_stream(c.opts.seed, c.opts.chain_id);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(c.apply_blocks);
-    cfg.blockDim = dim3(kPlanThreads);
-    cfg.dynamicSmemBytes = c.apply_smem;
-    cfg.stream = c.stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_plan_apply, a);
+    return with_table(c, [&](auto tab) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c.apply_blocks);
+        cfg.blockDim = dim3(kPlanThreads);
+        cfg.dynamicSmemBytes = c.apply_smem;
+        cfg.stream = c.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_plan_apply<decltype(tab)>, tab, kind, c.gbar,
+                                  (int64_t)(c.apply_smem / sizeof(uint32_t)));
+    });
 }
 
 }  // namespace dpmm

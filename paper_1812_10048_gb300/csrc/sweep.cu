@@ -64,74 +64,95 @@ __device__ __forceinline__ void clear_accumulators(int K, uint32_t* acc_nsub,
     for (int i = threadIdx.x; i < K; i += blockDim.x) acc_sumlogq[i] = 0.0;
 }
 
-__global__ void k_select_engine(DevScalars* sc, int32_t tile_enabled, uint32_t* acc_nsub,
-                                double* acc_sumlogq) {
-    const int K = sc->K;
-    if (threadIdx.x == 0) select_engine(sc, K, tile_enabled);
-    clear_accumulators(K, acc_nsub, acc_sumlogq);
+template <class Tab>
+__global__ void k_select_engine(const __grid_constant__ Tab tab) {
+    for (int b = blockIdx.x; b < tab.n(); b += gridDim.x) {
+        const ChainArgs& ch = tab[b];
+        const int K = ch.sc->K;
+        __syncthreads();
+        if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
+        clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
+    }
 }
 
 // Rows 0 .. 3K-1 are theta rows (row 3k + p: cluster k for p = 0, its
 // sub-cluster p - 1 otherwise); row 3K is the pi row.  log G is written to the
 // output slot first, then normalised in place (log theta = log G - logsumexp).
-// Block 0 also selects the labelling engine of the sweep and clears the
-// accumulators of n-bar and sum log q.
-__global__ void __launch_bounds__(kDrawThreads)
-k_draw_params(DevScalars* sc, const uint32_t* __restrict__ nsub,
-              const uint32_t* __restrict__ Ssub, float* __restrict__ Lc, float* __restrict__ Ls,
-              float* __restrict__ logpi, int32_t D, int32_t kmax, float alpha, float beta,
-              Stream st, int32_t tile_enabled, uint32_t* __restrict__ acc_nsub,
-              double* __restrict__ acc_sumlogq) {
-    __shared__ float red[32];
-    const int K = sc->K;
-    if (blockIdx.x == 0) {
-        if (threadIdx.x == 0) select_engine(sc, K, tile_enabled);
-        clear_accumulators(K, acc_nsub, acc_sumlogq);
-    }
-    const uint32_t t = sc->t;
-    const int rows = 3 * K + 1;
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        if (row < 3 * K) {
-            const int k = row / 3, p = row % 3;
-            const uint32_t* S0 = Ssub + (size_t)(2 * k) * D;
-            const uint32_t* S1 = S0 + D;
-            float mx = -CUDART_INF_F;
-            for (int u = threadIdx.x; u < D; u += blockDim.x) {
-                const uint32_t S = p == 0 ? S0[u] + S1[u] : (p == 1 ? S0[u] : S1[u]);
-                const float lg = log_gamma_draw(st, TAG_THETA, beta + (float)S,
-                                                (uint32_t)row * (uint32_t)D + (uint32_t)u, t);
-                float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
-                *out = lg;
-                mx = fmaxf(mx, lg);
-            }
-            mx = block_reduce_max(mx, red);
-            float s = 0.0f;
-            for (int u = threadIdx.x; u < D; u += blockDim.x) {
-                const float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
-                s += expf(*out - mx);
-            }
-            s = block_reduce_sum(s, red);
-            const float lse = mx + logf(s);
-            for (int u = threadIdx.x; u < D; u += blockDim.x) {
-                float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
-                *out -= lse;
-            }
-        } else {
-            float mx = -CUDART_INF_F;
-            for (int k = threadIdx.x; k <= K; k += blockDim.x) {
-                const float a = k < K ? (float)(nsub[2 * k] + nsub[2 * k + 1]) : alpha;
-                const float lg = log_gamma_draw(st, TAG_PI, a, (uint32_t)k, t);
-                logpi[k] = lg;
-                mx = fmaxf(mx, lg);
-            }
-            mx = block_reduce_max(mx, red);
-            float s = 0.0f;
-            for (int k = threadIdx.x; k <= K; k += blockDim.x) s += expf(logpi[k] - mx);
-            s = block_reduce_sum(s, red);
-            const float lse = mx + logf(s);
-            for (int k = threadIdx.x; k <= K; k += blockDim.x) logpi[k] -= lse;
+__device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, uint32_t t, int row,
+                                         float* red) {
+    const int D = ch.D, kmax = ch.kmax;
+    const float beta = (float)ch.beta, alpha = (float)ch.alpha;
+    const Stream& st = ch.st;
+    if (row < 3 * K) {
+        const int k = row / 3, p = row % 3;
+        const uint32_t* S0 = ch.Ssub + (size_t)(2 * k) * D;
+        const uint32_t* S1 = S0 + D;
+        float* Lc = ch.Lc;
+        float* Ls = ch.Ls;
+        float mx = -CUDART_INF_F;
+        for (int u = threadIdx.x; u < D; u += blockDim.x) {
+            const uint32_t S = p == 0 ? S0[u] + S1[u] : (p == 1 ? S0[u] : S1[u]);
+            const float lg = log_gamma_draw(st, TAG_THETA, beta + (float)S,
+                                            (uint32_t)row * (uint32_t)D + (uint32_t)u, t);
+            float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
+            *out = lg;
+            mx = fmaxf(mx, lg);
         }
-        __syncthreads();
+        mx = block_reduce_max(mx, red);
+        float s = 0.0f;
+        for (int u = threadIdx.x; u < D; u += blockDim.x) {
+            const float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
+            s += expf(*out - mx);
+        }
+        s = block_reduce_sum(s, red);
+        const float lse = mx + logf(s);
+        for (int u = threadIdx.x; u < D; u += blockDim.x) {
+            float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
+            *out -= lse;
+        }
+    } else {
+        const uint32_t* nsub = ch.nsub;
+        float* logpi = ch.logpi;
+        float mx = -CUDART_INF_F;
+        for (int k = threadIdx.x; k <= K; k += blockDim.x) {
+            const float a = k < K ? (float)(nsub[2 * k] + nsub[2 * k + 1]) : alpha;
+            const float lg = log_gamma_draw(st, TAG_PI, a, (uint32_t)k, t);
+            logpi[k] = lg;
+            mx = fmaxf(mx, lg);
+        }
+        mx = block_reduce_max(mx, red);
+        float s = 0.0f;
+        for (int k = threadIdx.x; k <= K; k += blockDim.x) s += expf(logpi[k] - mx);
+        s = block_reduce_sum(s, red);
+        const float lse = mx + logf(s);
+        for (int k = threadIdx.x; k <= K; k += blockDim.x) logpi[k] -= lse;
+    }
+}
+
+// The 3K + 1 rows of every chain form one list dealt round-robin to the
+// blocks.  The block that draws row 0 of a chain also selects the chain's
+// labelling engine and clears its n-bar / sum log q accumulators.
+template <class Tab>
+__global__ void __launch_bounds__(kDrawThreads)
+k_draw_params(const __grid_constant__ Tab tab) {
+    __shared__ float red[32];
+    int64_t base = 0;
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        const int K = ch.sc->K;
+        const uint32_t t = ch.sc->t;
+        const int rows = 3 * K + 1;
+        int64_t first = base + (((int64_t)blockIdx.x - base) % gridDim.x + gridDim.x) % gridDim.x;
+        for (int64_t id = first; id < base + rows; id += gridDim.x) {
+            const int row = (int)(id - base);
+            if (row == 0) {
+                if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
+                clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
+            }
+            draw_row(ch, K, t, row, red);
+            __syncthreads();
+        }
+        base += rows;
     }
 }
 
@@ -178,26 +199,10 @@ __device__ __forceinline__ float2 sub_scores(const Csr& csr, int64_t beg, int64_
     return make_float2(warp_sum(t0), warp_sum(t1));
 }
 
-struct AssignArgs {
-    Csr csr;
-    DevScalars* sc;
-    uint32_t* state;
-    const uint32_t* nsub;     // sweep-start n-bar
-    const float* logpi;
-    const float* Lc;
-    const float2* Ls2;
-    double* acc_sumlogq;
-    uint32_t* acc_nsub;       // statistics accumulators (fused path)
-    uint32_t* acc_Ssub;
-    int64_t N;
-    int32_t D, kmax;
-    int64_t smem_bytes;       // dynamic shared memory of the launch
-    Stream st;
-};
 
 // eq. 8 draw for cell `cell` of cluster c given its two likelihood factors;
 // returns the sub-label and writes log q_i.
-__device__ __forceinline__ uint32_t draw_sublabel(const AssignArgs& a, int64_t cell, int c,
+__device__ __forceinline__ uint32_t draw_sublabel(const ChainArgs& a, int64_t cell, int c,
                                                   float2 lik, uint32_t t, float* logq) {
     const uint32_t old = a.state[cell];
     const bool stays = state_label(old) == (uint32_t)c;
@@ -230,7 +235,7 @@ __device__ __forceinline__ int warp_argmax(float best, int bestk) {
 
 // K > 32: lanes own clusters lane, lane + 32, ...; the row is contracted once
 // per chunk of 32 clusters and the running Gumbel-max kept across chunks.
-__device__ __forceinline__ void assign_cells(const AssignArgs& a, const float* L, int ldL, int K,
+__device__ __forceinline__ void assign_cells(const ChainArgs& a, const float* L, int ldL, int K,
                                              uint32_t t, double* blk_sumlogq) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -255,7 +260,7 @@ __device__ __forceinline__ void assign_cells(const AssignArgs& a, const float* L
         }
         const int c = warp_argmax(best, bestk);
         // eq. 8 with the sweep-start counts minus this cell's own old membership
-        const float2 lik = sub_scores(a.csr, beg, end, a.Ls2, a.kmax, c, lane);
+        const float2 lik = sub_scores(a.csr, beg, end, reinterpret_cast<const float2*>(a.Ls), a.kmax, c, lane);
         if (lane == 0) {
             float logq;
             const uint32_t s = draw_sublabel(a, cell, c, lik, t, &logq);
@@ -376,7 +381,7 @@ constexpr int kRowRegs = 8;   // row entries a lane keeps in registers (rows up 
 // Gumbel-max picks c; pass 2 gathers the two sub-cluster factors of c; lane 0
 // draws the eq. 8 sub-label; pass 3 adds the row into the block's statistics.
 template <int P>
-__device__ __forceinline__ void assign_cells_v2(const AssignArgs& a, const float* sLc, int Kp,
+__device__ __forceinline__ void assign_cells_v2(const ChainArgs& a, const float* sLc, int Kp,
                                                 const float2* Ls2, int ldS, int K, uint32_t t,
                                                 const float* spi, const float* slw,
                                                 double* wsq, uint32_t* wn, uint32_t* sS) {
@@ -512,8 +517,7 @@ __device__ __forceinline__ void assign_cells_v2(const AssignArgs& a, const float
     }
 }
 
-__global__ void __launch_bounds__(kAssignThreads, 1)
-k_assign(AssignArgs a) {
+__device__ __forceinline__ void assign_chain(const ChainArgs& a, int64_t smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (a.sc->tile_used) return;   // the dense-tile engine labelled this sweep
     const int K = a.sc->K;
@@ -530,7 +534,7 @@ k_assign(AssignArgs a) {
     const size_t head = ((size_t)(reinterpret_cast<unsigned char*>(slw + 4 * K) - smem_raw) + 15) &
                         ~(size_t)15;
     unsigned char* rest = smem_raw + head;
-    const int64_t avail = a.smem_bytes - (int64_t)head;
+    const int64_t avail = smem_bytes - (int64_t)head;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         blk_sumlogq[k] = 0.0;
         spi[k] = a.logpi[k];
@@ -560,13 +564,13 @@ k_assign(AssignArgs a) {
         if (sub_in)
             for (int64_t i = threadIdx.x; i < (int64_t)D * K; i += blockDim.x) {
                 const int64_t u = i / K, k = i - u * K;
-                sLs[i] = __ldg(a.Ls2 + u * a.kmax + k);
+                sLs[i] = __ldg(reinterpret_cast<const float2*>(a.Ls) + u * a.kmax + k);
             }
         if (fused)
             for (int64_t i = threadIdx.x; i < (int64_t)2 * K * D; i += blockDim.x) sS[i] = 0u;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->stats_fused = fused ? 1 : 0;
         __syncthreads();
-        const float2* Ls2 = sub_in ? sLs : a.Ls2;
+        const float2* Ls2 = sub_in ? sLs : reinterpret_cast<const float2*>(a.Ls);
         const int ldS = sub_in ? K : a.kmax;
         if (K <= 4) assign_cells_v2<4>(a, sLc, Kp, Ls2, ldS, K, t, spi, slw, wsq, wn, sS);
         else if (K <= 8) assign_cells_v2<8>(a, sLc, Kp, Ls2, ldS, K, t, spi, slw, wsq, wn, sS);
@@ -609,45 +613,64 @@ k_assign(AssignArgs a) {
         if (blk_sumlogq[k] != 0.0) atomicAdd(&a.acc_sumlogq[k], blk_sumlogq[k]);
 }
 
+
+// Every chain of the table in turn (a chain labelled by the dense-tile engine
+// returns at once), each with all blocks.
+template <class Tab>
+__global__ void __launch_bounds__(kAssignThreads, 1)
+k_assign(const __grid_constant__ Tab tab, int64_t smem_bytes) {
+    for (int b = 0; b < tab.n(); ++b) {
+        assign_chain(tab[b], smem_bytes);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Sufficient statistics n-bar[k][r], S-bar[k][r][u] of the cells whose
 // cluster passes `mask` (all cells if mask is null), added into nsub / Ssub.
 // Block-private shared-memory counters when 2 K D words fit, else direct
 // global atomics.  Integer sums: the result is exact and order-independent.
 // ---------------------------------------------------------------------------
+template <class Tab>
 __global__ void __launch_bounds__(kStatsThreads, 1)
-k_stats(Csr csr, const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
-        const uint8_t* __restrict__ mask, uint32_t* __restrict__ nsub,
-        uint32_t* __restrict__ Ssub, int64_t N, int32_t D, int64_t priv_cap, int sweep) {
+k_stats(const __grid_constant__ Tab tab, int64_t priv_cap, int sweep) {
     extern __shared__ __align__(16) uint32_t spriv[];
-    // a sweep's statistics: only when the CSR label kernel did not add them
-    if (sweep && (sc->stats_fused || sc->tile_used)) return;
-    stats_cells(csr, state, mask, nsub, Ssub, N, D, sc->K, spriv, priv_cap);
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        const DevScalars* sc = ch.sc;
+        if (sweep) {
+            // a sweep's statistics into the accumulators, unless the CSR label
+            // kernel added them (or the dense-tile configuration counts them)
+            if (sc->stats_fused || sc->tile_used) continue;
+            stats_cells(ch.csr, ch.state, nullptr, ch.acc_nsub, ch.acc_Ssub, ch.N, ch.D, sc->K,
+                        spriv, priv_cap);
+        } else {
+            // every cell into the main statistics (cleared by the caller)
+            stats_cells(ch.csr, ch.state, nullptr, ch.nsub, ch.Ssub, ch.N, ch.D, sc->K, spriv,
+                        priv_cap);
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Commit of a CSR-labelled sweep's statistics.
 // ---------------------------------------------------------------------------
-// Rows [0, 2 K_rows) of src (and, if given, the 2 K_rows counts of nsrc):
-// copied to dst / ndst and cleared.  K_rows is sc->K (use_new = 0) or
-// sc->K_new (use_new = 1).  gate 1: only when the pending plan is applied;
-// gate 2: only when the CSR engine labelled the sweep.
-__global__ void k_copy_clear(const DevScalars* __restrict__ sc, uint32_t* __restrict__ src,
-                             uint32_t* __restrict__ dst, uint32_t* __restrict__ nsrc,
-                             uint32_t* __restrict__ ndst, int32_t D, int use_new, int gate) {
-    if ((gate == 1 && !sc->apply) || (gate == 2 && sc->tile_used)) return;
-    const int Kr = use_new ? sc->K_new : sc->K;
-    const int64_t total = (int64_t)2 * Kr * D;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (dst) dst[i] = src[i];
-        src[i] = 0u;
-    }
-    if (nsrc && blockIdx.x == 0)
-        for (int i = threadIdx.x; i < 2 * Kr; i += blockDim.x) {
-            ndst[i] = nsrc[i];
-            nsrc[i] = 0u;
+// A CSR-labelled sweep's S-bar rows [0, 2K) move from the accumulator into
+// the main statistics (the accumulator is cleared); chains labelled by the
+// dense-tile engine are skipped (their counts went to the main rows directly).
+template <class Tab>
+__global__ void k_csr_commit(const __grid_constant__ Tab tab) {
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        if (ch.sc->tile_used) continue;
+        const int64_t total = (int64_t)2 * ch.sc->K * ch.D;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            ch.Ssub[i] = ch.acc_Ssub[i];
+            ch.acc_Ssub[i] = 0u;
         }
+    }
 }
 
 __global__ void k_init_state(uint32_t* __restrict__ state, int64_t N, Stream st) {
@@ -714,10 +737,13 @@ cudaError_t configure_launches(Ctx& c) {
     c.smem_optin = (size_t)optin;
     c.assign_smem = (size_t)optin;
     c.stats_smem = (size_t)optin;
-    if ((e = cudaFuncSetAttribute(k_assign, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)c.assign_smem)))
-        return e;
-    if ((e = cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_assign<TabV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)c.assign_smem)) ||
+        (e = cudaFuncSetAttribute(k_assign<TabP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)c.assign_smem)) ||
+        (e = cudaFuncSetAttribute(k_stats<TabV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)c.stats_smem)) ||
+        (e = cudaFuncSetAttribute(k_stats<TabP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)c.stats_smem)))
         return e;
     c.assign_blocks = c.num_sms;
@@ -726,66 +752,55 @@ cudaError_t configure_launches(Ctx& c) {
 }
 
 cudaError_t launch_draw_params(Ctx& c) {
-    const int rows = 3 * c.kmax + 1;
-    const int grid = rows < 2 * c.num_sms ? rows : 2 * c.num_sms;
-    k_draw_params<<<grid, kDrawThreads, 0, c.stream>>>(
-        c.sc, c.nsub, c.Ssub, c.Lc, c.Ls, c.logpi, c.D, c.kmax, (float)c.alpha, (float)c.beta,
-        make_stream(c.opts.seed, c.opts.chain_id), c.tile_enabled ? 1 : 0, c.acc_nsub,
-        c.acc_sumlogq);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_draw_params<<<2 * c.num_sms, kDrawThreads, 0, c.stream>>>(tab);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_select_engine(Ctx& c) {
-    k_select_engine<<<1, 256, 0, c.stream>>>(c.sc, c.tile_enabled ? 1 : 0, c.acc_nsub,
-                                              c.acc_sumlogq);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_select_engine<<<c.nchains < c.num_sms ? c.nchains : c.num_sms, 256, 0, c.stream>>>(tab);
+        return cudaGetLastError();
+    });
 }
 
-// CSR labelling kernel (returns at once when the dense-tile engine labels the
-// sweep); its statistics go to the accumulators, see launch_csr_commit.
+// CSR labelling kernel (returns at once for a chain the dense-tile engine
+// labels); its statistics go to the accumulators, see launch_csr_commit.
 cudaError_t launch_assign(Ctx& c) {
-    AssignArgs a;
-    a.csr = csr_of(c);
-    a.sc = c.sc;
-    a.state = c.state;
-    a.nsub = c.nsub;
-    a.logpi = c.logpi;
-    a.Lc = c.Lc;
-    a.Ls2 = reinterpret_cast<const float2*>(c.Ls);
-    a.acc_sumlogq = c.acc_sumlogq;
-    a.N = c.N;
-    a.D = c.D;
-    a.kmax = c.kmax;
-    a.acc_nsub = c.acc_nsub;
-    a.acc_Ssub = c.acc_Ssub;
-    a.smem_bytes = (int64_t)c.assign_smem;
-    a.st = make_stream(c.opts.seed, c.opts.chain_id);
-    k_assign<<<c.assign_blocks, kAssignThreads, c.assign_smem, c.stream>>>(a);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_assign<<<c.assign_blocks, kAssignThreads, c.assign_smem, c.stream>>>(
+            tab, (int64_t)c.assign_smem);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_stats(Ctx& c, const uint8_t* mask, uint32_t* nsub, uint32_t* Ssub) {
-    k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
-        csr_of(c), c.sc, c.state, mask, nsub, Ssub, c.N, c.D,
-        (int64_t)(c.stats_smem / sizeof(uint32_t)), 0);
-    return cudaGetLastError();
+// Main statistics of every chain from its cell states (main rows cleared first).
+cudaError_t launch_recount(Ctx& c) {
+    return with_table(c, [&](auto tab) {
+        k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
+            tab, (int64_t)(c.stats_smem / sizeof(uint32_t)), 0);
+        return cudaGetLastError();
+    });
 }
 
 // Statistics of a CSR-labelled sweep unless the label kernel already added them.
 cudaError_t launch_sweep_stats(Ctx& c) {
-    k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
-        csr_of(c), c.sc, c.state, nullptr, c.acc_nsub, c.acc_Ssub, c.N, c.D,
-        (int64_t)(c.stats_smem / sizeof(uint32_t)), 1);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
+            tab, (int64_t)(c.stats_smem / sizeof(uint32_t)), 1);
+        return cudaGetLastError();
+    });
 }
 
 // A CSR-labelled sweep's S-bar becomes the main S-bar (the dense-tile
 // configuration adds it there itself); the accumulator is cleared.  n-bar stays
 // in the accumulator for the compaction.
 cudaError_t launch_csr_commit(Ctx& c) {
-    k_copy_clear<<<2 * c.num_sms, 256, 0, c.stream>>>(c.sc, c.acc_Ssub, c.Ssub, nullptr,
-                                                       nullptr, c.D, 0, 2);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_csr_commit<<<2 * c.num_sms, 256, 0, c.stream>>>(tab);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_init_state(Ctx& c) {

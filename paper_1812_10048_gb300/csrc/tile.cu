@@ -132,15 +132,22 @@ __device__ __forceinline__ float bf16_value(uint16_t b) {
     return __uint_as_float((uint32_t)b << 16);
 }
 
-// B operand of one sweep: block (c, q) fills rows 16q .. 16q + 15 of chunk c
-// (genes 64c .. 64c + 63); every block of chunk c forms the same m_u.  In a
-// step (force = 0) the blocks first clear the main S-bar rows.
+// B operand of one sweep: block (c, q, b) fills rows 16q .. 16q + 15 of chunk
+// c (genes 64c .. 64c + 63) of chain b; every block of chunk c forms the same
+// m_u.  In a step (force = 0) the blocks of chain b first clear its main
+// S-bar rows.
+template <class Tab>
 __global__ void __launch_bounds__(256)
-k_build_b(const DevScalars* __restrict__ sc, const float* __restrict__ Lc,
-          const float* __restrict__ Ls, unsigned char* __restrict__ B, int32_t D, int32_t kmax,
-          uint32_t* __restrict__ Ssub, int32_t force) {
+k_build_b(const __grid_constant__ Tab tab, int32_t force) {
     __shared__ float part[4][64];
     __shared__ float m[64];
+    const ChainArgs& ch = tab[blockIdx.z];
+    const DevScalars* sc = ch.sc;
+    const float* __restrict__ Lc = ch.Lc;
+    const float* __restrict__ Ls = ch.Ls;
+    unsigned char* __restrict__ B = ch.tile_B;
+    uint32_t* __restrict__ Ssub = ch.Ssub;
+    const int32_t D = ch.D, kmax = ch.kmax;
     const int K = sc->K;
     if (!force) {
         // the main S-bar rows are dead from here until the statistics kernel
@@ -151,8 +158,9 @@ k_build_b(const DevScalars* __restrict__ sc, const float* __restrict__ Lc,
              i < words; i += nthr)
             Ssub[i] = 0u;
     }
-    if (!tile_usable(K) || (!force && !sc->tile_used)) return;
+    if (!ch.tile_enabled || !tile_usable(K) || (!force && !sc->tile_used)) return;
     const int c = blockIdx.x;
+    if (c >= ch.tile_C) return;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
     if ((int)blockIdx.y * 16 >= Ntot) return;
     {
@@ -197,22 +205,19 @@ k_build_b(const DevScalars* __restrict__ sc, const float* __restrict__ Lc,
     }
 }
 
-struct TileArgs {
-    const uint32_t* ent;      // blocked entries: row << 22 | gene-in-chunk << 16 | count
-    const int32_t* ptr;       // [4 T C + 1] quarter starts of every (tile, chunk) segment
-    const unsigned char* B;   // [C][kBChunkBytes]
-    DevScalars* sc;
-    uint32_t* state;
-    const uint32_t* nsub;
-    const float* logpi;
-    double* acc_sumlogq;
-    float* dbg;               // optional [N][3K] centred scores; no state/statistics writes
-    int64_t N;
-    int32_t D, C, T;
-    int32_t Lslot;            // entries per segment slot (longest padded segment)
-    int64_t smem_bytes;
-    Stream st;
-};
+
+// Chains the dense-tile engine labels in this launch.  Their tiles form one
+// list (chain order) dealt round-robin to the CTAs: chain b's tiles handled
+// by this CTA are first, first + gridDim.x, ... (cnt of them), where off is
+// the number of listed tiles before chain b.
+__device__ __forceinline__ bool chain_on_tiles(const ChainArgs& ch, bool dbg) {
+    return ch.tile_enabled && tile_usable(ch.sc->K) && (dbg || ch.sc->tile_used);
+}
+__device__ __forceinline__ void chain_tiles(int64_t off, int T, int& first, int& cnt) {
+    const int64_t G = gridDim.x;
+    first = (int)((((int64_t)blockIdx.x - off) % G + G) % G);
+    cnt = first < T ? (T - 1 - first) / (int)G + 1 : 0;
+}
 
 // Warp roles of the pipelined engine (19 warps):
 //   warps 0-7   epilogue, two halves of four warps over the same 128 cells
@@ -227,6 +232,8 @@ struct TileArgs {
 //   warp 17     segment loader: bulk-copies each chunk's entries into a ring
 //               of slots, reading the segment table a warp-batch ahead
 //   warp 18     lane 0 bulk-copies the B operand of each chunk into its ring
+// Every role walks the same sequence: the chains in order, this CTA's tiles
+// of each chain, the chunks of each tile.
 // Hand-offs are mbarriers: ent_full / ent_free (segment slots), a_full (four
 // producer warps -> MMA) / stage_free (MMA commit -> producers), b_full /
 // b_free (B slots), acc_full (MMA -> epilogue) / acc_empty (epilogue -> MMA).
@@ -246,27 +253,44 @@ constexpr int kBarEpi = 1, kBarLabel = 2;
 constexpr int kSmallBytes = 8192;
 constexpr int kScatter = 12;         // entries per producer lane and batch
 
+// dbg: optional [N][3K] centred scores of a single chain (no state or
+// statistics writes).
+template <class Tab>
 __global__ void __launch_bounds__(kTileThreadsP, 1)
-k_assign_tc(TileArgs a) {
+k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int K = a.sc->K;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (!tile_usable(K) || (!a.dbg && !a.sc->tile_used)) return;
-    const int S0 = tile_s0(K), Ntot = tile_ntot(K);
-    const uint32_t t = a.sc->t;
+    const bool dbg = dbg_out != nullptr;
+    // this CTA's work and the largest operand / segment over the chains
+    uint32_t total = 0;   // chunks of this block
+    int ntot_max = 0, lslot_max = 4;
+    {
+        int64_t off = 0;
+        for (int b = 0; b < tab.n(); ++b) {
+            const ChainArgs& ch = tab[b];
+            if (!chain_on_tiles(ch, dbg)) continue;
+            int first, cnt;
+            chain_tiles(off, ch.tile_T, first, cnt);
+            off += ch.tile_T;
+            total += (uint32_t)cnt * (uint32_t)ch.tile_C;
+            ntot_max = max(ntot_max, tile_ntot(ch.sc->K));
+            lslot_max = max(lslot_max, ch.tile_Lslot);
+        }
+    }
+    if (total == 0) return;
     // shared-memory plan (identical in every thread): A stages, B slots,
     // segment slots, then the small area
-    const int64_t b_slot = ((int64_t)Ntot * 128 + 1023) & ~(int64_t)1023;
-    const int64_t e_slot = (int64_t)a.Lslot * 4;
-    const int64_t avail = a.smem_bytes - (int64_t)(base - smem_raw) - kSmallBytes;
+    const int64_t b_slot = ((int64_t)ntot_max * 128 + 1023) & ~(int64_t)1023;
+    const int64_t e_slot = (int64_t)lslot_max * 4;
+    const int64_t avail = smem_bytes - (int64_t)(base - smem_raw) - kSmallBytes;
     const int nS = (int64_t)kMaxStages * 32768 + 2 * b_slot + 2 * e_slot <= avail ? kMaxStages : 2;
     const int nB = (int)min((int64_t)kMaxBSlots, (avail - nS * 32768 - 2 * e_slot) / b_slot);
     const int nE = (int)min((int64_t)kMaxESlots,
                             (avail - nS * 32768 - (int64_t)max(nB, 0) * b_slot) / e_slot);
     if (nB < 2 || nE < 2) {
-        if (tid == 0) atomicExch(&a.sc->error, DPMM_ECAPACITY);
+        if (tid == 0) atomicExch(&tab[0].sc->error, DPMM_ECAPACITY);
         return;
     }
     unsigned char* A_base = base;                                  // stage s: lo, then hi
@@ -295,13 +319,6 @@ k_assign_tc(TileArgs a) {
     float* xg0 = reinterpret_cast<float*>(xc + 256);                // [2][128]
     float* xg1 = xg0 + 256;                                         // [2][128]
 
-    for (int k = tid; k < K; k += blockDim.x) spi[k] = a.logpi[k];
-    for (int i = tid; i < 2 * K; i += blockDim.x) {
-        const float n = (float)a.nsub[i];
-        slw[2 * i] = n > 0.0f ? logf(n) : -CUDART_INF_F;
-        slw[2 * i + 1] = n > 1.0f ? logf(n - 1.0f) : -CUDART_INF_F;
-    }
-    for (int i = tid; i < 4 * K; i += blockDim.x) wsq[i] = 0.0f;
     if (tid < 4 * kMaxStages) stage_hib[tid] = 0;
     {
         // the hi halves start clear: a producer warp clears its quarter of a hi
@@ -342,9 +359,6 @@ k_assign_tc(TileArgs a) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *taddr_s;
-    const uint32_t my_tiles =
-        (int)blockIdx.x < a.T ? (uint32_t)((a.T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1) : 0u;
-    const uint32_t total = my_tiles * (uint32_t)a.C;   // chunks of this block
 
     if (warp >= kProdWarp0 && warp < kMmaWarp) {
         // ---------------- producers ----------------
@@ -412,125 +426,170 @@ k_assign_tc(TileArgs a) {
         }
     } else if (warp == kELoadWarp) {
         // ---------------- segment loader ----------------
-        // lane j holds the five quarter pointers of chunk gb + j
-        auto seg_ptrs = [&](uint32_t g, int32_t (&p)[5]) {
-            if (g < total) {
-                const uint32_t ti = g / (uint32_t)a.C, ci = g - ti * (uint32_t)a.C;
-                const int64_t sgm = ((int64_t)blockIdx.x + (int64_t)ti * gridDim.x) * a.C + ci;
+        uint32_t g = 0;        // chunks started (slot sequence)
+        bool stop_l = false;
+        int64_t off = 0;
+        for (int b = 0; b < tab.n() && !stop_l; ++b) {
+            const ChainArgs& ch = tab[b];
+            if (!chain_on_tiles(ch, dbg)) continue;
+            int first, cnt;
+            chain_tiles(off, ch.tile_T, first, cnt);
+            off += ch.tile_T;
+            const uint32_t C = (uint32_t)ch.tile_C;
+            const uint32_t nchunk = (uint32_t)cnt * C;
+            // lane j holds the five quarter pointers of chunk jb + j of this chain
+            auto seg_ptrs = [&](uint32_t j, int32_t (&p)[5]) {
+                if (j < nchunk) {
+                    const uint32_t ti = j / C, ci = j - ti * C;
+                    const int64_t sgm =
+                        ((int64_t)first + (int64_t)ti * gridDim.x) * (int64_t)C + ci;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) p[k] = __ldg(a.ptr + 4 * sgm + k);
-            } else {
+                    for (int k = 0; k < 5; ++k) p[k] = __ldg(ch.tile_ptr + 4 * sgm + k);
+                } else {
 #pragma unroll
-                for (int k = 0; k < 5; ++k) p[k] = 0;
-            }
-        };
-        int32_t cur[5], nxt[5];
-        seg_ptrs((uint32_t)lane, cur);
-        uint32_t issued = 0;   // chunks whose copy was started
-        for (uint32_t gb = 0; gb < total; gb += 32) {
-            if (__any_sync(0xFFFFFFFFu, *err != 0)) break;
-            seg_ptrs(gb + 32 + (uint32_t)lane, nxt);
-            bool stop_l = false;
-            for (uint32_t j = 0; j < 32 && gb + j < total; ++j) {
-                const uint32_t g = gb + j;
-                const int es = (int)(g % (uint32_t)nE);
-                int32_t p[5];
-#pragma unroll
-                for (int k = 0; k < 5; ++k) p[k] = __shfl_sync(0xFFFFFFFFu, cur[k], (int)j);
-                bool ok = true;
-                if (lane == 0 && g >= (uint32_t)nE)
-                    ok = tc::mbar_wait(&ent_free[es], ((g / (uint32_t)nE) - 1u) & 1u, kWaitLimit);
-                ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-                if (!ok && lane == 0) *err = DPMM_ETIMEOUT;
-                if (__any_sync(0xFFFFFFFFu, !ok || *err != 0)) {
+                    for (int k = 0; k < 5; ++k) p[k] = 0;
+                }
+            };
+            int32_t cur[5], nxt[5];
+            seg_ptrs((uint32_t)lane, cur);
+            for (uint32_t jb = 0; jb < nchunk; jb += 32) {
+                if (__any_sync(0xFFFFFFFFu, *err != 0)) {
                     stop_l = true;
                     break;
                 }
-                if (lane == 0) {
-                    int32_t* mt = meta + 4 * es;
-                    mt[0] = p[1] - p[0];
-                    mt[1] = p[2] - p[0];
-                    mt[2] = p[3] - p[0];
-                    mt[3] = p[4] - p[0];
-                    const uint32_t bytes = (uint32_t)(p[4] - p[0]) * 4u;
-                    if (bytes) {
-                        tc::mbar_arrive_expect_tx(&ent_full[es], bytes);
-                        tc::bulk_g2s(E_base + es * e_slot, a.ent + p[0], bytes, &ent_full[es]);
-                    } else {
-                        tc::mbar_arrive(&ent_full[es]);
+                seg_ptrs(jb + 32 + (uint32_t)lane, nxt);
+                for (uint32_t j = 0; j < 32 && jb + j < nchunk; ++j, ++g) {
+                    const int es = (int)(g % (uint32_t)nE);
+                    int32_t p[5];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) p[k] = __shfl_sync(0xFFFFFFFFu, cur[k], (int)j);
+                    bool ok = true;
+                    if (lane == 0 && g >= (uint32_t)nE)
+                        ok = tc::mbar_wait(&ent_free[es], ((g / (uint32_t)nE) - 1u) & 1u,
+                                           kWaitLimit);
+                    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+                    if (!ok && lane == 0) *err = DPMM_ETIMEOUT;
+                    if (__any_sync(0xFFFFFFFFu, !ok || *err != 0)) {
+                        stop_l = true;
+                        break;
+                    }
+                    if (lane == 0) {
+                        int32_t* mt = meta + 4 * es;
+                        mt[0] = p[1] - p[0];
+                        mt[1] = p[2] - p[0];
+                        mt[2] = p[3] - p[0];
+                        mt[3] = p[4] - p[0];
+                        const uint32_t bytes = (uint32_t)(p[4] - p[0]) * 4u;
+                        if (bytes) {
+                            tc::mbar_arrive_expect_tx(&ent_full[es], bytes);
+                            tc::bulk_g2s(E_base + es * e_slot, ch.tile_ent + p[0], bytes,
+                                         &ent_full[es]);
+                        } else {
+                            tc::mbar_arrive(&ent_full[es]);
+                        }
                     }
                 }
-                issued = g + 1;
-            }
-            if (stop_l) break;
+                if (stop_l) break;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) cur[k] = nxt[k];
+                for (int k = 0; k < 5; ++k) cur[k] = nxt[k];
+            }
         }
         // every started copy has landed before the block can exit
+        const uint32_t issued = g;
         if (lane == 0)
-            for (uint32_t g = issued > (uint32_t)nE ? issued - (uint32_t)nE : 0u; g < issued; ++g)
-                tc::mbar_wait(&ent_full[g % (uint32_t)nE], (g / (uint32_t)nE) & 1u, kWaitLimit);
+            for (uint32_t q = issued > (uint32_t)nE ? issued - (uint32_t)nE : 0u; q < issued; ++q)
+                tc::mbar_wait(&ent_full[q % (uint32_t)nE], (q / (uint32_t)nE) & 1u, kWaitLimit);
     } else if (warp == kBLoadWarp) {
         // ---------------- B loader ----------------
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)Ntot * 128u;
-            uint32_t issued = 0;
-            for (uint32_t g = 0; g < total; ++g) {
-                const int bs = (int)(g % (uint32_t)nB);
-                if (g >= (uint32_t)nB &&
-                    !tc::mbar_wait(&b_free[bs], ((g / (uint32_t)nB) - 1u) & 1u, kWaitLimit)) {
-                    *err = DPMM_ETIMEOUT;
-                    break;
+            uint32_t g = 0;
+            bool stop_b = false;
+            int64_t off = 0;
+            for (int b = 0; b < tab.n() && !stop_b; ++b) {
+                const ChainArgs& ch = tab[b];
+                if (!chain_on_tiles(ch, dbg)) continue;
+                int first, cnt;
+                chain_tiles(off, ch.tile_T, first, cnt);
+                off += ch.tile_T;
+                const uint32_t bytes = (uint32_t)tile_ntot(ch.sc->K) * 128u;
+                const uint32_t nchunk = (uint32_t)cnt * (uint32_t)ch.tile_C;
+                for (uint32_t j = 0; j < nchunk; ++j, ++g) {
+                    const int bs = (int)(g % (uint32_t)nB);
+                    if (g >= (uint32_t)nB &&
+                        !tc::mbar_wait(&b_free[bs], ((g / (uint32_t)nB) - 1u) & 1u, kWaitLimit)) {
+                        *err = DPMM_ETIMEOUT;
+                        stop_b = true;
+                        break;
+                    }
+                    if (*err) {
+                        stop_b = true;
+                        break;
+                    }
+                    const uint32_t c = j % (uint32_t)ch.tile_C;
+                    tc::mbar_arrive_expect_tx(&b_full[bs], bytes);
+                    tc::bulk_g2s(B_base + bs * b_slot, ch.tile_B + (size_t)c * kBChunkBytes, bytes,
+                                 &b_full[bs]);
                 }
-                if (*err) break;
-                const uint32_t c = g % (uint32_t)a.C;
-                tc::mbar_arrive_expect_tx(&b_full[bs], bytes);
-                tc::bulk_g2s(B_base + bs * b_slot, a.B + (size_t)c * kBChunkBytes, bytes,
-                             &b_full[bs]);
-                issued = g + 1;
             }
-            for (uint32_t g = issued > (uint32_t)nB ? issued - (uint32_t)nB : 0u; g < issued; ++g)
-                tc::mbar_wait(&b_full[g % (uint32_t)nB], (g / (uint32_t)nB) & 1u, kWaitLimit);
+            const uint32_t issued = g;
+            for (uint32_t q = issued > (uint32_t)nB ? issued - (uint32_t)nB : 0u; q < issued; ++q)
+                tc::mbar_wait(&b_full[q % (uint32_t)nB], (q / (uint32_t)nB) & 1u, kWaitLimit);
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
             uint32_t g = 0, it = 0;
-            const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)Ntot);
-            for (int tile = blockIdx.x; tile < a.T && !*err; tile += gridDim.x, ++it) {
-                const uint32_t buf = it & 1;
-                if (it >= 2 && !tc::mbar_wait(&acc_empty[buf], ((it >> 1) - 1) & 1, kWaitLimit)) {
-                    *err = DPMM_ETIMEOUT;
-                    break;
-                }
-                tc::fence_after_sync();
-                const uint32_t acc = tmem + buf * 256u;
-                for (int c = 0; c < a.C; ++c) {
-                    const int st = (int)(g % (uint32_t)nS), bs = (int)(g % (uint32_t)nB);
-                    if (!tc::mbar_wait(&a_full[st], (g / (uint32_t)nS) & 1u, kWaitLimit) ||
-                        !tc::mbar_wait(&b_full[bs], (g / (uint32_t)nB) & 1u, kWaitLimit)) {
+            bool stop_m = false;
+            int64_t off = 0;
+            for (int b = 0; b < tab.n() && !stop_m; ++b) {
+                const ChainArgs& ch = tab[b];
+                if (!chain_on_tiles(ch, dbg)) continue;
+                int first, cnt;
+                chain_tiles(off, ch.tile_T, first, cnt);
+                off += ch.tile_T;
+                const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)tile_ntot(ch.sc->K));
+                for (int i = 0; i < cnt && !stop_m; ++i, ++it) {
+                    if (*err) {
+                        stop_m = true;
+                        break;
+                    }
+                    const uint32_t buf = it & 1;
+                    if (it >= 2 &&
+                        !tc::mbar_wait(&acc_empty[buf], ((it >> 1) - 1) & 1, kWaitLimit)) {
                         *err = DPMM_ETIMEOUT;
+                        stop_m = true;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t alo = tc::smem_addr(A_base + st * 32768);
-                    const uint32_t bsm = tc::smem_addr(B_base + bs * b_slot);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        tc::mma_bf16(acc, tc::desc_sw128(alo + 32 * k), tc::desc_sw128(bsm + 32 * k),
-                                     idesc, (c | k) != 0);
-                    if (*reinterpret_cast<volatile uint32_t*>(stage_hib + 4 * st)) {
+                    const uint32_t acc = tmem + buf * 256u;
+                    for (int c = 0; c < ch.tile_C; ++c) {
+                        const int st = (int)(g % (uint32_t)nS), bs = (int)(g % (uint32_t)nB);
+                        if (!tc::mbar_wait(&a_full[st], (g / (uint32_t)nS) & 1u, kWaitLimit) ||
+                            !tc::mbar_wait(&b_full[bs], (g / (uint32_t)nB) & 1u, kWaitLimit)) {
+                            *err = DPMM_ETIMEOUT;
+                            stop_m = true;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t alo = tc::smem_addr(A_base + st * 32768);
+                        const uint32_t bsm = tc::smem_addr(B_base + bs * b_slot);
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            tc::mma_bf16(acc, tc::desc_sw128(alo + 16384 + 32 * k),
-                                         tc::desc_sw128(bsm + 32 * k), idesc, 1u);
+                            tc::mma_bf16(acc, tc::desc_sw128(alo + 32 * k),
+                                         tc::desc_sw128(bsm + 32 * k), idesc, (c | k) != 0);
+                        if (*reinterpret_cast<volatile uint32_t*>(stage_hib + 4 * st)) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                tc::mma_bf16(acc, tc::desc_sw128(alo + 16384 + 32 * k),
+                                             tc::desc_sw128(bsm + 32 * k), idesc, 1u);
+                        }
+                        tc::mma_commit(&stage_free[st]);
+                        tc::mma_commit(&b_free[bs]);
+                        ++g;
                     }
-                    tc::mma_commit(&stage_free[st]);
-                    tc::mma_commit(&b_free[bs]);
-                    ++g;
+                    if (stop_m) break;
+                    tc::mma_commit(&acc_full[buf]);
                 }
-                if (*err) break;
-                tc::mma_commit(&acc_full[buf]);
             }
             // the MMAs of the last chunk have completed (and signalled) before exit
             if (g > 0) {
@@ -544,115 +603,144 @@ k_assign_tc(TileArgs a) {
         const int h = warp >> 2, qw = warp & 3;
         const int r = 32 * qw + lane;
         uint32_t it = 0;
-        for (int tile = blockIdx.x; tile < a.T; tile += gridDim.x, ++it) {
-            const uint32_t buf = it & 1, xb = it & 1;
-            const bool ok = tc::mbar_wait(&acc_full[buf], (it >> 1) & 1, kWaitLimit);
-            if (!ok) *err = DPMM_ETIMEOUT;
-            tc::fence_after_sync();
-            const bool okw = __all_sync(0xFFFFFFFFu, ok);
-            const int64_t cell = (int64_t)tile * 128 + r;
-            const bool live = cell < a.N;
-            const uint32_t trow = tmem + buf * 256u + ((uint32_t)(32 * qw) << 16);
-            float best = -CUDART_INF_F;
-            int c = h ? K : 0;   // half 1's "none" loses every tie
-            if (okw) {
-                for (int q = h; q < S0 / 16; q += 2) {
-                    float v[16];
-                    tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
-                    tc::tmem_ld_wait();
-                    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+        bool halt = false;
+        int64_t off = 0;
+        for (int b = 0; b < tab.n() && !halt; ++b) {
+            const ChainArgs& ch = tab[b];
+            if (!chain_on_tiles(ch, dbg)) continue;
+            int first, cnt;
+            chain_tiles(off, ch.tile_T, first, cnt);
+            off += ch.tile_T;
+            if (!cnt) continue;
+            const int K = ch.sc->K;
+            const int S0 = tile_s0(K), Ntot = tile_ntot(K);
+            const uint32_t t = ch.sc->t;
+            // this chain's log pi, eq. 8 weights and log q sums in shared memory
+            tc::named_bar(kBarEpi, 32 * kEpiWarps);
+            for (int k = tid; k < K; k += 32 * kEpiWarps) spi[k] = ch.logpi[k];
+            for (int i = tid; i < 2 * K; i += 32 * kEpiWarps) {
+                const float n = (float)ch.nsub[i];
+                slw[2 * i] = n > 0.0f ? logf(n) : -CUDART_INF_F;
+                slw[2 * i + 1] = n > 1.0f ? logf(n - 1.0f) : -CUDART_INF_F;
+            }
+            for (int i = tid; i < 4 * K; i += 32 * kEpiWarps) wsq[i] = 0.0f;
+            tc::named_bar(kBarEpi, 32 * kEpiWarps);
+            for (int ti = 0; ti < cnt; ++ti, ++it) {
+                const int tile = first + ti * (int)gridDim.x;
+                const uint32_t buf = it & 1, xb = it & 1;
+                const bool ok = tc::mbar_wait(&acc_full[buf], (it >> 1) & 1, kWaitLimit);
+                if (!ok) *err = DPMM_ETIMEOUT;
+                tc::fence_after_sync();
+                const bool okw = __all_sync(0xFFFFFFFFu, ok);
+                const int64_t cell = (int64_t)tile * 128 + r;
+                const bool live = cell < ch.N;
+                const uint32_t trow = tmem + buf * 256u + ((uint32_t)(32 * qw) << 16);
+                float best = -CUDART_INF_F;
+                int c = h ? K : 0;   // half 1's "none" loses every tie
+                if (okw) {
+                    for (int q = h; q < S0 / 16; q += 2) {
+                        float v[16];
+                        tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
+                        tc::tmem_ld_wait();
+                        uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int k = 8 * q + i;
-                        if ((i & 3) == 0 && k < K)
-                            w4 = a.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
-                        if (k < K) {
-                            const float sc = v[2 * i] + v[2 * i + 1];
-                            if (a.dbg && live) a.dbg[(size_t)cell * 3 * K + k] = sc;
-                            const float val = (spi[k] + sc) + gumbel(word_of(w4, i & 3));
-                            if (val > best) {
-                                best = val;
-                                c = k;
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = 8 * q + i;
+                            if ((i & 3) == 0 && k < K)
+                                w4 = ch.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
+                            if (k < K) {
+                                const float sc = v[2 * i] + v[2 * i + 1];
+                                if (dbg && live) dbg_out[(size_t)cell * 3 * K + k] = sc;
+                                const float val = (spi[k] + sc) + gumbel(word_of(w4, i & 3));
+                                if (val > best) {
+                                    best = val;
+                                    c = k;
+                                }
                             }
                         }
                     }
                 }
-            }
-            if (h == 1) {
-                xbest[128 * xb + r] = best;
-                xc[128 * xb + r] = c;
-                const uint4 hw = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
-                xg0[128 * xb + r] = gumbel(hw.x);
-                xg1[128 * xb + r] = gumbel(hw.y);
-            }
-            tc::fence_before_sync();
-            if (tid == 0) stop[xb] = *err;
-            tc::named_bar(kBarEpi, 32 * kEpiWarps);
-            if (stop[xb]) break;
-            if (h == 1) continue;
-            {
-                const float b1 = xbest[128 * xb + r];
-                const int c1 = xc[128 * xb + r];
-                if (b1 > best || (b1 == best && c1 < c)) {
-                    best = b1;
-                    c = c1;
+                if (h == 1) {
+                    xbest[128 * xb + r] = best;
+                    xc[128 * xb + r] = c;
+                    const uint4 hw = ch.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+                    xg0[128 * xb + r] = gumbel(hw.x);
+                    xg1[128 * xb + r] = gumbel(hw.y);
                 }
-            }
-            float t0 = 0.0f, t1 = 0.0f;
-            const int s0 = S0 + 4 * c;
-            for (int q = S0 / 16; q < Ntot / 16; ++q) {
-                float v[16];
-                tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
-                tc::tmem_ld_wait();
-                if (a.dbg && live) {
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const int col = 16 * q + i - S0;
-                        if (col < 4 * K)
-                            a.dbg[(size_t)cell * 3 * K + K + (col >> 1)] = v[i] + v[i + 1];
+                tc::fence_before_sync();
+                if (tid == 0) stop[xb] = *err;
+                tc::named_bar(kBarEpi, 32 * kEpiWarps);
+                if (stop[xb]) {
+                    halt = true;
+                    break;
+                }
+                if (h == 1) continue;
+                {
+                    const float b1 = xbest[128 * xb + r];
+                    const int c1 = xc[128 * xb + r];
+                    if (b1 > best || (b1 == best && c1 < c)) {
+                        best = b1;
+                        c = c1;
                     }
                 }
-                if ((s0 >> 4) == q) {
-                    const int o = s0 & 15;
-                    if (o == 0) { t0 = v[0] + v[1]; t1 = v[2] + v[3]; }
-                    else if (o == 4) { t0 = v[4] + v[5]; t1 = v[6] + v[7]; }
-                    else if (o == 8) { t0 = v[8] + v[9]; t1 = v[10] + v[11]; }
-                    else { t0 = v[12] + v[13]; t1 = v[14] + v[15]; }
+                float t0 = 0.0f, t1 = 0.0f;
+                const int s0 = S0 + 4 * c;
+                for (int q = S0 / 16; q < Ntot / 16; ++q) {
+                    float v[16];
+                    tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
+                    tc::tmem_ld_wait();
+                    if (dbg && live) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            const int col = 16 * q + i - S0;
+                            if (col < 4 * K)
+                                dbg_out[(size_t)cell * 3 * K + K + (col >> 1)] = v[i] + v[i + 1];
+                        }
+                    }
+                    if ((s0 >> 4) == q) {
+                        const int o = s0 & 15;
+                        if (o == 0) { t0 = v[0] + v[1]; t1 = v[2] + v[3]; }
+                        else if (o == 4) { t0 = v[4] + v[5]; t1 = v[6] + v[7]; }
+                        else if (o == 8) { t0 = v[8] + v[9]; t1 = v[10] + v[11]; }
+                        else { t0 = v[12] + v[13]; t1 = v[14] + v[15]; }
+                    }
                 }
+                tc::fence_before_sync();
+                if (live && !dbg) {
+                    const uint32_t old = ch.state[cell];
+                    const bool stays = state_label(old) == (uint32_t)c;
+                    const uint32_t so = state_sub(old);
+                    const float lw0 = slw[4 * c + (stays && so == 0 ? 1 : 0)];
+                    const float lw1 = slw[4 * c + 2 + (stays && so == 1 ? 1 : 0)];
+                    const bool both_empty = lw0 == -CUDART_INF_F && lw1 == -CUDART_INF_F;
+                    const float l0 = (both_empty ? 0.0f : lw0) + t0;
+                    const float l1 = (both_empty ? 0.0f : lw1) + t1;
+                    const uint32_t s =
+                        (l1 + xg1[128 * xb + r] > l0 + xg0[128 * xb + r]) ? 1u : 0u;
+                    const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
+                    const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
+                    ch.state[cell] = pack_state((uint32_t)c, s);
+                    atomicAdd(&wsq[qw * K + c], logq);
+                }
+                tc::named_bar(kBarLabel, 128);
+                if (tid == 0) tc::mbar_arrive(&acc_empty[buf]);
             }
-            tc::fence_before_sync();
-            if (live && !a.dbg) {
-                const uint32_t old = a.state[cell];
-                const bool stays = state_label(old) == (uint32_t)c;
-                const uint32_t so = state_sub(old);
-                const float lw0 = slw[4 * c + (stays && so == 0 ? 1 : 0)];
-                const float lw1 = slw[4 * c + 2 + (stays && so == 1 ? 1 : 0)];
-                const bool both_empty = lw0 == -CUDART_INF_F && lw1 == -CUDART_INF_F;
-                const float l0 = (both_empty ? 0.0f : lw0) + t0;
-                const float l1 = (both_empty ? 0.0f : lw1) + t1;
-                const uint32_t s =
-                    (l1 + xg1[128 * xb + r] > l0 + xg0[128 * xb + r]) ? 1u : 0u;
-                const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
-                const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
-                a.state[cell] = pack_state((uint32_t)c, s);
-                atomicAdd(&wsq[qw * K + c], logq);
-            }
-            tc::named_bar(kBarLabel, 128);
-            if (tid == 0) tc::mbar_arrive(&acc_empty[buf]);
+            if (halt) break;
+            // this chain's sum log q (per cluster, over its tiles of this block)
+            tc::named_bar(kBarEpi, 32 * kEpiWarps);
+            if (!dbg)
+                for (int k = tid; k < K; k += 32 * kEpiWarps) {
+                    const double v = (double)wsq[k] + wsq[K + k] + wsq[2 * K + k] + wsq[3 * K + k];
+                    if (v != 0.0) atomicAdd(&ch.acc_sumlogq[k], v);
+                }
         }
     }
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
-    if (*err) {
-        if (tid == 0) atomicExch(&a.sc->error, *err);
-        return;
-    }
-    if (a.dbg) return;
-    for (int k = tid; k < K; k += blockDim.x) {
-        const double v = (double)wsq[k] + wsq[K + k] + wsq[2 * K + k] + wsq[3 * K + k];
-        if (v != 0.0) atomicAdd(&a.acc_sumlogq[k], v);
-    }
+    if (*err && tid == 0)
+        for (int b = 0; b < tab.n(); ++b)
+            if (chain_on_tiles(tab[b], dbg)) atomicExch(&tab[b].sc->error, *err);
 }
 
 // Statistics n-bar[k][r], S-bar[k][r][u] of the sweep's labels (from either
@@ -702,14 +790,16 @@ __device__ __forceinline__ void count_segments(T_* priv, int ld, uint32_t* pn, u
     }
 }
 
-__global__ void __launch_bounds__(kStatsTileThreads)
-k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ state,
-             const uint32_t* __restrict__ ent, const int32_t* __restrict__ ptr, int32_t T,
-             int32_t C, int64_t N, int32_t D, uint32_t* __restrict__ acc_nsub,
-             uint32_t* __restrict__ Ssub) {
-    __shared__ uint32_t cache[kStatsTileThreads / 32][128];
-    __shared__ uint32_t priv[2 * kTileMaxK * 64];
-    __shared__ uint32_t pn[2 * kTileMaxK];
+__device__ __forceinline__ void
+stats_tile_chain(const ChainArgs& ch, uint32_t (*cache)[128], uint32_t* priv, uint32_t* pn) {
+    const DevScalars* sc = ch.sc;
+    const uint32_t* __restrict__ state = ch.state;
+    const uint32_t* __restrict__ ent = ch.tile_ent;
+    const int32_t* __restrict__ ptr = ch.tile_ptr;
+    const int32_t T = ch.tile_T, C = ch.tile_C, D = ch.D;
+    const int64_t N = ch.N;
+    uint32_t* __restrict__ acc_nsub = ch.acc_nsub;
+    uint32_t* __restrict__ Ssub = ch.Ssub;
     const int K = sc->K;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
@@ -735,49 +825,55 @@ k_stats_tile(const DevScalars* __restrict__ sc, const uint32_t* __restrict__ sta
             if (pn[i]) atomicAdd(&acc_nsub[i], pn[i]);
 }
 
+// Every chain of the table in turn, each with the whole grid.
+template <class Tab>
+__global__ void __launch_bounds__(kStatsTileThreads)
+k_stats_tile(const __grid_constant__ Tab tab) {
+    __shared__ uint32_t cache[kStatsTileThreads / 32][128];
+    __shared__ uint32_t priv[2 * kTileMaxK * 64];
+    __shared__ uint32_t pn[2 * kTileMaxK];
+    for (int b = 0; b < tab.n(); ++b) {
+        if (!tab[b].tile_enabled) continue;
+        stats_tile_chain(tab[b], cache, priv, pn);
+        __syncthreads();
+    }
+}
+
 int32_t tile_stat_groups(const Ctx& c) { return max(1, (2 * c.num_sms) / c.tile_C); }
 
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
 
 cudaError_t configure_tile(Ctx& c) {
-    return cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_assign_tc<TabV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)c.smem_optin);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_assign_tc<TabP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)c.smem_optin);
 }
 
 cudaError_t launch_build_b(Ctx& c, bool force) {
-    k_build_b<<<dim3(c.tile_C, kNtotMax / 16), 256, 0, c.stream>>>(
-        c.sc, c.Lc, c.Ls, c.tile_B, c.D, c.kmax, c.Ssub, force ? 1 : 0);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_build_b<<<dim3(c.tile_C, kNtotMax / 16, c.nchains), 256, 0, c.stream>>>(tab,
+                                                                                  force ? 1 : 0);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_tile_label(Ctx& c, float* dbg) {
-    TileArgs a;
-    a.ent = c.tile_ent;
-    a.ptr = c.tile_ptr;
-    a.B = c.tile_B;
-    a.sc = c.sc;
-    a.state = c.state;
-    a.nsub = c.nsub;
-    a.logpi = c.logpi;
-    a.acc_sumlogq = c.acc_sumlogq;
-    a.dbg = dbg;
-    a.N = c.N;
-    a.D = c.D;
-    a.C = c.tile_C;
-    a.T = c.tile_T;
-    a.Lslot = c.tile_Lslot;
-    a.smem_bytes = (int64_t)c.smem_optin;
-    a.st = make_stream(c.opts.seed, c.opts.chain_id);
-    const int grid = c.tile_T < c.num_sms ? c.tile_T : c.num_sms;
-    k_assign_tc<<<grid, kTileThreadsP, c.smem_optin, c.stream>>>(a);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_assign_tc<<<c.num_sms, kTileThreadsP, c.smem_optin, c.stream>>>(
+            tab, dbg, (int64_t)c.smem_optin);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_tile_stats(Ctx& c) {
     const int nt = tile_stat_groups(c);   // tile groups per gene chunk
-    k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(
-        c.sc, c.state, c.tile_ent, c.tile_ptr, c.tile_T, c.tile_C, c.N, c.D, c.acc_nsub, c.Ssub);
-    return cudaGetLastError();
+    return with_table(c, [&](auto tab) {
+        k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(tab);
+        return cudaGetLastError();
+    });
 }
 
 // The whole dense-tile labelling: B operand, labels, statistics (dbg: scores

@@ -89,8 +89,10 @@ def test_chain_bound_logml_grad_matches_oracle(P):
         lbt = torch.from_numpy(lb).cuda()
         argt = None if arg is None else torch.from_numpy(np.ascontiguousarray(arg, np.int32)).cuda()
         val2, ga2, gb2 = P.dpmm_logml_grad(s.ctx, la, lbt, labels=argt, K=k)
-        assert val2 == val and ga2 == ga
-        np.testing.assert_array_equal(gb2, gb)
+        # the FP64 cluster sums are added in device order: equal up to rounding
+        assert abs(val2 - val) <= 1e-13 * abs(val)
+        assert abs(ga2 - ga) <= 1e-12 * max(1.0, abs(ga))
+        np.testing.assert_allclose(gb2, gb, rtol=1e-6, atol=1e-6)
     # the chain itself is untouched
     labels2, K2 = s.labels()
     assert K2 == K and np.array_equal(labels2, labels)
