@@ -78,6 +78,33 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices,
 void dpmm_free(dpmm_ctx* ctx);
 
 /*
+ * A batch of B independent chains (datasets of uneven size sharing D genes),
+ * stepped together: every kernel of a dpmm_step / dpmm_sweep /
+ * dpmm_split_merge on the batch is ONE launch over all chains (rows, tiles
+ * and proposals of all chains dealt to one grid), replayed from one CUDA
+ * graph.  Chain b is a full chain (as from dpmm_init) with its own data
+ * (indptr[b], indices[b], data[b] of N[b] cells), alpha[b], beta[b], and the
+ * random stream of chain_id = opts->chain_id + b; it evolves exactly as that
+ * single chain would.  All chains share opts otherwise and the batch's stream
+ * (stream, or a new one when NULL).  Paper: the sampler of §2 run for many
+ * datasets at once; the batching itself has no counterpart in the paper.
+ * Errors as dpmm_init (the first failing chain's).
+ */
+int dpmm_init_batch(dpmm_ctx** out, int32_t B, const int32_t* const* indptr,
+                    const int32_t* const* indices, const int32_t* const* data, const int64_t* N,
+                    int32_t D, const double* alpha, const double* beta, const dpmm_opts* opts,
+                    void* stream);
+
+/*
+ * Chain b of a batch (for a single-chain context: itself, b = 0), for every
+ * per-chain call (dpmm_labels, dpmm_get_state, dpmm_set_state, ...; those
+ * calls reject a batch context with DPMM_EINVAL).  The handle belongs to the
+ * batch: dpmm_free on it does nothing, and it is freed with the batch.
+ * dpmm_step / dpmm_sweep / dpmm_split_merge on it step that chain alone.
+ */
+int dpmm_chain(dpmm_ctx* batch, int32_t b, dpmm_ctx** chain);
+
+/*
  * n_sweeps blocked sweeps of eq. 4 (pi, theta, theta-bar from their Dirichlet
  * posteriors, eq. 19; every label from pi_k p(x_i | theta_k) and every
  * sub-label from eq. 8; Sections 2.1-2.3), each followed by removal of empty

@@ -17,7 +17,8 @@ from ._lib import (DpmmError, ENGINE_AUTO, ENGINE_CSR_FP32, ENGINE_TILE_BF16, ch
 __all__ = [
     "DpmmError", "Sampler", "LogML", "dpmm_default_opts", "dpmm_init", "dpmm_free", "dpmm_sweep",
     "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
-    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_get_state",
+    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_init_batch",
+    "dpmm_chain", "BatchSampler", "dpmm_get_state",
     "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
     "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_tile_scores", "dpmm_debug_moves", "dpmm_logml_create",
     "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_logml_grad_noalloc",
@@ -53,6 +54,31 @@ def dpmm_init(indptr, indices, data, N, D, alpha, beta, opts=None, stream=None):
 
 def dpmm_free(ctx):
     lib().dpmm_free(ctx)
+
+
+def dpmm_init_batch(csrs, Ns, D, alphas, betas, opts=None, stream=None):
+    """A batch of chains: csrs = [(indptr, indices, data), ...] (numpy or torch)."""
+    B = len(csrs)
+    arrs = [tuple(_i32(a) for a in t) for t in csrs]
+    P3 = ctypes.c_void_p * B
+    ip = P3(*[ptr(a[0]) for a in arrs])
+    ix = P3(*[ptr(a[1]) for a in arrs])
+    dt = P3(*[ptr(a[2]) for a in arrs])
+    n = np.ascontiguousarray(Ns, dtype=np.int64)
+    al = np.ascontiguousarray(alphas, dtype=np.float64)
+    be = np.ascontiguousarray(betas, dtype=np.float64)
+    h = ctypes.c_void_p()
+    o = opts if opts is not None else dpmm_default_opts()
+    check(lib().dpmm_init_batch(ctypes.byref(h), int(B), ip, ix, dt, ptr(n), int(D), ptr(al),
+                                ptr(be), ctypes.byref(o),
+                                ctypes.c_void_p(stream) if stream else None))
+    return h
+
+
+def dpmm_chain(ctx, b):
+    h = ctypes.c_void_p()
+    check(lib().dpmm_chain(ctx, int(b), ctypes.byref(h)))
+    return h
 
 
 def dpmm_sweep(ctx, n_sweeps=1):
@@ -298,6 +324,68 @@ class Sampler:
 
     def stats(self):
         return dpmm_get_stats(self.ctx, self.labels_K(), self.D)
+
+    def sync(self):
+        dpmm_sync(self.ctx)
+
+    def plans_applied(self):
+        return dpmm_plans_applied(self.ctx)
+
+    @property
+    def stream(self):
+        return dpmm_stream(self.ctx)
+
+
+class _ChainView(Sampler):
+    """Chain b of a BatchSampler (owned by the batch)."""
+
+    def __init__(self, batch, b, N, D, kmax):
+        self.N, self.D, self.kmax = int(N), int(D), int(kmax)
+        self.ctx = dpmm_chain(batch.ctx, b)
+        self._batch = batch
+
+    def close(self):
+        self.ctx = None
+
+
+class BatchSampler:
+    """Independent chains on datasets of uneven size (same D), stepped together:
+    one launch per kernel over all chains, one CUDA graph per step."""
+
+    def __init__(self, datasets, D, alpha=1.0, beta=0.5, *, kmax=256, seed=42, chain_id=0,
+                 engine=ENGINE_AUTO, split_q=True, stream=None):
+        """datasets: list of (indptr, indices, data, N); alpha / beta scalars or lists."""
+        B = len(datasets)
+        self.B, self.D, self.kmax = B, int(D), int(kmax)
+        self.Ns = [int(d[3]) for d in datasets]
+        al = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (B,))
+        be = np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,))
+        opts = dpmm_default_opts(kmax=kmax, seed=seed, chain_id=chain_id, engine=engine,
+                                 split_q=int(bool(split_q)))
+        self.ctx = dpmm_init_batch([d[:3] for d in datasets], self.Ns, D, al, be, opts, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            dpmm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def chain(self, b):
+        return _ChainView(self, b, self.Ns[b], self.D, self.kmax)
+
+    def step(self, n=1):
+        dpmm_step(self.ctx, n)
+
+    def sweep(self, n=1):
+        dpmm_sweep(self.ctx, n)
+
+    def split_merge(self, mode=0):
+        return dpmm_split_merge(self.ctx, mode)
 
     def sync(self):
         dpmm_sync(self.ctx)

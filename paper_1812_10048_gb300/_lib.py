@@ -47,6 +47,8 @@ SIGNATURES = {
     "dpmm_labels": (ctypes.c_int, [_P, _P, _P]),
     "dpmm_sync": (ctypes.c_int, [_P]),
     "dpmm_plans_applied": (ctypes.c_int, [_P, _P]),
+    "dpmm_init_batch": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P]),
+    "dpmm_chain": (ctypes.c_int, [_P, _I32, _P]),
     "dpmm_logml_grad": (ctypes.c_int, [_P, _P, _I32, ctypes.c_double, _P, _P, _P, _P]),
     "dpmm_profile": (ctypes.c_int, [_P, _I32]),
     "dpmm_phase_times": (ctypes.c_int, [_P, _P, _I32]),

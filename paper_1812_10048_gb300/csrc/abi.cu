@@ -17,6 +17,8 @@ using namespace dpmm;
 
 struct dpmm_ctx {
     Ctx c;
+    std::vector<dpmm_ctx*> members;   // a batch: its chains (owned)
+    bool member = false;              // a chain of a batch (freed with it)
 };
 struct dpmm_logml {
     LmlPlan p;
@@ -196,7 +198,17 @@ int mark(Ctx& c, int i) {
 // (+ the dense-tile B operand), [1] label kernel, [2] statistics (+ the CSR
 // fallback), [3] compaction, [4] move.
 int enqueue_labelling(Ctx& c) {
-    if (c.tile_enabled) {
+    if (c.tile_any && !c.tile_enabled) {
+        // a batch mixing chains with and without the blocked copy
+        CK(launch_build_b(c, false));
+        MARK(1);
+        CK(launch_tile_label(c, nullptr));
+        MARK(2);
+        CK(launch_assign(c));
+        CK(launch_tile_stats(c));
+        CK(launch_sweep_stats(c));
+        CK(launch_csr_commit(c));
+    } else if (c.tile_enabled) {
         // dense-tile labels (1 <= K <= 40), else CSR labels; statistics of
         // either from the blocked copy
         CK(launch_build_b(c, false));
@@ -258,6 +270,13 @@ int recount_all(Ctx& c) {
 #define CHECK_CTX(ctx)                                                  \
     do {                                                                \
         if (!(ctx)) return fail(DPMM_EINVAL, "null context");           \
+    } while (0)
+// calls that read or write one chain's state
+#define CHECK_CHAIN(ctx)                                                              \
+    do {                                                                              \
+        if (!(ctx)) return fail(DPMM_EINVAL, "null context");                         \
+        if (!(ctx)->members.empty())                                                  \
+            return fail(DPMM_EINVAL, "a batch context: select a chain with dpmm_chain"); \
     } while (0)
 
 }  // namespace
@@ -483,10 +502,111 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
 }
 
 void dpmm_free(dpmm_ctx* ctx) {
-    if (!ctx) return;
+    if (!ctx || ctx->member) return;   // a batch's chain goes with the batch
     cudaStreamSynchronize(ctx->c.stream);
+    for (dpmm_ctx* m : ctx->members) {
+        free_ctx(m->c);
+        delete m;
+    }
     free_ctx(ctx->c);
     delete ctx;
+}
+
+int dpmm_init_batch(dpmm_ctx** out, int32_t B, const int32_t* const* indptr,
+                    const int32_t* const* indices, const int32_t* const* data, const int64_t* N,
+                    int32_t D, const double* alpha, const double* beta, const dpmm_opts* opts,
+                    void* stream) {
+    if (!out) return fail(DPMM_EINVAL, "out is null");
+    *out = nullptr;
+    if (B < 1) return fail(DPMM_EINVAL, "B = %d < 1", B);
+    if (!indptr || !indices || !data || !N || !alpha || !beta)
+        return fail(DPMM_EINVAL, "null array argument");
+    dpmm_opts o;
+    dpmm_default_opts(&o);
+    if (opts) o = *opts;
+    if ((int64_t)o.chain_id + B > (1 << 24))
+        return fail(DPMM_EINVAL, "chain ids %d .. %d exceed 2^24 - 1", o.chain_id,
+                    o.chain_id + B - 1);
+    dpmm_ctx* h = new (std::nothrow) dpmm_ctx();
+    if (!h) return fail(DPMM_ENOMEM, "host allocation failed");
+    Ctx& c = h->c;
+    auto bail = [&](int rc) {
+        if (c.stream) cudaStreamSynchronize(c.stream);
+        for (dpmm_ctx* m : h->members) {
+            free_ctx(m->c);
+            delete m;
+        }
+        h->members.clear();
+        free_ctx(c);
+        delete h;
+        return rc;
+    };
+    if (stream) {
+        c.stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+        if (e) return bail(fail(DPMM_ECUDA, "stream: %s", cudaGetErrorString(e)));
+        c.own_stream = true;
+    }
+    for (int32_t b = 0; b < B; ++b) {
+        dpmm_opts ob = o;
+        ob.chain_id = o.chain_id + b;
+        dpmm_ctx* m = nullptr;
+        int rc = dpmm_init(&m, indptr[b], indices[b], data[b], N[b], D, alpha[b], beta[b], &ob,
+                           (void*)c.stream);
+        if (rc) return bail(rc);
+        m->member = true;
+        h->members.push_back(m);
+    }
+    const Ctx& m0 = h->members[0]->c;
+    c.device = m0.device;
+    c.num_sms = m0.num_sms;
+    c.smem_optin = m0.smem_optin;
+    c.D = D;
+    c.kmax = m0.kmax;
+    c.opts = o;
+    c.assign_blocks = m0.assign_blocks;
+    c.assign_smem = m0.assign_smem;
+    c.stats_blocks = m0.stats_blocks;
+    c.stats_smem = m0.stats_smem;
+    c.apply_blocks = m0.apply_blocks;
+    c.apply_smem = m0.apply_smem;
+    c.tile_C = m0.tile_C;
+    c.tile_enabled = true;
+    c.tile_any = false;
+    std::vector<ChainArgs> tab;
+    for (dpmm_ctx* m : h->members) {
+        c.tile_enabled = c.tile_enabled && m->c.tile_enabled;
+        c.tile_any = c.tile_any || m->c.tile_enabled;
+        if (m->c.tile_enabled) c.tile_C = m->c.tile_C;
+        c.max_Lslot = std::max(c.max_Lslot, m->c.tile_Lslot);
+        tab.push_back(*m->c.h_chain0);
+    }
+    cudaError_t e;
+    if ((e = dalloc(&c.gbar, 1)) || (e = dalloc(&c.d_chains, (size_t)B)) ||
+        (e = cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.stream)) ||
+        (e = cudaMemcpyAsync(c.d_chains, tab.data(), sizeof(ChainArgs) * B,
+                             cudaMemcpyHostToDevice, c.stream)) ||
+        (e = cudaStreamSynchronize(c.stream)))
+        return bail(fail(e == cudaErrorMemoryAllocation ? DPMM_ENOMEM : DPMM_ECUDA,
+                         "batch table: %s", cudaGetErrorString(e)));
+    c.nchains = B;
+    *out = h;
+    return DPMM_OK;
+}
+
+int dpmm_chain(dpmm_ctx* batch, int32_t b, dpmm_ctx** chain) {
+    CHECK_CTX(batch);
+    if (!chain) return fail(DPMM_EINVAL, "chain is null");
+    if (batch->members.empty()) {
+        if (b != 0) return fail(DPMM_EINVAL, "chain %d of a single-chain context", b);
+        *chain = batch;
+        return DPMM_OK;
+    }
+    if (b < 0 || b >= (int32_t)batch->members.size())
+        return fail(DPMM_EINVAL, "chain %d outside [0, %d)", b, (int)batch->members.size());
+    *chain = batch->members[b];
+    return DPMM_OK;
 }
 
 int dpmm_sweep(dpmm_ctx* ctx, int32_t n) {
@@ -505,8 +625,15 @@ int dpmm_split_merge(dpmm_ctx* ctx, int32_t mode, int32_t* n_accepted) {
     int rc = enqueue_moves(ctx->c, mode);
     if (rc) return rc;
     if (n_accepted) {
-        if ((rc = sync_scalars(ctx->c))) return rc;
-        *n_accepted = ctx->c.sc_host->n_accepted;
+        *n_accepted = 0;
+        if (ctx->members.empty()) {
+            if ((rc = sync_scalars(ctx->c))) return rc;
+            *n_accepted = ctx->c.sc_host->n_accepted;
+        }
+        for (dpmm_ctx* m : ctx->members) {
+            if ((rc = sync_scalars(m->c))) return rc;
+            *n_accepted += m->c.sc_host->n_accepted;
+        }
     }
     return DPMM_OK;
 }
@@ -540,7 +667,7 @@ int dpmm_step(dpmm_ctx* ctx, int32_t n) {
 }
 
 int dpmm_labels(dpmm_ctx* ctx, int32_t* out, int32_t* K_out) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     int rc;
     if (out) {
@@ -578,9 +705,16 @@ int dpmm_phase_times(dpmm_ctx* ctx, float* ms, int32_t n) {
 int dpmm_plans_applied(dpmm_ctx* ctx, int64_t* n) {
     CHECK_CTX(ctx);
     if (!n) return fail(DPMM_EINVAL, "n is NULL");
-    int rc = sync_scalars(ctx->c);
-    if (rc) return rc;
-    *n = (int64_t)ctx->c.sc_host->n_apply;
+    int rc;
+    *n = 0;
+    if (ctx->members.empty()) {
+        if ((rc = sync_scalars(ctx->c))) return rc;
+        *n = (int64_t)ctx->c.sc_host->n_apply;
+    }
+    for (dpmm_ctx* m : ctx->members) {
+        if ((rc = sync_scalars(m->c))) return rc;
+        *n += (int64_t)m->c.sc_host->n_apply;
+    }
     return DPMM_OK;
 }
 
@@ -594,7 +728,7 @@ void* dpmm_stream(dpmm_ctx* ctx) { return ctx ? (void*)ctx->c.stream : nullptr; 
 
 int dpmm_get_state(dpmm_ctx* ctx, int32_t* labels, uint8_t* sub, int32_t* K, int64_t* t,
                    int64_t* m) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     std::vector<uint32_t> st;
     if (labels || sub) {
@@ -616,7 +750,7 @@ int dpmm_get_state(dpmm_ctx* ctx, int32_t* labels, uint8_t* sub, int32_t* K, int
 
 int dpmm_set_state(dpmm_ctx* ctx, const int32_t* labels, const uint8_t* sub, int32_t K,
                    int64_t t, int64_t m, const double* sumlogq) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     if (K < 1 || K > c.kmax) return fail(DPMM_EINVAL, "K = %d outside [1, %d]", K, c.kmax);
     if (!labels || !sub) return fail(DPMM_EINVAL, "labels/sub are null");
@@ -660,7 +794,7 @@ int dpmm_set_state(dpmm_ctx* ctx, const int32_t* labels, const uint8_t* sub, int
 }
 
 int dpmm_get_stats(dpmm_ctx* ctx, uint32_t* nsub, uint32_t* Ssub, double* sumlogq) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     int rc = sync_scalars(c);
     if (rc) return rc;
@@ -672,18 +806,18 @@ int dpmm_get_stats(dpmm_ctx* ctx, uint32_t* nsub, uint32_t* Ssub, double* sumlog
 }
 
 int dpmm_draw_params(dpmm_ctx* ctx) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     CK(launch_draw_params(ctx->c));
     return DPMM_OK;
 }
 
 int dpmm_assign(dpmm_ctx* ctx) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     return enqueue_assign_half(ctx->c);
 }
 
 int dpmm_get_params(dpmm_ctx* ctx, float* logpi, float* logtheta) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     int rc = sync_scalars(c);
     if (rc) return rc;
@@ -706,7 +840,7 @@ int dpmm_get_params(dpmm_ctx* ctx, float* logpi, float* logtheta) {
 }
 
 int dpmm_set_params(dpmm_ctx* ctx, const float* logpi, const float* logtheta) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     if (!logpi || !logtheta) return fail(DPMM_EINVAL, "logpi/logtheta are null");
     int rc = sync_scalars(c);
@@ -729,7 +863,7 @@ int dpmm_set_params(dpmm_ctx* ctx, const float* logpi, const float* logtheta) {
 }
 
 int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     if (n <= 0 || !cells || !out) return fail(DPMM_EINVAL, "bad cells/out");
     int rc = sync_scalars(c);
@@ -755,7 +889,7 @@ int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out
 }
 
 int dpmm_debug_tile_scores(dpmm_ctx* ctx, float* out) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     if (!out) return fail(DPMM_EINVAL, "out is null");
     if (!c.tile_enabled) return fail(DPMM_ESTATE, "the dense-tile engine is not enabled");
@@ -777,7 +911,7 @@ int dpmm_debug_tile_scores(dpmm_ctx* ctx, float* out) {
 
 int dpmm_debug_moves(dpmm_ctx* ctx, int32_t* chain, double* log_h, int32_t* pair_ab,
                      int32_t* n_entries) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     int rc = sync_scalars(c);
     if (rc) return rc;
@@ -917,7 +1051,7 @@ int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
 int dpmm_logml_grad(dpmm_ctx* ctx, const int32_t* labels, int32_t K_labels, double log_alpha,
                     const float* log_beta, double* logml, double* grad_log_alpha,
                     float* grad_log_beta) {
-    CHECK_CTX(ctx);
+    CHECK_CHAIN(ctx);
     Ctx& c = ctx->c;
     if (!log_beta) return fail(DPMM_EINVAL, "log_beta is null");
     int rc = sync_scalars(c);

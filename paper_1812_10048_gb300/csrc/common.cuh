@@ -162,8 +162,7 @@ struct Ctx {
     struct ChainArgs* d_chains = nullptr;
     int32_t nchains = 0;
     struct ChainArgs* h_chain0 = nullptr;   // host copy of the single chain (nchains == 1)
-    std::vector<Ctx*> members;       // owned by a batch context
-    bool is_member = false;          // a chain of a batch (its stream is the batch's)
+    bool tile_any = false;           // some chain of the table has the blocked copy
     int32_t max_Lslot = 0;           // longest segment slot over the chains
 
     // plan + application kernel (cooperative, one block per SM)

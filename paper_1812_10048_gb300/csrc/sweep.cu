@@ -640,8 +640,9 @@ k_stats(const __grid_constant__ Tab tab, int64_t priv_cap, int sweep) {
         const DevScalars* sc = ch.sc;
         if (sweep) {
             // a sweep's statistics into the accumulators, unless the CSR label
-            // kernel added them (or the dense-tile configuration counts them)
-            if (sc->stats_fused || sc->tile_used) continue;
+            // kernel added them (a chain with the blocked copy is counted by
+            // the tile statistics kernel)
+            if (sc->stats_fused || ch.tile_enabled) continue;
             stats_cells(ch.csr, ch.state, nullptr, ch.acc_nsub, ch.acc_Ssub, ch.N, ch.D, sc->K,
                         spriv, priv_cap);
         } else {
@@ -657,13 +658,13 @@ k_stats(const __grid_constant__ Tab tab, int64_t priv_cap, int sweep) {
 // Commit of a CSR-labelled sweep's statistics.
 // ---------------------------------------------------------------------------
 // A CSR-labelled sweep's S-bar rows [0, 2K) move from the accumulator into
-// the main statistics (the accumulator is cleared); chains labelled by the
-// dense-tile engine are skipped (their counts went to the main rows directly).
+// the main statistics (the accumulator is cleared); chains with the blocked
+// copy are skipped (the tile statistics kernel adds to their main rows).
 template <class Tab>
 __global__ void k_csr_commit(const __grid_constant__ Tab tab) {
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
-        if (ch.sc->tile_used) continue;
+        if (ch.tile_enabled) continue;
         const int64_t total = (int64_t)2 * ch.sc->K * ch.D;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
              i += (int64_t)gridDim.x * blockDim.x) {
