@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="main", choices=["main", "batched", "large"],
+                    help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
+                         "as one batch; large: 1.3M x 2k")
+    ap.add_argument("--workers", type=int, default=0,
+                    help="processes drawing the batched / large data (0: all cores)")
     return ap.parse_args()
 
 
@@ -322,8 +327,156 @@ def run_ours(args, rank, world, local):
     return result
 
 
+
+# ---------------------------------------------------------------------------
+# Other workloads (their own JSON line; the driver's default run is "main")
+# ---------------------------------------------------------------------------
+def time_steps(step_fn, stream, steps, warmup, torch, flush=None):
+    """Per-step device times of step_fn() on `stream` after `warmup` untimed steps."""
+    for _ in range(warmup):
+        step_fn()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            if flush is not None:
+                flush.zero_()
+            starts[i].record(stream)
+        step_fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
+
+
+def run_batched(args):
+    """64 datasets (N ~ U[1k, 50k], D = 1,000, K_true ~ U[3, 20]): the BF16 batch and
+    the FP32 batch (one launch per kernel over all chains, one graph per step) and the
+    plain FP32 sampler run one chain at a time; aggregate chain-sweeps/s."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    from oracle.ari import adjusted_rand_index
+    t0 = time.time()
+    dss = synth.batched(workers=args.workers or os.cpu_count())
+    gen_s = time.time() - t0
+    B, D = len(dss), 1000
+    data = [(d.indptr, d.indices, d.data, d.N) for d in dss]
+    steps, warmup = args.steps, max(3, args.warmup)
+    forms = {}
+    clocks = ClockSampler(0)
+    labels = {}
+    for name, eng in [("bf16_batched", P.ENGINE_AUTO), ("fp32_batched", P.ENGINE_CSR_FP32)]:
+        bs = P.BatchSampler(data, D, 1.0, 0.5, kmax=64, seed=42, engine=eng)
+        st = torch.cuda.ExternalStream(bs.stream)
+        if name == "bf16_batched":
+            clocks.start()
+        ms = time_steps(lambda: bs.step(1), st, steps, warmup, torch)
+        if name == "bf16_batched":
+            clk = clocks.stop()
+        labels[name] = [bs.chain(b).labels()[0] for b in range(B)]
+        forms[name] = {"chain_sweeps_per_s": round(B * steps / (ms.sum() / 1e3), 1),
+                       "ms_per_batched_step": round(float(ms.mean()), 4),
+                       "K": [int(bs.chain(b).labels_K()) for b in range(B)],
+                       "mean_ari_vs_truth": round(float(np.mean([
+                           adjusted_rand_index(labels[name][b], dss[b].labels)
+                           for b in range(B)])), 4)}
+        bs.close()
+    # the plain FP32 sampler, one chain at a time (each its own graph)
+    singles = [P.Sampler(d[0], d[1], d[2], d[3], D, 1.0, 0.5, kmax=64, seed=42, chain_id=b,
+                         engine=P.ENGINE_CSR_FP32) for b, d in enumerate(data)]
+    st0 = torch.cuda.ExternalStream(singles[0].stream)
+
+    def round_robin():
+        for s in singles:
+            s.step(1)
+    # the singles run on their own streams: synchronise around each timed round
+    for _ in range(warmup):
+        round_robin()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(steps):
+        round_robin()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t1
+    forms["fp32_plain_one_chain_at_a_time"] = {
+        "chain_sweeps_per_s": round(B * steps / plain_s, 1),
+        "timing": "wall clock around all chains' steps (each chain its own stream and graph)"}
+    for s in singles:
+        s.close()
+    del st0
+    ari_bf = float(np.mean([adjusted_rand_index(labels["bf16_batched"][b],
+                                                labels["fp32_batched"][b]) for b in range(B)]))
+    line = {
+        "metric": "aggregate chain-sweeps/s, 64 datasets stepped as one batch (BF16 form)",
+        "value": forms["bf16_batched"]["chain_sweeps_per_s"], "unit": "chain-sweeps/s",
+        "n_gpus": 1, "steps": steps, "warmup": warmup, "higher_is_better": True,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "64 datasets, N ~ U[1,000, 50,000], D = 1,000, "
+                               "K_true ~ U[3, 20], Dir(0.1) profiles, LogNormal(log 1500, 0.5)",
+                   "cells": int(sum(d.N for d in dss)), "nnz": int(sum(d.nnz for d in dss)),
+                   "alpha": 1.0, "beta": 0.5, "kmax": 64, "generation_s": round(gen_s, 1),
+                   "l2": "inputs (> 1 GB) larger than L2"},
+        "forms": forms, "mean_ari_bf16_vs_fp32_labels": round(ari_bf, 4), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_large(args):
+    """1.3M cells x 2,000 genes, 40 Zipf clusters, 2% deep cells: BF16 vs FP32."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    from oracle.ari import adjusted_rand_index
+    t0 = time.time()
+    ds = synth.large(workers=args.workers or os.cpu_count())
+    gen_s = time.time() - t0
+    steps, warmup = args.steps, max(3, args.warmup)
+    forms = {}
+    clocks = ClockSampler(0)
+    clk = None
+    for name, eng in [("bf16", P.ENGINE_AUTO), ("fp32", P.ENGINE_CSR_FP32)]:
+        s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                      engine=eng)
+        st = torch.cuda.ExternalStream(s.stream)
+        if name == "bf16":
+            clocks.start()
+        ms = time_steps(lambda: s.step(1), st, steps, warmup, torch)
+        if name == "bf16":
+            clk = clocks.stop()
+        lab, K = s.labels()
+        forms[name] = {"sweeps_per_s": round(steps / (ms.sum() / 1e3), 2),
+                       "ms_per_step": round(float(ms.mean()), 4), "K_final": int(K),
+                       "ari_vs_truth": round(adjusted_rand_index(lab, ds.labels), 4)}
+        s.close()
+    line = {
+        "metric": "Gibbs sweeps/sec at 1.3M cells x 2k genes (BF16 hi/lo form)",
+        "value": forms["bf16"]["sweeps_per_s"], "unit": "sweeps/s", "n_gpus": 1,
+        "steps": steps, "warmup": warmup, "higher_is_better": True, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "1.3M cells x 2,000 genes, 40 Zipf(1.0) clusters, Dir(0.05), "
+                               "LogNormal(log 1000, 0.6), 2% deep cells LogUniform[5k, 60k]",
+                   "N": ds.N, "D": ds.D, "nnz": ds.nnz, "max_count": int(ds.data.max()),
+                   "counts_over_255": int((ds.data > 255).sum()), "alpha": 1.0, "beta": 0.1,
+                   "kmax": 256, "generation_s": round(gen_s, 1),
+                   "l2": "inputs (> 1 GB) larger than L2"},
+        "forms": forms, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.config == "batched":
+        return run_batched(args)
+    if args.config == "large":
+        return run_large(args)
     rank, world, local = dist_env()
     if world > 1:
         import torch
