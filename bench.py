@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="main", choices=["main", "batched", "large"],
+    ap.add_argument("--config", default="main", choices=["main", "batched", "large", "grad"],
                     help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
                          "as one batch; large: 1.3M x 2k")
     ap.add_argument("--workers", type=int, default=0,
@@ -471,8 +471,116 @@ def run_large(args):
     return 0
 
 
+def run_grad(args):
+    """Collapsed log-ML + gradient at 100k cells x 2k genes, K = 25 (the generating
+    labels): device time per forward + backward, the autograd call as a user makes
+    it, and the FP32 gradient's error against the FP64 analytic gradient and FP64
+    central finite differences."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    from oracle.logml import cluster_stats, log_ml, log_ml_grad
+    ds = synth.grad_workload()
+    K = int(ds.labels.max()) + 1
+    rng = np.random.default_rng(1005)
+    lb = (np.log(0.1) + 0.1 * rng.standard_normal(ds.D)).astype(np.float32)
+    la = 0.0
+    # the handle runs on this torch stream, so events recorded there bracket its work
+    tstream = torch.cuda.Stream()
+    h = P.LogML(ds.indptr, ds.indices, ds.data, ds.N, ds.D, ds.labels, K,
+                stream=tstream.cuda_stream)
+    lbt = torch.from_numpy(lb).cuda()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    gb = torch.empty(ds.D, dtype=torch.float32, device="cuda")
+    lib = P._lib.lib()
+    ptr = P._lib.ptr
+    n_it = max(50, args.steps)
+
+    def fwd_bwd():
+        P.check(lib.dpmm_logml_forward(h.h, float(la), ptr(lbt), ptr(out)))
+        P.check(lib.dpmm_logml_backward(h.h, float(la), ptr(lbt),
+                                        P.ctypes.c_void_p(out.data_ptr() + 8), ptr(gb)))
+    for _ in range(10):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(tstream)
+    for _ in range(n_it):
+        fwd_bwd()
+    e1.record(tstream)
+    torch.cuda.synchronize()
+    dev_us = e0.elapsed_time(e1) * 1e3 / n_it
+    # as a user calls it: autograd forward + backward (scalar to the host)
+    lat = torch.tensor(la, dtype=torch.float64, requires_grad=True)
+    lbr = lbt.clone().requires_grad_(True)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(tstream):
+        for _ in range(n_it):
+            v = h(lat, lbr)
+            v.backward()
+    torch.cuda.synchronize()
+    e2e_us = (time.perf_counter() - t0) * 1e6 / n_it
+    # accuracy against FP64
+    n, S = cluster_stats(ds.indptr, ds.indices, ds.data, ds.N, ds.D, ds.labels, K)
+    lb64 = lb.astype(np.float64)
+    ref = log_ml(n, S, la, lb64)
+    ga_ref, gb_ref = log_ml_grad(n, S, la, lb64)
+    val = float(out[0].item())
+    ga = float(out[1].item())
+    g = gb.cpu().numpy().astype(np.float64)
+    step = 1e-6
+    fd_idx = np.linspace(0, ds.D - 1, 16).astype(int)
+    fd = []
+    for u in fd_idx:
+        e = np.zeros(ds.D)
+        e[u] = step
+        fd.append((log_ml(n, S, la, lb64 + e) - log_ml(n, S, la, lb64 - e)) / (2 * step))
+    fd = np.array(fd)
+    fd_a = (log_ml(n, S, la + step, lb64) - log_ml(n, S, la - step, lb64)) / (2 * step)
+    # h = 1e-6 sits on the rounding floor of an FP64 function of size ~1e8
+    # (eps |f| / h ~ 1e-2); h = 1e-3 balances rounding and truncation
+    step2 = 1e-3
+    fd2 = []
+    for u in fd_idx:
+        e = np.zeros(ds.D)
+        e[u] = step2
+        fd2.append((log_ml(n, S, la, lb64 + e) - log_ml(n, S, la, lb64 - e)) / (2 * step2))
+    fd2 = np.array(fd2)
+    line = {
+        "metric": "collapsed log-ML forward + backward at 100k cells x 2k genes, K = 25",
+        "value": round(dev_us, 2), "unit": "us per forward+backward (device)",
+        "higher_is_better": False, "n_gpus": 1, "steps": n_it, "dtype": "f64 forward / f32 backward",
+        "data": "synthetic",
+        "config": {"workload": "100,000 cells x 2,000 genes, 25 Zipf(1.0) clusters, Dir(0.05), "
+                               "LogNormal(log 1000, 0.6); labels = the generating ones; "
+                               "log beta_u ~ log 0.1 + N(0, 0.1^2), log alpha = 0",
+                   "N": ds.N, "D": ds.D, "nnz": ds.nnz, "K": K},
+        "autograd_call_us": round(e2e_us, 2),
+        "errors": {
+            "logml_rel_vs_fp64": abs(val - ref) / abs(ref),
+            "grad_log_alpha_rel_vs_fp64": abs(ga - ga_ref) / max(1.0, abs(ga_ref)),
+            "grad_log_beta_max_rel_vs_fp64": float(np.max(np.abs(g - gb_ref)) /
+                                                   np.max(np.abs(gb_ref))),
+            "fp64_fd_vs_analytic_max_rel": float(np.max(np.abs(fd - gb_ref[fd_idx])) /
+                                                 np.max(np.abs(gb_ref[fd_idx]))),
+            "fp64_fd_vs_analytic_alpha_rel": abs(fd_a - ga_ref) / max(1.0, abs(ga_ref)),
+            "fp64_fd_h1e-3_vs_analytic_max_rel": float(np.max(np.abs(fd2 - gb_ref[fd_idx])) /
+                                                       np.max(np.abs(gb_ref[fd_idx]))),
+            "fp32_grad_vs_fp64_fd_h1e-3_max_rel": float(np.max(np.abs(g[fd_idx] - fd2)) /
+                                                        np.max(np.abs(fd2))),
+            "fd_step": step, "fd_genes": len(fd_idx)},
+    }
+    h.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.config == "grad":
+        return run_grad(args)
     if args.config == "batched":
         return run_batched(args)
     if args.config == "large":

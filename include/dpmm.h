@@ -256,15 +256,17 @@ void dpmm_logml_free(dpmm_logml* h);
  * LML = K log alpha + lgamma(alpha) - lgamma(alpha+N) + sum_k lgamma(n_k)
  *     + sum_k [lgamma(B) - lgamma(B+T_k) + sum_u (lgamma(beta_u+S_ku) - lgamma(beta_u))]
  * with alpha = exp(log_alpha), beta = exp(log_beta) (float[D]), B = sum beta.
- * Summed in FP64 on the device.  *logml is a host double.  Synchronises.
+ * Summed in FP64 on the device.  logml is a host double (the call then
+ * synchronises) or a device double (asynchronous on the handle's stream).
  */
 int dpmm_logml_forward(dpmm_logml* h, double log_alpha, const float* log_beta, double* logml);
 
 /*
  * Gradient of LML: *grad_log_alpha = K + alpha (psi(alpha) - psi(alpha+N)),
  * grad_log_beta[u] = beta_u sum_k [psi(B) - psi(B+T_k) + psi(beta_u+S_ku) - psi(beta_u)]
- * (float[D], FP32 digamma sums).  grad_log_beta may be a device pointer, in
- * which case the call is asynchronous apart from *grad_log_alpha (host).
+ * (float[D], FP32 digamma sums).  Each output may be host or device memory;
+ * the call is asynchronous on the handle's stream when every output given
+ * is device memory, else it synchronises.
  */
 int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
                         double* grad_log_alpha, float* grad_log_beta);

@@ -1023,7 +1023,7 @@ int dpmm_logml_forward(dpmm_logml* h, double log_alpha, const float* log_beta, d
     if (rc) return rc;
     CK(lml_forward(p, log_alpha, lb, p.out));
     CK(cudaMemcpyAsync(logml, p.out, sizeof(double), cudaMemcpyDefault, p.stream));
-    CK(cudaStreamSynchronize(p.stream));
+    if (!is_device_ptr(logml)) CK(cudaStreamSynchronize(p.stream));
     return DPMM_OK;
 }
 
@@ -1039,12 +1039,10 @@ int dpmm_logml_backward(dpmm_logml* h, double log_alpha, const float* log_beta,
     if (!dev_out)
         CK(cudaMemcpyAsync(grad_log_beta, p.grad, sizeof(float) * p.D, cudaMemcpyDeviceToHost,
                            p.stream));
-    if (grad_log_alpha) {
+    const bool dev_alpha = grad_log_alpha && is_device_ptr(grad_log_alpha);
+    if (grad_log_alpha)
         CK(cudaMemcpyAsync(grad_log_alpha, p.out + 1, sizeof(double), cudaMemcpyDefault, p.stream));
-        CK(cudaStreamSynchronize(p.stream));
-    } else if (!dev_out) {
-        CK(cudaStreamSynchronize(p.stream));
-    }
+    if ((grad_log_alpha && !dev_alpha) || !dev_out) CK(cudaStreamSynchronize(p.stream));
     return DPMM_OK;
 }
 

@@ -3,7 +3,7 @@
 // eq. 12 against eq. 28 with lambda generalised to beta_u, pi out of eq. 10).
 //
 //   k_lml_stats     n_k, S_ku of the labelled cells (integer, exact)
-//   k_lml_forward   FP64: per cluster lgamma(n_k) + lgamma(B) - lgamma(B + T_k)
+//   k_lml_forward   FP64, blocks (cluster, 256 genes): lgamma(n_k) + lgamma(B) - lgamma(B + T_k)
 //                   + sum_{u: S_ku > 0} [lgamma(beta_u + S_ku) - lgamma(beta_u)];
 //                   one extra block adds K log alpha + lgamma(alpha) - lgamma(alpha + N)
 //   k_lml_common    B = sum beta_u; c = sum_k [psi(B) - psi(B + T_k)];
@@ -59,13 +59,16 @@ __global__ void __launch_bounds__(kLmlThreads)
 k_lml_forward(const uint32_t* __restrict__ n, const uint32_t* __restrict__ S,
               const unsigned long long* __restrict__ T, const float* __restrict__ log_beta,
               int64_t N, int32_t D, int32_t K, double log_alpha, double* __restrict__ out) {
+    // block (k, g): the gene terms of cluster k over genes [256 g, 256 g + 256);
+    // blocks (k, 0) also add cluster k's count and total terms, block (K, 0)
+    // the partition terms.  GB300's FP64 rate makes the lgamma calls the cost,
+    // so they are spread over K x D / 256 blocks.
     __shared__ double red[32];
-    double B = 0.0;
-    for (int u = threadIdx.x; u < D; u += blockDim.x) B += exp((double)log_beta[u]);
-    B = block_sum_lml(B, red);
-    if ((int)blockIdx.x == K) {
+    const int k = blockIdx.x, g = blockIdx.y;
+    if (k == K) {
+        if (g != 0) return;
         double keff = 0.0;
-        for (int k = threadIdx.x; k < K; k += blockDim.x) keff += n[k] ? 1.0 : 0.0;
+        for (int j = threadIdx.x; j < K; j += blockDim.x) keff += n[j] ? 1.0 : 0.0;
         keff = block_sum_lml(keff, red);
         if (threadIdx.x == 0) {
             const double alpha = exp(log_alpha);
@@ -73,20 +76,25 @@ k_lml_forward(const uint32_t* __restrict__ n, const uint32_t* __restrict__ S,
         }
         return;
     }
-    const int k = blockIdx.x;
     if (n[k] == 0) return;
     const uint32_t* Sk = S + (size_t)k * D;
     double acc = 0.0;
-    for (int u = threadIdx.x; u < D; u += blockDim.x) {
+    const int u = g * blockDim.x + threadIdx.x;
+    if (u < D) {
         const uint32_t s = Sk[u];
         if (s) {
             const double b = exp((double)log_beta[u]);
-            acc += lgamma(b + (double)s) - lgamma(b);
+            acc = lgamma(b + (double)s) - lgamma(b);
         }
     }
+    if (g == 0) {
+        double B = 0.0;
+        for (int v = threadIdx.x; v < D; v += blockDim.x) B += exp((double)log_beta[v]);
+        B = block_sum_lml(B, red);
+        if (threadIdx.x == 0) acc += lgamma((double)n[k]) + lgamma(B) - lgamma(B + (double)T[k]);
+    }
     acc = block_sum_lml(acc, red);
-    if (threadIdx.x == 0)
-        atomicAdd(out, acc + lgamma((double)n[k]) + lgamma(B) - lgamma(B + (double)T[k]));
+    if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 
 __global__ void __launch_bounds__(kLmlThreads)
@@ -215,8 +223,9 @@ cudaError_t lml_compute_stats(LmlPlan& p) {
 cudaError_t lml_forward(LmlPlan& p, double log_alpha, const float* log_beta, double* out_dev) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(out_dev, 0, sizeof(double), p.stream))) return e;
-    k_lml_forward<<<p.K + 1, kLmlThreads, 0, p.stream>>>(p.n, p.S, p.T, log_beta, p.N, p.D, p.K,
-                                                         log_alpha, out_dev);
+    const dim3 grid(p.K + 1, (p.D + kLmlThreads - 1) / kLmlThreads);
+    k_lml_forward<<<grid, kLmlThreads, 0, p.stream>>>(p.n, p.S, p.T, log_beta, p.N, p.D, p.K,
+                                                      log_alpha, out_dev);
     return cudaGetLastError();
 }
 
