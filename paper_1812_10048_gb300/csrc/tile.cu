@@ -219,36 +219,38 @@ __device__ __forceinline__ void chain_tiles(int64_t off, int T, int& first, int&
     cnt = first < T ? (T - 1 - first) / (int)G + 1 : 0;
 }
 
-// Warp roles of the pipelined engine (19 warps):
+// Warp roles of the pipelined engine (27 warps):
 //   warps 0-7   epilogue, two halves of four warps over the same 128 cells
 //               (warp w reads TMEM lanes 32 (w % 4) ..): each half takes every
 //               other 8-cluster column group of the Gumbel-max; half 1 also
 //               draws the eq. 8 noise, half 0 merges and finishes the cell
-//   warps 8-15  producers, two sets of four warps taking alternate chunks;
-//               warp q of a set densifies rows 32q .. 32q + 31 of its chunk
-//               (the entries of one quarter) from the staged segment, so the
-//               four warps never wait on one another
-//   warp 16     lane 0 issues the MMAs (two TMEM accumulators of 256 columns)
-//   warp 17     segment loader: bulk-copies each chunk's entries into a ring
+//   warps 8-23  producers, four sets of four warps taking chunks in turn
+//               (two sets when only two A stages fit); warp q of a set
+//               densifies rows 32q .. 32q + 31 of its chunk (the entries of
+//               one quarter) from the staged segment, so the four warps never
+//               wait on one another
+//   warp 24     lane 0 issues the MMAs (two TMEM accumulators of 256 columns)
+//   warp 25     segment loader: bulk-copies each chunk's entries into a ring
 //               of slots, reading the segment table a warp-batch ahead
-//   warp 18     lane 0 bulk-copies the B operand of each chunk into its ring
+//   warp 26     lane 0 bulk-copies the B operand of each chunk into its ring
 // Every role walks the same sequence: the chains in order, this CTA's tiles
 // of each chain, the chunks of each tile.
-// Hand-offs are mbarriers: ent_full / ent_free (segment slots), a_full (four
-// producer warps -> MMA) / stage_free (MMA commit -> producers), b_full /
-// b_free (B slots), acc_full (MMA -> epilogue) / acc_empty (epilogue -> MMA).
+// Hand-offs are mbarriers: ent_full / ent_free (segment slots), a_full (the
+// four producer warps and the B loader's bulk copy -> MMA: a stage holds a
+// chunk's A tiles and B operand), stage_free (MMA commit -> producers and B
+// loader), acc_full (MMA -> epilogue) / acc_empty (epilogue -> MMA).
 // Every wait is bounded; a timeout records DPMM_ETIMEOUT, every role leaves
 // its loop, and each role that issued asynchronous work waits (bounded) for
 // it before the block exits.
 constexpr int kMaxStages = 4;        // A stages (lo + hi), even
-constexpr int kMaxBSlots = 4;
 constexpr int kMaxESlots = 16;
 constexpr int kEpiWarps = 8;
+constexpr int kProdSets = 4;        // producer sets (4 warps each) on alternate chunks
 constexpr int kProdWarp0 = 8;
-constexpr int kMmaWarp = 16;
-constexpr int kELoadWarp = 17;
-constexpr int kBLoadWarp = 18;
-constexpr int kTileThreadsP = 19 * 32;
+constexpr int kMmaWarp = kProdWarp0 + 4 * kProdSets;
+constexpr int kELoadWarp = kMmaWarp + 1;
+constexpr int kBLoadWarp = kMmaWarp + 2;
+constexpr int kTileThreadsP = (kMmaWarp + 3) * 32;
 constexpr int kBarEpi = 1, kBarLabel = 2;
 constexpr int kSmallBytes = 8192;
 constexpr int kScatter = 12;         // entries per producer lane and batch
@@ -285,10 +287,18 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
     const int64_t b_slot = ((int64_t)ntot_max * 128 + 1023) & ~(int64_t)1023;
     const int64_t e_slot = (int64_t)lslot_max * 4;
     const int64_t avail = smem_bytes - (int64_t)(base - smem_raw) - kSmallBytes;
-    const int nS = (int64_t)kMaxStages * 32768 + 2 * b_slot + 2 * e_slot <= avail ? kMaxStages : 2;
-    const int nB = (int)min((int64_t)kMaxBSlots, (avail - nS * 32768 - 2 * e_slot) / b_slot);
-    const int nE = (int)min((int64_t)kMaxESlots,
-                            (avail - nS * 32768 - (int64_t)max(nB, 0) * b_slot) / e_slot);
+    // a stage holds a chunk's A tiles (lo, hi) and its B operand: one MMA
+    // commit per chunk frees both
+    const int nS = (int64_t)kMaxStages * (32768 + b_slot) + 2 * e_slot <= avail ? kMaxStages : 2;
+    const int nB = nS;
+    const int nE_fit = (int)min((int64_t)kMaxESlots,
+                                (avail - (int64_t)nS * (32768 + b_slot)) / e_slot);
+    // producer sets in use: each set must meet the same A stages (its hi
+    // halves) and the same segment slots, so nsets divides nS and nE.  Slot
+    // g % nE is then refilled for chunk g only after the same set consumed
+    // chunk g - nE, and a set's parity wait can never be two phases ahead.
+    const int nsets = (nS % kProdSets == 0 && nE_fit >= kProdSets) ? kProdSets : 2;
+    const int nE = (nE_fit / nsets) * nsets;
     if (nB < 2 || nE < 2) {
         if (tid == 0) atomicExch(&tab[0].sc->error, DPMM_ECAPACITY);
         return;
@@ -300,9 +310,7 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
     small = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(small) + 15) & ~(uintptr_t)15);
     uint64_t* a_full = reinterpret_cast<uint64_t*>(small);         // [kMaxStages]
     uint64_t* stage_free = a_full + kMaxStages;                     // [kMaxStages]
-    uint64_t* b_full = stage_free + kMaxStages;                     // [kMaxBSlots]
-    uint64_t* b_free = b_full + kMaxBSlots;                         // [kMaxBSlots]
-    uint64_t* ent_full = b_free + kMaxBSlots;                       // [kMaxESlots]
+    uint64_t* ent_full = stage_free + kMaxStages;                   // [kMaxESlots]
     uint64_t* ent_free = ent_full + kMaxESlots;                     // [kMaxESlots]
     uint64_t* acc_full = ent_free + kMaxESlots;                     // [2]
     uint64_t* acc_empty = acc_full + 2;                             // [2]
@@ -333,12 +341,8 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
         *err = 0;
         stop[0] = stop[1] = 0;
         for (int i = 0; i < kMaxStages; ++i) {
-            tc::mbar_init(&a_full[i], 4);
+            tc::mbar_init(&a_full[i], 5);   // four producer warps + the B copy
             tc::mbar_init(&stage_free[i], 1);
-        }
-        for (int i = 0; i < kMaxBSlots; ++i) {
-            tc::mbar_init(&b_full[i], 1);
-            tc::mbar_init(&b_free[i], 1);
         }
         for (int i = 0; i < kMaxESlots; ++i) {
             tc::mbar_init(&ent_full[i], 1);
@@ -365,7 +369,7 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
         const int set = (warp - kProdWarp0) >> 2, q = (warp - kProdWarp0) & 3;
         uint32_t hi_dirty = 0u;   // stages whose hi quarter this warp left non-zero
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        for (uint32_t g = (uint32_t)set; g < total; g += 2) {
+        for (uint32_t g = (uint32_t)set; set < nsets && g < total; g += (uint32_t)nsets) {
             const int st = (int)(g % (uint32_t)nS);
             const int es = (int)(g % (uint32_t)nE);
             bool ok = tc::mbar_wait(&ent_full[es], (g / (uint32_t)nE) & 1u, kWaitLimit);
@@ -402,7 +406,9 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
 #pragma unroll
                 for (int u = 0; u < kScatter; ++u) {
                     const uint32_t x = v[u] & 0xFFFFu;
-                    if (x) {
+                    // an entry's row lies in this warp's quarter (checked, so
+                    // that no entry can address outside the stage)
+                    if (x && (v[u] >> 22) - 32u * (uint32_t)q < 32u) {
                         const uint32_t off = tc::swz_offset(v[u] >> 22, (v[u] >> 16) & 63u);
                         *reinterpret_cast<uint16_t*>(A_lo + off) =
                             (uint16_t)(__float_as_uint((float)(x & 255u)) >> 16);
@@ -516,7 +522,8 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                 for (uint32_t j = 0; j < nchunk; ++j, ++g) {
                     const int bs = (int)(g % (uint32_t)nB);
                     if (g >= (uint32_t)nB &&
-                        !tc::mbar_wait(&b_free[bs], ((g / (uint32_t)nB) - 1u) & 1u, kWaitLimit)) {
+                        !tc::mbar_wait(&stage_free[bs], ((g / (uint32_t)nB) - 1u) & 1u,
+                                       kWaitLimit)) {
                         *err = DPMM_ETIMEOUT;
                         stop_b = true;
                         break;
@@ -526,14 +533,14 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                         break;
                     }
                     const uint32_t c = j % (uint32_t)ch.tile_C;
-                    tc::mbar_arrive_expect_tx(&b_full[bs], bytes);
+                    tc::mbar_arrive_expect_tx(&a_full[bs], bytes);
                     tc::bulk_g2s(B_base + bs * b_slot, ch.tile_B + (size_t)c * kBChunkBytes, bytes,
-                                 &b_full[bs]);
+                                 &a_full[bs]);
                 }
             }
             const uint32_t issued = g;
             for (uint32_t q = issued > (uint32_t)nB ? issued - (uint32_t)nB : 0u; q < issued; ++q)
-                tc::mbar_wait(&b_full[q % (uint32_t)nB], (q / (uint32_t)nB) & 1u, kWaitLimit);
+                tc::mbar_wait(&a_full[q % (uint32_t)nB], (q / (uint32_t)nB) & 1u, kWaitLimit);
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issue ----------------
@@ -564,8 +571,7 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                     const uint32_t acc = tmem + buf * 256u;
                     for (int c = 0; c < ch.tile_C; ++c) {
                         const int st = (int)(g % (uint32_t)nS), bs = (int)(g % (uint32_t)nB);
-                        if (!tc::mbar_wait(&a_full[st], (g / (uint32_t)nS) & 1u, kWaitLimit) ||
-                            !tc::mbar_wait(&b_full[bs], (g / (uint32_t)nB) & 1u, kWaitLimit)) {
+                        if (!tc::mbar_wait(&a_full[st], (g / (uint32_t)nS) & 1u, kWaitLimit)) {
                             *err = DPMM_ETIMEOUT;
                             stop_m = true;
                             break;
@@ -584,7 +590,6 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                                              tc::desc_sw128(bsm + 32 * k), idesc, 1u);
                         }
                         tc::mma_commit(&stage_free[st]);
-                        tc::mma_commit(&b_free[bs]);
                         ++g;
                     }
                     if (stop_m) break;
@@ -595,7 +600,6 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
             if (g > 0) {
                 const uint32_t l = g - 1;
                 tc::mbar_wait(&stage_free[l % (uint32_t)nS], (l / (uint32_t)nS) & 1u, kWaitLimit);
-                tc::mbar_wait(&b_free[l % (uint32_t)nB], (l / (uint32_t)nB) & 1u, kWaitLimit);
             }
         }
     } else {

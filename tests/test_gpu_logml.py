@@ -63,7 +63,10 @@ def test_autograd_function_matches_finite_differences(P):
         fm = model.forward(0.1, torch.from_numpy(lb - e).cuda())
         fd = (fp - fm) / (2 * h)
         assert abs(lbt.grad[u].item() - fd) <= 2e-3 * max(1.0, abs(fd))
-    fa = (model.forward(0.1 + 1e-6, lbt.detach()) - model.forward(0.1 - 1e-6, lbt.detach())) / 2e-6
+    # the FP64 forward adds (cluster, gene-block) partials in device order: a
+    # step of 1e-6 would sit on its rounding floor (|LML| ~ 1e5, eps ~ 1e-16);
+    # 1e-4 keeps the central difference's truncation error below 1e-8
+    fa = (model.forward(0.1 + 1e-4, lbt.detach()) - model.forward(0.1 - 1e-4, lbt.detach())) / 2e-4
     assert abs(la.grad.item() - fa) <= 1e-5 * max(1.0, abs(fa))
 
 
