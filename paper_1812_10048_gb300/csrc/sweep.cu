@@ -76,10 +76,12 @@ __global__ void k_select_engine(const __grid_constant__ Tab tab) {
 }
 
 // Rows 0 .. 3K-1 are theta rows (row 3k + p: cluster k for p = 0, its
-// sub-cluster p - 1 otherwise); row 3K is the pi row.  log G is written to the
-// output slot first, then normalised in place (log theta = log G - logsumexp).
+// sub-cluster p - 1 otherwise); row 3K is the pi row.  log G is kept in the
+// block's cache (D <= kDrawCache; else in the output slot), then normalised
+// into the output (log theta = log G - logsumexp).
+constexpr int kDrawCache = 8192;
 __device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, uint32_t t, int row,
-                                         float* red) {
+                                         float* red, float* lgc) {
     const int D = ch.D, kmax = ch.kmax;
     const float beta = (float)ch.beta, alpha = (float)ch.alpha;
     const Stream& st = ch.st;
@@ -89,27 +91,27 @@ __device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, uint32_t t,
         const uint32_t* S1 = S0 + D;
         float* Lc = ch.Lc;
         float* Ls = ch.Ls;
+        const bool cached = D <= kDrawCache;
+        auto slot = [&](int u) -> float* {
+            return p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
+        };
         float mx = -CUDART_INF_F;
         for (int u = threadIdx.x; u < D; u += blockDim.x) {
             const uint32_t S = p == 0 ? S0[u] + S1[u] : (p == 1 ? S0[u] : S1[u]);
             const float lg = log_gamma_draw(st, TAG_THETA, beta + (float)S,
                                             (uint32_t)row * (uint32_t)D + (uint32_t)u, t);
-            float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
-            *out = lg;
+            if (cached) lgc[u] = lg;
+            else *slot(u) = lg;
             mx = fmaxf(mx, lg);
         }
-        mx = block_reduce_max(mx, red);
+        mx = block_reduce_max(mx, red);   // (its barrier also publishes lgc)
         float s = 0.0f;
-        for (int u = threadIdx.x; u < D; u += blockDim.x) {
-            const float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
-            s += expf(*out - mx);
-        }
+        for (int u = threadIdx.x; u < D; u += blockDim.x)
+            s += expf((cached ? lgc[u] : *slot(u)) - mx);
         s = block_reduce_sum(s, red);
         const float lse = mx + logf(s);
-        for (int u = threadIdx.x; u < D; u += blockDim.x) {
-            float* out = p == 0 ? &Lc[(size_t)u * kmax + k] : &Ls[((size_t)u * kmax + k) * 2 + (p - 1)];
-            *out -= lse;
-        }
+        for (int u = threadIdx.x; u < D; u += blockDim.x)
+            *slot(u) = (cached ? lgc[u] : *slot(u)) - lse;
     } else {
         const uint32_t* nsub = ch.nsub;
         float* logpi = ch.logpi;
@@ -136,6 +138,7 @@ template <class Tab>
 __global__ void __launch_bounds__(kDrawThreads)
 k_draw_params(const __grid_constant__ Tab tab) {
     __shared__ float red[32];
+    __shared__ float lgc[kDrawCache];
     int64_t base = 0;
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
@@ -149,7 +152,7 @@ k_draw_params(const __grid_constant__ Tab tab) {
                 if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
                 clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
             }
-            draw_row(ch, K, t, row, red);
+            draw_row(ch, K, t, row, red, lgc);
             __syncthreads();
         }
         base += rows;

@@ -843,7 +843,7 @@ k_stats_tile(const __grid_constant__ Tab tab) {
     }
 }
 
-int32_t tile_stat_groups(const Ctx& c) { return max(1, (2 * c.num_sms) / c.tile_C); }
+int32_t tile_stat_groups(const Ctx& c) { return max(1, (4 * c.num_sms) / c.tile_C); }
 
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
 
