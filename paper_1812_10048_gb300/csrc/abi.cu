@@ -106,7 +106,7 @@ void free_ctx(Ctx& c) {
     void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
                     c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
-                    c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B,
+                    c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B, c.noise,
                     c.gbar, c.d_chains};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -159,6 +159,7 @@ ChainArgs dpmm::chain_args(const Ctx& c) {
     a.tile_Lslot = c.tile_Lslot;
     a.tile_ent = c.tile_ent;
     a.tile_ptr = c.tile_ptr;
+    a.noise = c.noise;
     a.tile_B = c.tile_B;
     a.alpha = c.alpha;
     a.beta = c.beta;
@@ -457,6 +458,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         CKI(dalloc(&c.tile_ent, (size_t)pos));
         CKI(dalloc(&c.tile_ptr, 4 * TC + 1));
         CKI(dalloc(&c.tile_B, tile_b_bytes(c.tile_C)));
+        CKI(dalloc(&c.noise, (size_t)(kTileMaxK + 2) * (size_t)N));
 
         CKI(cudaMemcpyAsync(c.tile_ptr, tptr.data(), sizeof(int32_t) * (4 * TC + 1),
                             cudaMemcpyHostToDevice, c.stream));

@@ -155,6 +155,7 @@ struct Ctx {
     uint32_t* tile_ent = nullptr;   // row << 22 | gene-in-chunk << 16 | count (0: padding)
     int32_t* tile_ptr = nullptr;    // [4 T C + 1] quarter starts
     unsigned char* tile_B = nullptr;  // per-sweep BF16 hi/lo table, [C][256 rows][64] swizzled
+    float* noise = nullptr;         // [kTileMaxK + 2][N] the sweep's label noise (tile engine)
 
 
     // chains this context's launches walk: itself (nchains = 1) or, for a
@@ -250,6 +251,35 @@ __device__ __forceinline__ float log_gamma_draw(const Stream& st, uint32_t tag, 
     return logf(d);
 }
 
+// Label noise of a sweep for the dense-tile engine (chains with the blocked
+// copy and 1 <= K <= kTileMaxK): row k < K of ch.noise holds the Gumbel of
+// (cell, k) from the eq. 4 label words (cell, t, ., k / 4), word k % 4; rows K
+// and K + 1 the two eq. 8 sub-label Gumbels (words 0, 1 of (cell, t, ., 0));
+// cluster-major, N floats a row.  The values are the ones the label kernel
+// would draw itself; it reads them before its accumulators are ready.  Filled
+// by the launch before it, cells dealt over the given threads.
+template <class Tab>
+__device__ __forceinline__ void fill_noise(const Tab& tab, int64_t nthreads, int64_t gtid) {
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        const int K = ch.sc->K;
+        if (!ch.tile_enabled || K < 1 || K > kTileMaxK) continue;
+        const uint32_t t = ch.sc->t;
+        const int64_t N = ch.N;
+        float* __restrict__ out = ch.noise;
+        for (int64_t cell = gtid; cell < N; cell += nthreads) {
+            for (int k0 = 0; k0 < K; k0 += 4) {
+                const uint4 w = ch.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k0 >> 2));
+                const int n = min(4, K - k0);
+                for (int i = 0; i < n; ++i) out[(size_t)(k0 + i) * N + cell] = gumbel(word_of(w, i));
+            }
+            const uint4 h = ch.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+            out[(size_t)K * N + cell] = gumbel(h.x);
+            out[(size_t)(K + 1) * N + cell] = gumbel(h.y);
+        }
+    }
+}
+
 // Digamma psi(x), x > 0: upward recurrence psi(x) = psi(x+1) - 1/x to x >= 6,
 // then the asymptotic series ln x - 1/(2x) - 1/(12x^2) + 1/(120x^4)
 // - 1/(252x^6) + 1/(240x^8) (Abramowitz & Stegun 6.3.5, 6.3.18).
@@ -334,6 +364,7 @@ struct ChainArgs {
     int32_t tile_enabled, tile_C, tile_T, tile_Lslot;
     uint32_t* tile_ent;
     int32_t* tile_ptr;
+    float* noise;
     unsigned char* tile_B;
     // hyper-parameters and random stream
     double alpha, beta, log_alpha, lg_beta;

@@ -73,6 +73,7 @@ __global__ void k_select_engine(const __grid_constant__ Tab tab) {
         if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
         clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
     }
+    fill_noise(tab, (int64_t)gridDim.x * blockDim.x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Rows 0 .. 3K-1 are theta rows (row 3k + p: cluster k for p = 0, its
@@ -157,6 +158,12 @@ k_draw_params(const __grid_constant__ Tab tab) {
         }
         base += rows;
     }
+    // the label noise: blocks without a row take it (all blocks when every
+    // block has rows)
+    const int64_t free0 = base < gridDim.x ? base : 0;
+    if ((int64_t)blockIdx.x >= free0)
+        fill_noise(tab, ((int64_t)gridDim.x - free0) * blockDim.x,
+                   ((int64_t)blockIdx.x - free0) * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -764,7 +771,7 @@ cudaError_t launch_draw_params(Ctx& c) {
 
 cudaError_t launch_select_engine(Ctx& c) {
     return with_table(c, [&](auto tab) {
-        k_select_engine<<<c.nchains < c.num_sms ? c.nchains : c.num_sms, 256, 0, c.stream>>>(tab);
+        k_select_engine<<<2 * c.num_sms, 256, 0, c.stream>>>(tab);
         return cudaGetLastError();
     });
 }

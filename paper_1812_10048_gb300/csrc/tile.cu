@@ -618,7 +618,6 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
             if (!cnt) continue;
             const int K = ch.sc->K;
             const int S0 = tile_s0(K), Ntot = tile_ntot(K);
-            const uint32_t t = ch.sc->t;
             // this chain's log pi, eq. 8 weights and log q sums in shared memory
             tc::named_bar(kBarEpi, 32 * kEpiWarps);
             for (int k = tid; k < K; k += 32 * kEpiWarps) spi[k] = ch.logpi[k];
@@ -632,12 +631,23 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
             for (int ti = 0; ti < cnt; ++ti, ++it) {
                 const int tile = first + ti * (int)gridDim.x;
                 const uint32_t buf = it & 1, xb = it & 1;
+                const int64_t cell = (int64_t)tile * 128 + r;
+                const bool live = cell < ch.N;
+                // this cell's noise for the first cluster group of the half (and
+                // half 1's eq. 8 noise), loaded before the accumulator is ready
+                float gpre[8], gs0 = 0.0f, gs1 = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    gpre[i] = live && 8 * h + i < K ? __ldg(ch.noise + (size_t)(8 * h + i) * ch.N + cell)
+                                                    : 0.0f;
+                if (h == 1 && live) {
+                    gs0 = __ldg(ch.noise + (size_t)K * ch.N + cell);
+                    gs1 = __ldg(ch.noise + (size_t)(K + 1) * ch.N + cell);
+                }
                 const bool ok = tc::mbar_wait(&acc_full[buf], (it >> 1) & 1, kWaitLimit);
                 if (!ok) *err = DPMM_ETIMEOUT;
                 tc::fence_after_sync();
                 const bool okw = __all_sync(0xFFFFFFFFu, ok);
-                const int64_t cell = (int64_t)tile * 128 + r;
-                const bool live = cell < ch.N;
                 const uint32_t trow = tmem + buf * 256u + ((uint32_t)(32 * qw) << 16);
                 float best = -CUDART_INF_F;
                 int c = h ? K : 0;   // half 1's "none" loses every tie
@@ -646,16 +656,15 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                         float v[16];
                         tc::tmem_ld16(trow + (uint32_t)(16 * q), v);
                         tc::tmem_ld_wait();
-                        uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const int k = 8 * q + i;
-                            if ((i & 3) == 0 && k < K)
-                                w4 = ch.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k >> 2));
                             if (k < K) {
                                 const float sc = v[2 * i] + v[2 * i + 1];
                                 if (dbg && live) dbg_out[(size_t)cell * 3 * K + k] = sc;
-                                const float val = (spi[k] + sc) + gumbel(word_of(w4, i & 3));
+                                const float gk = q == h ? gpre[i]
+                                                 : (live ? __ldg(ch.noise + (size_t)k * ch.N + cell) : 0.0f);
+                                const float val = (spi[k] + sc) + gk;
                                 if (val > best) {
                                     best = val;
                                     c = k;
@@ -667,9 +676,8 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                 if (h == 1) {
                     xbest[128 * xb + r] = best;
                     xc[128 * xb + r] = c;
-                    const uint4 hw = ch.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
-                    xg0[128 * xb + r] = gumbel(hw.x);
-                    xg1[128 * xb + r] = gumbel(hw.y);
+                    xg0[128 * xb + r] = gs0;
+                    xg1[128 * xb + r] = gs1;
                 }
                 tc::fence_before_sync();
                 if (tid == 0) stop[xb] = *err;
