@@ -251,35 +251,6 @@ __device__ __forceinline__ float log_gamma_draw(const Stream& st, uint32_t tag, 
     return logf(d);
 }
 
-// Label noise of a sweep for the dense-tile engine (chains with the blocked
-// copy and 1 <= K <= kTileMaxK): row k < K of ch.noise holds the Gumbel of
-// (cell, k) from the eq. 4 label words (cell, t, ., k / 4), word k % 4; rows K
-// and K + 1 the two eq. 8 sub-label Gumbels (words 0, 1 of (cell, t, ., 0));
-// cluster-major, N floats a row.  The values are the ones the label kernel
-// would draw itself; it reads them before its accumulators are ready.  Filled
-// by the launch before it, cells dealt over the given threads.
-template <class Tab>
-__device__ __forceinline__ void fill_noise(const Tab& tab, int64_t nthreads, int64_t gtid) {
-    for (int b = 0; b < tab.n(); ++b) {
-        const ChainArgs& ch = tab[b];
-        const int K = ch.sc->K;
-        if (!ch.tile_enabled || K < 1 || K > kTileMaxK) continue;
-        const uint32_t t = ch.sc->t;
-        const int64_t N = ch.N;
-        float* __restrict__ out = ch.noise;
-        for (int64_t cell = gtid; cell < N; cell += nthreads) {
-            for (int k0 = 0; k0 < K; k0 += 4) {
-                const uint4 w = ch.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k0 >> 2));
-                const int n = min(4, K - k0);
-                for (int i = 0; i < n; ++i) out[(size_t)(k0 + i) * N + cell] = gumbel(word_of(w, i));
-            }
-            const uint4 h = ch.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
-            out[(size_t)K * N + cell] = gumbel(h.x);
-            out[(size_t)(K + 1) * N + cell] = gumbel(h.y);
-        }
-    }
-}
-
 // Digamma psi(x), x > 0: upward recurrence psi(x) = psi(x+1) - 1/x to x >= 6,
 // then the asymptotic series ln x - 1/(2x) - 1/(12x^2) + 1/(120x^4)
 // - 1/(252x^6) + 1/(240x^8) (Abramowitz & Stegun 6.3.5, 6.3.18).
@@ -474,6 +445,46 @@ __device__ __forceinline__ void stats_cells(const Csr& csr, const uint32_t* __re
 }
 
 // Calls launch(table) with the context's chains in the fitting table form.
+// Label noise of a sweep for the dense-tile engine (chains with the blocked
+// copy and 1 <= K <= kTileMaxK): row k < K of ch.noise holds the Gumbel of
+// (cell, k) from the eq. 4 label words (cell, t, ., k / 4), word k % 4; rows K
+// and K + 1 the two eq. 8 sub-label Gumbels (words 0, 1 of (cell, t, ., 0));
+// cluster-major, N floats a row.  The values are the ones the label kernel
+// would draw itself; it reads them before its accumulators are ready.
+__device__ __forceinline__ void noise_cells(const ChainArgs& ch, int64_t first, int64_t stride) {
+    const int K = ch.sc->K;
+    if (!ch.tile_enabled || K < 1 || K > kTileMaxK) return;
+    const uint32_t t = ch.sc->t;
+    const int64_t N = ch.N;
+    float* __restrict__ out = ch.noise;
+    for (int64_t cell = first; cell < N; cell += stride) {
+        for (int k0 = 0; k0 < K; k0 += 4) {
+            const uint4 w = ch.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k0 >> 2));
+            out[(size_t)k0 * N + cell] = gumbel(w.x);
+            if (k0 + 1 < K) out[(size_t)(k0 + 1) * N + cell] = gumbel(w.y);
+            if (k0 + 2 < K) out[(size_t)(k0 + 2) * N + cell] = gumbel(w.z);
+            if (k0 + 3 < K) out[(size_t)(k0 + 3) * N + cell] = gumbel(w.w);
+        }
+        const uint4 h = ch.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+        out[(size_t)K * N + cell] = gumbel(h.x);
+        out[(size_t)(K + 1) * N + cell] = gumbel(h.y);
+    }
+}
+// Blocks blk of nblocks take the noise: with at least as many blocks as
+// chains, chain c gets the blocks blk = c mod n and splits its cells over
+// them; else block blk takes chains blk, blk + nblocks, ... alone.
+template <class Tab>
+__device__ __forceinline__ void fill_noise(const Tab& tab, int64_t nblocks, int64_t blk) {
+    const int64_t n = tab.n();
+    if (nblocks >= n) {
+        const int64_t c = blk % n, rank = blk / n, nb = (nblocks - c + n - 1) / n;
+        noise_cells(tab[(int)c], rank * blockDim.x + threadIdx.x, nb * blockDim.x);
+    } else {
+        for (int64_t c = blk; c < n; c += nblocks)
+            noise_cells(tab[(int)c], threadIdx.x, blockDim.x);
+    }
+}
+
 template <class F>
 cudaError_t with_table(const Ctx& c, F launch) {
     if (c.nchains == 1) return launch(TabV{*c.h_chain0});

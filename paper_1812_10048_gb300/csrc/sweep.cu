@@ -73,7 +73,7 @@ __global__ void k_select_engine(const __grid_constant__ Tab tab) {
         if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
         clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
     }
-    fill_noise(tab, (int64_t)gridDim.x * blockDim.x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    fill_noise(tab, (int64_t)gridDim.x, (int64_t)blockIdx.x);
 }
 
 // Rows 0 .. 3K-1 are theta rows (row 3k + p: cluster k for p = 0, its
@@ -162,8 +162,7 @@ k_draw_params(const __grid_constant__ Tab tab) {
     // block has rows)
     const int64_t free0 = base < gridDim.x ? base : 0;
     if ((int64_t)blockIdx.x >= free0)
-        fill_noise(tab, ((int64_t)gridDim.x - free0) * blockDim.x,
-                   ((int64_t)blockIdx.x - free0) * blockDim.x + threadIdx.x);
+        fill_noise(tab, (int64_t)gridDim.x - free0, (int64_t)blockIdx.x - free0);
 }
 
 // ---------------------------------------------------------------------------

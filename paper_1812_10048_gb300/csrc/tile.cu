@@ -851,7 +851,12 @@ k_stats_tile(const __grid_constant__ Tab tab) {
     }
 }
 
-int32_t tile_stat_groups(const Ctx& c) { return max(1, (4 * c.num_sms) / c.tile_C); }
+// Tile groups per gene chunk of the statistics launch: four blocks per SM
+// for one chain; two for a batch, whose chains the blocks take in turn (each
+// chain costs every block a clear and a flush of its counters).
+int32_t tile_stat_groups(const Ctx& c) {
+    return max(1, ((c.nchains > 1 ? 2 : 4) * c.num_sms) / c.tile_C);
+}
 
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
 
