@@ -287,6 +287,29 @@ int dpmm_logml_grad(dpmm_ctx* ctx, const int32_t* labels, int32_t K_labels, doub
                     float* grad_log_beta);
 
 /*
+ * Replace the DP concentration alpha and the symmetric Dirichlet parameter
+ * beta of a chain (the alpha of eq. 4's pi draw, the lambda of eq. 28) between
+ * steps.  The chain's state is kept; the next step draws with the new values.
+ * alpha, beta > 0 and finite, else DPMM_EINVAL; a batch or a batch member:
+ * DPMM_EINVAL / DPMM_ESTATE.  Synchronises the context's stream.
+ */
+int dpmm_set_hyper(dpmm_ctx* ctx, double alpha, double beta);
+
+/*
+ * One empirical-Bayes step on (log alpha, log beta) for the chain's current
+ * partition: gradient ascent on the collapsed log marginal likelihood of
+ * dpmm_logml_grad, with beta tied across genes (its gradient is the sum of
+ * the gene-wise ones, in FP64):
+ *   log alpha += clamp(eta_alpha * dLML/dlog alpha, -max_step, max_step)
+ *   log beta  += clamp(eta_beta  * sum_u dLML/dlog beta_u, -max_step, max_step)
+ * then dpmm_set_hyper.  Alternating it with dpmm_step gives an empirical-Bayes
+ * loop.  Outputs (host, may be NULL): the log ML before the step and the new
+ * alpha and beta.  eta finite, max_step >= 0, else DPMM_EINVAL.  Synchronises.
+ */
+int dpmm_eb_step(dpmm_ctx* ctx, double eta_alpha, double eta_beta, double max_step,
+                 double* logml, double* alpha_out, double* beta_out);
+
+/*
  * Allocation-free variant of dpmm_logml_create + dpmm_logml_forward +
  * dpmm_logml_backward, for callers that cannot allocate device memory (for
  * example a framework whose caching allocator owns the GPU's memory, or

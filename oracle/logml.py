@@ -60,3 +60,18 @@ def log_ml_grad(n, S, log_alpha, log_beta):
     per_gene = (digamma(B) - digamma(B + T)).sum() + (digamma(beta[None, :] + S)
                                                        - digamma(beta)[None, :]).sum(axis=0)
     return g_alpha, beta * per_gene
+
+
+def eb_step(n, S, log_alpha, log_beta, eta_alpha, eta_beta, max_step):
+    """One empirical-Bayes step on (log alpha, log beta) with beta tied across
+    genes: gradient ascent on ``log_ml`` (whose log beta is the vector of D
+    equal values), each move clamped to [-max_step, max_step].  Returns (log ML
+    before the step, new log alpha, new log beta).  The tied gradient is the
+    sum of the gene-wise ones (chain rule for a shared log beta)."""
+    D = S.shape[1]
+    lb = np.full(D, float(log_beta))
+    lml = log_ml(n, S, log_alpha, lb)
+    g_alpha, g_beta = log_ml_grad(n, S, log_alpha, lb)
+    da = min(max_step, max(-max_step, eta_alpha * g_alpha))
+    db = min(max_step, max(-max_step, eta_beta * float(np.sum(g_beta))))
+    return lml, log_alpha + da, float(log_beta) + db

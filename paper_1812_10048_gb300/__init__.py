@@ -17,7 +17,8 @@ from ._lib import (DpmmError, ENGINE_AUTO, ENGINE_CSR_FP32, ENGINE_TILE_BF16, ch
 __all__ = [
     "DpmmError", "Sampler", "LogML", "dpmm_default_opts", "dpmm_init", "dpmm_free", "dpmm_sweep",
     "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
-    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_init_batch",
+    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_set_hyper",
+    "dpmm_eb_step", "empirical_bayes", "dpmm_init_batch",
     "dpmm_chain", "BatchSampler", "dpmm_get_state",
     "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
     "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_tile_scores", "dpmm_debug_moves", "dpmm_logml_create",
@@ -130,6 +131,31 @@ def dpmm_logml_grad(ctx, log_alpha, log_beta, labels=None, K=0, grad=True):
                                 float(log_alpha), ptr(lb), ctypes.byref(out),
                                 ctypes.byref(ga) if grad else None, ptr(gb) if grad else None))
     return (out.value, ga.value, gb) if grad else out.value
+
+
+def dpmm_set_hyper(ctx, alpha, beta):
+    """Replace a chain's alpha and beta between steps (state kept)."""
+    check(lib().dpmm_set_hyper(ctx, float(alpha), float(beta)))
+
+
+def dpmm_eb_step(ctx, eta_alpha, eta_beta, max_step=0.5):
+    """One empirical-Bayes step on (log alpha, tied log beta) for the chain's
+    current partition; returns (log ML before the step, new alpha, new beta)."""
+    lml, a, b = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(lib().dpmm_eb_step(ctx, float(eta_alpha), float(eta_beta), float(max_step),
+                             ctypes.byref(lml), ctypes.byref(a), ctypes.byref(b)))
+    return lml.value, a.value, b.value
+
+
+def empirical_bayes(sampler, rounds, sweeps, eta_alpha, eta_beta, max_step=0.5):
+    """Empirical-Bayes loop: `rounds` times, `sweeps` steps of the sampler then
+    one dpmm_eb_step.  Returns the trace [(log ML, alpha, beta), ...]."""
+    trace = []
+    for _ in range(int(rounds)):
+        if sweeps:
+            sampler.step(int(sweeps))
+        trace.append(dpmm_eb_step(sampler.ctx, eta_alpha, eta_beta, max_step))
+    return trace
 
 
 def dpmm_profile(ctx, enable=True):
@@ -303,6 +329,9 @@ class Sampler:
 
     def step(self, n=1):
         dpmm_step(self.ctx, n)
+
+    def set_hyper(self, alpha, beta):
+        dpmm_set_hyper(self.ctx, alpha, beta)
 
     def labels(self):
         return dpmm_labels(self.ctx, self.N)

@@ -50,6 +50,9 @@ SIGNATURES = {
     "dpmm_init_batch": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "dpmm_chain": (ctypes.c_int, [_P, _I32, _P]),
     "dpmm_logml_grad": (ctypes.c_int, [_P, _P, _I32, ctypes.c_double, _P, _P, _P, _P]),
+    "dpmm_set_hyper": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double]),
+    "dpmm_eb_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P,
+                                    _P]),
     "dpmm_profile": (ctypes.c_int, [_P, _I32]),
     "dpmm_phase_times": (ctypes.c_int, [_P, _P, _I32]),
     "dpmm_stream": (_P, [_P]),

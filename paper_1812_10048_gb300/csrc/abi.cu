@@ -1117,6 +1117,58 @@ int dpmm_logml_grad(dpmm_ctx* ctx, const int32_t* labels, int32_t K_labels, doub
     return DPMM_OK;
 }
 
+int dpmm_set_hyper(dpmm_ctx* ctx, double alpha, double beta) {
+    CHECK_CHAIN(ctx);
+    if (ctx->member)
+        return fail(DPMM_ESTATE, "a batch member: its hyper-parameters are held by the batch");
+    if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta))
+        return fail(DPMM_EINVAL, "alpha and beta must be positive and finite");
+    Ctx& c = ctx->c;
+    CK(cudaStreamSynchronize(c.stream));
+    c.alpha = alpha;
+    c.beta = beta;
+    // the chain table (alpha, beta, log alpha, lgamma(beta)) the kernels take,
+    // the lgamma tables that depend on beta, and the step graph that holds the
+    // old table by value
+    *c.h_chain0 = chain_args(c);
+    CK(cudaMemcpyAsync(c.d_chains, c.h_chain0, sizeof(ChainArgs), cudaMemcpyHostToDevice,
+                       c.stream));
+    CK(launch_lg_table(c));
+    if (c.step_exec) {
+        cudaGraphExecDestroy(c.step_exec);
+        c.step_exec = nullptr;
+    }
+    CK(cudaStreamSynchronize(c.stream));
+    return DPMM_OK;
+}
+
+int dpmm_eb_step(dpmm_ctx* ctx, double eta_alpha, double eta_beta, double max_step,
+                 double* logml, double* alpha_out, double* beta_out) {
+    CHECK_CHAIN(ctx);
+    if (ctx->member)
+        return fail(DPMM_ESTATE, "a batch member: its hyper-parameters are held by the batch");
+    if (!(max_step >= 0.0) || !std::isfinite(eta_alpha) || !std::isfinite(eta_beta))
+        return fail(DPMM_EINVAL, "eta_alpha, eta_beta must be finite and max_step >= 0");
+    Ctx& c = ctx->c;
+    const double la = std::log(c.alpha), lb = std::log(c.beta);
+    std::vector<float> lbv((size_t)c.D, (float)lb), g((size_t)c.D, 0.0f);
+    double lml = 0.0, ga = 0.0;
+    int rc = dpmm_logml_grad(ctx, nullptr, 0, la, lbv.data(), &lml, &ga, g.data());
+    if (rc) return rc;
+    // beta is tied across genes: its gradient is the sum of the gene-wise ones
+    // (FP64, gene order)
+    double gb = 0.0;
+    for (int32_t u = 0; u < c.D; ++u) gb += (double)g[(size_t)u];
+    const double da = std::min(max_step, std::max(-max_step, eta_alpha * ga));
+    const double db = std::min(max_step, std::max(-max_step, eta_beta * gb));
+    const double alpha = std::exp(la + da), beta = std::exp(lb + db);
+    if ((rc = dpmm_set_hyper(ctx, alpha, beta))) return rc;
+    if (logml) *logml = lml;
+    if (alpha_out) *alpha_out = alpha;
+    if (beta_out) *beta_out = beta;
+    return DPMM_OK;
+}
+
 // ---- generator test hooks --------------------------------------------------
 
 __global__ void k_debug_philox(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,

@@ -77,3 +77,40 @@ def test_ari_matches_brute_force_pair_counting():
         b = np.where(rng.random(60) < 0.6, a, rng.integers(0, 5, size=60))
         assert abs(adjusted_rand_index(a, b) - pair_counting_ari(a, b)) < 1e-12
     assert adjusted_rand_index([0, 0, 1, 1], [5, 5, 2, 2]) == 1.0
+
+
+# ---------------------------------------------------------------------------
+# empirical-Bayes step (beta tied across genes)
+# ---------------------------------------------------------------------------
+def test_eb_step_tied_gradient_matches_finite_differences():
+    """The tied log-beta move is eta times d LML / d(shared log beta), checked
+    by a central difference of log_ml along the common log beta; likewise for
+    log alpha."""
+    from oracle.logml import eb_step
+    x, labels, indptr, indices, data = small_problem(seed=3)
+    n, S = cluster_stats(indptr, indices, data, x.shape[0], x.shape[1], labels, 4)
+    D = x.shape[1]
+    la, lb, h = 0.2, math.log(0.3), 1e-6
+    lml, la2, lb2 = eb_step(n, S, la, lb, 1.0, 1.0, 1e9)
+    fa = (log_ml(n, S, la + h, np.full(D, lb)) - log_ml(n, S, la - h, np.full(D, lb))) / (2 * h)
+    fb = (log_ml(n, S, la, np.full(D, lb + h)) - log_ml(n, S, la, np.full(D, lb - h))) / (2 * h)
+    assert abs(lml - log_ml(n, S, la, np.full(D, lb))) == 0.0
+    assert abs((la2 - la) - fa) < 1e-6 * max(1.0, abs(fa))
+    assert abs((lb2 - lb) - fb) < 1e-6 * max(1.0, abs(fb))
+
+
+def test_eb_step_clamps_and_ascends():
+    from oracle.logml import eb_step
+    x, labels, indptr, indices, data = small_problem(seed=4)
+    n, S = cluster_stats(indptr, indices, data, x.shape[0], x.shape[1], labels, 4)
+    D = x.shape[1]
+    la, lb = 1.5, math.log(3.0)
+    _, la2, lb2 = eb_step(n, S, la, lb, 1e6, 1e6, 0.25)
+    assert abs(abs(la2 - la) - 0.25) < 1e-15 and abs(abs(lb2 - lb) - 0.25) < 1e-15
+    # small steps go uphill
+    prev = log_ml(n, S, la, np.full(D, lb))
+    for _ in range(20):
+        _, la, lb = eb_step(n, S, la, lb, 1e-3, 1e-3, 0.1)
+        cur = log_ml(n, S, la, np.full(D, lb))
+        assert cur >= prev - 1e-12
+        prev = cur
