@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="main", choices=["main", "batched", "large", "grad"],
+    ap.add_argument("--config", default="main", choices=["main", "batched", "large", "grad", "eb"],
                     help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
                          "as one batch; large: 1.3M x 2k")
     ap.add_argument("--workers", type=int, default=0,
@@ -577,10 +577,60 @@ def run_grad(args):
     return 0
 
 
+def run_eb(args):
+    """Empirical-Bayes loop on the 68k x 1k workload: rounds of S steps and one
+    dpmm_eb_step (collapsed log-ML gradient, tied beta, new alpha and beta in
+    the chain).  Reports the wall time of an EB step alone (it synchronises)
+    and the sweeps/s of the whole loop at S = 10."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    ds = synth.pbmc68k()
+    s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                  engine=P.ENGINE_AUTO)
+    s.step(max(3, args.warmup))
+    s.sync()
+    rounds, S = max(10, args.steps), 10
+    eta_a, eta_b, cap = 0.01, 1e-6, 0.1
+    # one EB step alone (after its first call, which allocates the log-ML scratch)
+    P.dpmm_eb_step(s.ctx, eta_a, eta_b, cap)
+    s.step(1)
+    s.sync()
+    t0 = time.perf_counter()
+    for _ in range(rounds):
+        P.dpmm_eb_step(s.ctx, eta_a, eta_b, cap)
+    eb_us = (time.perf_counter() - t0) * 1e6 / rounds
+    # the loop as a user runs it: S steps (the first re-captures the step
+    # graph with the new alpha, beta) then an EB step
+    s.sync()
+    t0 = time.perf_counter()
+    trace = P.empirical_bayes(s, rounds=rounds, sweeps=S, eta_alpha=eta_a, eta_beta=eta_b,
+                              max_step=cap)
+    s.sync()
+    loop_s = time.perf_counter() - t0
+    line = {
+        "metric": "empirical-Bayes loop at 68k cells x 1k genes (10 steps + 1 EB step per round)",
+        "value": round(rounds * S / loop_s, 1), "unit": "sweeps/s including the EB steps",
+        "n_gpus": 1, "steps": rounds, "warmup": args.warmup, "higher_is_better": True,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "pbmc68k-synthetic", "N": int(ds.N), "D": int(ds.D),
+                   "eta_alpha": eta_a, "eta_beta": eta_b, "max_step": cap},
+        "eb_step_us": round(eb_us, 1),
+        "trace": [[round(t[0], 1), round(t[1], 5), round(t[2], 5)] for t in trace[:: max(1, rounds // 5)]],
+    }
+    s.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.config == "grad":
         return run_grad(args)
+    if args.config == "eb":
+        return run_eb(args)
     if args.config == "batched":
         return run_batched(args)
     if args.config == "large":
