@@ -51,7 +51,11 @@ typedef struct dpmm_opts {
     int32_t split_q;   /* 1 (default): split ratio includes -sum_i log q_i */
     int32_t chain_id;  /* 0 .. 2^24-1, enters every Philox counter */
     uint64_t seed;     /* Philox key (default 42) */
-    int32_t reserved[8];
+    int32_t hastings;  /* split ratio: 0 (default) theta and pi integrated out (eq. 9,
+                          14, 16 in lgamma sums); 1 eq. 18 with theta and pi
+                          instantiated from the latest sweep's draws (see
+                          dpmm_split_merge); merges use the integrated form */
+    int32_t reserved[7];
 } dpmm_opts;
 
 /* Fill *opts with the defaults above. */
@@ -120,6 +124,13 @@ int dpmm_sweep(dpmm_ctx* ctx, int32_t n_sweeps);
  * proposal ratio), mode 0 picks one of the two by a fair coin.  If
  * n_accepted is not NULL the call synchronises and stores the number of
  * accepted moves; otherwise it is asynchronous.
+ * With opts.hastings = 1 a split's ratio is eq. 18 (eq. 14 times eq. 16)
+ * with theta_{k0,k1} = theta-bar_{k,0/1} and pi_{kr} = pi_k n-bar_r / n_k,
+ * taken from the draws of the latest dpmm_sweep / dpmm_step: a cluster is
+ * proposed only if that sweep's compaction was the last change of the state
+ * and kept its sub-labels; otherwise its log H is NaN and nothing is split.
+ * Eq. 18 carries no density for drawing the new theta, so it favours every
+ * split by thousands of nats at D ~ 1000 (use the default for sampling).
  */
 int dpmm_split_merge(dpmm_ctx* ctx, int32_t mode, int32_t* n_accepted);
 

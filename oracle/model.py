@@ -71,6 +71,36 @@ def log_hastings_split(nbar0, nbar1, Sbar0, Sbar1, alpha, beta, sum_logq):
             - log_marginal_cluster(Sk, beta) - sum_logq)
 
 
+def log_hastings_split_instantiated(nbar0, nbar1, Sbar0, Sbar1, logtheta_k, logtheta_0,
+                                    logtheta_1, logpi_k, alpha, beta, sum_logq):
+    """Log Hastings ratio of splitting cluster k with theta and pi instantiated
+    (eq. 7 with the likelihood ratio of eq. 18, i.e. eq. 14 times eq. 16).
+
+    Readings: the split clusters' parameters are the sweep's sub-cluster draws,
+    theta_{k0} = theta-bar_{k,0}, theta_{k1} = theta-bar_{k,1}, and the mixing
+    weights divide pi_k by the sub-cluster sizes, pi_{kr} = pi_k n-bar_r / n_k.
+    Eq. 14: log alpha + (n-bar_0 - 1) log pi_{k0} + (n-bar_1 - 1) log pi_{k1}
+    - (n_k - 1) log pi_k.  Eq. 16: one more Dirichlet(beta) density (its
+    normaliser lgamma(D beta) - D lgamma(beta) and (beta - 1) sum_u log theta of
+    each side) and the multinomial likelihoods sum_u S_u log theta_u of the
+    cells of each side (multinomial coefficients cancel).  The proposal term
+    is the one of the integrated form.
+    """
+    S0 = np.asarray(Sbar0, dtype=np.float64)
+    S1 = np.asarray(Sbar1, dtype=np.float64)
+    lk = np.asarray(logtheta_k, dtype=np.float64)
+    l0 = np.asarray(logtheta_0, dtype=np.float64)
+    l1 = np.asarray(logtheta_1, dtype=np.float64)
+    D = S0.size
+    nk = nbar0 + nbar1
+    lp0 = logpi_k + np.log(nbar0 / nk)
+    lp1 = logpi_k + np.log(nbar1 / nk)
+    eq14 = np.log(alpha) + (nbar0 - 1) * lp0 + (nbar1 - 1) * lp1 - (nk - 1) * logpi_k
+    prior = gammaln(D * beta) - D * gammaln(beta) + (beta - 1) * (l0.sum() + l1.sum() - lk.sum())
+    lik = S0 @ l0 + S1 @ l1 - (S0 + S1) @ lk
+    return eq14 + prior + lik - sum_logq
+
+
 def log_hastings_merge(na, nb, Sa, Sb, alpha, beta):
     """Log Hastings ratio of merging clusters a and b (Section 2.4).
 

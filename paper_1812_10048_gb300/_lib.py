@@ -29,7 +29,7 @@ class DpmmError(RuntimeError):
 class dpmm_opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_int32), ("engine", ctypes.c_int32), ("split_q", ctypes.c_int32),
                 ("chain_id", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("hastings", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 _P = ctypes.c_void_p

@@ -166,6 +166,7 @@ ChainArgs dpmm::chain_args(const Ctx& c) {
     a.log_alpha = std::log(c.alpha);
     a.lg_beta = std::lgamma(c.beta);
     a.split_q = c.opts.split_q;
+    a.hastings = c.opts.hastings;
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
     return a;
 }
@@ -319,6 +320,8 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         return fail(DPMM_EINVAL, "kmax = %d outside [1, %d]", o.kmax, kMaxKmax);
     if (o.chain_id < 0 || o.chain_id >= (1 << 24))
         return fail(DPMM_EINVAL, "chain_id = %d outside [0, 2^24)", o.chain_id);
+    if (o.hastings != 0 && o.hastings != 1)
+        return fail(DPMM_EINVAL, "hastings = %d, need 0 or 1", o.hastings);
 
     std::vector<int32_t> hptr, hidx, hval;
     int rc;
@@ -789,6 +792,7 @@ int dpmm_set_state(dpmm_ctx* ctx, const int32_t* labels, const uint8_t* sub, int
     c.sc_host->K_new = K;
     c.sc_host->t = (uint32_t)t;
     c.sc_host->m = (uint32_t)m;
+    c.sc_host->inst_fresh = 0;   // no sweep's draws belong to the new state
     CK(cudaMemcpy(c.sc, c.sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice));
     if ((rc = recount_all(c))) return rc;
     CK(cudaStreamSynchronize(c.stream));

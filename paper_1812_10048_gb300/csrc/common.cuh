@@ -75,7 +75,8 @@ struct DevScalars {
     int32_t tile_used;    // the dense-tile engine labels this sweep's cells
     int32_t apply;        // the pending plan changes some label or statistic
     uint32_t n_apply;     // plans applied so far (sweep compactions and moves)
-    int32_t pad;
+    int32_t inst_fresh;   // the last plan was a sweep's compaction: the sweep's
+                          // pi / theta draws (pre-compaction rows) serve eq. 18
 };
 
 // The dense-tile engine serves 1 <= K <= kTileMaxK.
@@ -340,7 +341,7 @@ struct ChainArgs {
     // hyper-parameters and random stream
     double alpha, beta, log_alpha, lg_beta;
     int32_t split_q;
-    int32_t pad;
+    int32_t hastings;     // 1: instantiated eq. 18 split ratio
     Stream st;
 };
 

@@ -157,7 +157,9 @@ __device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __res
                MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
                int32_t* __restrict__ decide, double* __restrict__ log_h, int32_t D,
                double log_alpha, double beta, double lg_beta, int32_t split_q, int32_t mode,
-               Stream st) {
+               Stream st, int32_t hastings, const float* __restrict__ Lc,
+               const float* __restrict__ Ls, const float* __restrict__ logpi,
+               const int32_t* __restrict__ desc, int32_t kmax) {
     __shared__ double fin[kPartialWarps][2];
     __shared__ int last;
     __shared__ uint32_t keys[kMaxKmax];
@@ -204,7 +206,30 @@ __device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __res
     const int u0 = g * Dc, u1 = min(D, u0 + Dc);
     double acc = 0.0;
     unsigned long long Ta = 0, Tb = 0;
-    if (split) {
+    // eq. 18 (instantiated): the pre-compaction row of cluster e in the
+    // latest sweep's draws, or -1 when they do not serve it (a move since the
+    // sweep, or its sub-labels were reset by the compaction)
+    int inst_row = -1;
+    if (split && hastings) {
+        const int32_t d = desc[2 * e];
+        if (sc->inst_fresh && (d & 3) == DESC_SUB0) inst_row = d >> 2;
+    }
+    if (split && hastings) {
+        // per gene: (beta - 1 + S0) log theta-bar_0 + (beta - 1 + S1) log theta-bar_1
+        //           - (beta - 1 + S0 + S1) log theta_k   (eq. 16, prior and likelihood)
+        const uint32_t* S0 = Ssub + (size_t)(2 * e) * D;
+        const uint32_t* S1 = S0 + D;
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+            const uint32_t a = S0[u], b = S1[u];
+            Ta += a;
+            Tb += b;
+            if (inst_row >= 0) {
+                const size_t r = (size_t)u * kmax + inst_row;
+                const double l0 = Ls[2 * r], l1 = Ls[2 * r + 1], lk = Lc[r];
+                acc += (beta - 1.0 + a) * l0 + (beta - 1.0 + b) * l1 - (beta - 1.0 + a + b) * lk;
+            }
+        }
+    } else if (split) {
         const uint32_t* S0 = Ssub + (size_t)(2 * e) * D;
         const uint32_t* S1 = S0 + D;
         for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
@@ -295,12 +320,24 @@ __device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __res
     acc = fin[0][0];
     const double log_u = fin[0][1];
     if (split) {
-        if (na < 1 || nb < 1) {
+        if (na < 1 || nb < 1 || (hastings && inst_row < 0)) {
             decide[e] = 0;
             log_h[e] = CUDART_NAN;
             return;
         }
-        double lh = log_alpha + lna + lnb - lnab + lfa + lfb - lfab + acc;
+        double lh;
+        if (hastings) {
+            // eq. 14 with pi_{k r} = pi_k n-bar_r / n_k, eq. 16's Dirichlet
+            // normaliser lgamma(D beta) - D lgamma(beta), and the per-gene sums
+            const double lpk = (double)__ldg(logpi + inst_row);
+            const double nk = (double)na + (double)nb;
+            const double lnk = log_tab(nk, tb);
+            lh = log_alpha + ((double)na - 1.0) * (lpk + log_tab((double)na, tb) - lnk) +
+                 ((double)nb - 1.0) * (lpk + log_tab((double)nb, tb) - lnk) - (nk - 1.0) * lpk +
+                 lgDb - (double)D * lg_beta + acc;
+        } else {
+            lh = log_alpha + lna + lnb - lnab + lfa + lfb - lfab + acc;
+        }
         if (split_q) lh -= sumlogq[e];
         decide[e] = log_u < lh ? 1 : 0;
         log_h[e] = lh;
@@ -321,7 +358,8 @@ k_move_partial(const __grid_constant__ Tab tab, int32_t mode) {
         const ChainArgs& ch = tab[b];
         move_chain(ch.sc, ch.nsub, ch.Ssub, ch.sumlogq, ch.pair_ab, ch.lg_table,
                    reinterpret_cast<MovePartial*>(ch.move_part), ch.move_ticket, ch.decide,
-                   ch.log_h, ch.D, ch.log_alpha, ch.beta, ch.lg_beta, ch.split_q, mode, ch.st);
+                   ch.log_h, ch.D, ch.log_alpha, ch.beta, ch.lg_beta, ch.split_q, mode, ch.st,
+                   ch.hastings, ch.Lc, ch.Ls, ch.logpi, ch.desc, ch.kmax);
         __syncthreads();
     }
 }
@@ -425,6 +463,7 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
             sc->K_new = total;
             sc->any_reinit = any_reset;
             sc->any_relabel = (total != K) || any_reset;
+            sc->inst_fresh = 1;   // desc maps each survivor to its pre-compaction row
             finish_plan(sc, bump);
         }
         return;
@@ -470,6 +509,7 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
             sc->capacity_rejects += total - A;
             sc->any_reinit = A > 0;
             sc->any_relabel = A > 0;
+            sc->inst_fresh = 0;
             finish_plan(sc, bump);
         }
         return;
@@ -533,6 +573,7 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
         sc->n_accepted = K - total;
         sc->any_reinit = 0;
         sc->any_relabel = total != K;
+        sc->inst_fresh = 0;
         finish_plan(sc, bump);
     }
 }

@@ -133,3 +133,84 @@ def test_merge_is_reverse_of_split_without_q():
     s = log_hastings_split(na, nb, Sa, Sb, 1.3, 0.1, 0.0)
     m = log_hastings_merge(na, nb, Sa, Sb, 1.3, 0.1)
     assert abs(m + s - (na + nb - 2) * math.log(0.5)) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# eq. 18 split ratio with theta and pi instantiated
+# ---------------------------------------------------------------------------
+def _tiny_split(seed=11, n=9, D=4):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 5, size=(n, D))
+    side = np.arange(n) % 2
+    lam = 0.7
+    th = rng.dirichlet(np.full(D, 2.0), size=3)          # theta_k, theta-bar_0, theta-bar_1
+    return x, side, lam, th
+
+
+def test_instantiated_split_eq16_part_matches_scipy_densities():
+    """The theta part of eq. 18 (eq. 16) equals the log ratio of the joint
+    densities of (theta, x) written with scipy's Dirichlet and multinomial
+    densities, cell by cell (an independent route: per-cell pmfs with their
+    coefficients, which cancel)."""
+    from scipy.stats import dirichlet, multinomial
+    from oracle.model import log_hastings_split_instantiated
+    x, side, lam, th = _tiny_split()
+    D = x.shape[1]
+    S0, S1 = x[side == 0].sum(0), x[side == 1].sum(0)
+    n0, n1 = int((side == 0).sum()), int((side == 1).sum())
+    # remove the eq. 14 and proposal parts: pi_k = 1 makes eq. 14 = log alpha +
+    # (n0 - 1) log(n0/n) + (n1 - 1) log(n1/n)
+    got = log_hastings_split_instantiated(n0, n1, S0, S1, np.log(th[0]), np.log(th[1]),
+                                          np.log(th[2]), 0.0, 1.0, lam, 0.0)
+    eq14 = (n0 - 1) * np.log(n0 / (n0 + n1)) + (n1 - 1) * np.log(n1 / (n0 + n1))
+    def joint(theta, rows):
+        return sum(multinomial.logpmf(r, r.sum(), theta) for r in rows)
+    ref = (dirichlet.logpdf(th[1], np.full(D, lam)) + dirichlet.logpdf(th[2], np.full(D, lam))
+           + joint(th[1], x[side == 0]) + joint(th[2], x[side == 1])
+           - dirichlet.logpdf(th[0], np.full(D, lam)) - joint(th[0], x))
+    assert abs((got - eq14) - ref) < 1e-9 * max(1.0, abs(ref))
+
+
+def test_instantiated_split_special_cases():
+    """Equal sub-cluster and cluster parameters leave one Dirichlet density and
+    the eq. 14 term; the proposal term enters with a minus sign."""
+    from scipy.stats import dirichlet
+    from oracle.model import log_hastings_split_instantiated
+    x, side, lam, th = _tiny_split(seed=12)
+    D = x.shape[1]
+    S0, S1 = x[side == 0].sum(0), x[side == 1].sum(0)
+    n0 = n1 = 6
+    lpk, alpha = np.log(0.3), 1.7
+    got = log_hastings_split_instantiated(n0, n1, S0, S1, np.log(th[0]), np.log(th[0]),
+                                          np.log(th[0]), lpk, alpha, lam, 0.25)
+    eq14 = np.log(alpha) + 2 * (n0 - 1) * (lpk + np.log(0.5)) - (2 * n0 - 1) * lpk
+    ref = eq14 + dirichlet.logpdf(th[0], np.full(D, lam)) - 0.25
+    assert abs(got - ref) < 1e-10 * max(1.0, abs(ref))
+
+
+def test_instantiated_split_with_posterior_proposal_densities_is_the_collapsed_ratio():
+    """Eq. 16 divided by the densities of drawing theta_k, theta-bar_0 and
+    theta-bar_1 from their Dirichlet posteriors (eq. 28) is the theta-integrated
+    ratio, whatever the theta values: Dir(theta | beta) Mult(x | theta) /
+    Dir(theta | beta + S) is the marginal likelihood of eq. 9's form.  The pi
+    part is removed on both sides with the eq. 14 and CRP terms."""
+    from scipy.stats import dirichlet
+    from scipy.special import gammaln as lg
+    from oracle.model import log_hastings_split_instantiated
+    rng = np.random.default_rng(31)
+    D, lam, alpha = 6, 0.4, 1.3
+    S0 = rng.integers(0, 7, size=D).astype(float)
+    S1 = rng.integers(0, 7, size=D).astype(float)
+    S0[2] = 0.0
+    n0, n1 = 5, 8
+    th = [rng.dirichlet(np.full(D, 1.0)) for _ in range(3)]     # any point of the simplex
+    inst = log_hastings_split_instantiated(n0, n1, S0, S1, np.log(th[0]), np.log(th[1]),
+                                           np.log(th[2]), np.log(0.2), alpha, lam, 0.0)
+    nk = n0 + n1
+    eq14 = (np.log(alpha) + (n0 - 1) * (np.log(0.2) + np.log(n0 / nk))
+            + (n1 - 1) * (np.log(0.2) + np.log(n1 / nk)) - (nk - 1) * np.log(0.2))
+    q = (dirichlet.logpdf(th[1], lam + S0) + dirichlet.logpdf(th[2], lam + S1)
+         - dirichlet.logpdf(th[0], lam + S0 + S1))
+    crp = np.log(alpha) + lg(n0) + lg(n1) - lg(nk)
+    col = log_hastings_split(n0, n1, S0, S1, alpha, lam, 0.0)
+    assert abs((inst - eq14 - q) - (col - crp)) < 1e-9 * max(1.0, abs(col))
