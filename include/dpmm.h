@@ -55,7 +55,12 @@ typedef struct dpmm_opts {
                           14, 16 in lgamma sums); 1 eq. 18 with theta and pi
                           instantiated from the latest sweep's draws (see
                           dpmm_split_merge); merges use the integrated form */
-    int32_t reserved[7];
+    int32_t open_new_cluster;  /* 1: every sweep offers the K+1 candidate of
+                          eq. 4 (theta, theta-bar from the Dirichlet(beta)
+                          prior, weight pi_{K+1}); the cells that choose it
+                          form one new cluster.  0 (default): labels range over
+                          the K existing clusters (new clusters come from splits) */
+    int32_t reserved[6];
 } dpmm_opts;
 
 /* Fill *opts with the defaults above. */
@@ -205,7 +210,11 @@ int dpmm_get_stats(dpmm_ctx* ctx, uint32_t* nsub, uint32_t* Ssub, double* sumlog
 /* ---- phase hooks (the two halves of one sweep) --------------------------- */
 
 /* First half of a sweep: draw log pi (K+1 entries) and log theta for the K
- * clusters and their 2K sub-clusters (eq. 4 first two lines, eq. 19). */
+ * clusters and their 2K sub-clusters (eq. 4 first two lines, eq. 19).  With
+ * opts.open_new_cluster (and K < kmax) it first appends the K+1 candidate as
+ * an empty cluster: K grows by one until dpmm_assign's compaction, the
+ * candidate's theta rows are prior draws, log pi_{K-1} is its alpha weight and
+ * log pi_K = -inf.  Follow it with dpmm_assign. */
 int dpmm_draw_params(dpmm_ctx* ctx);
 
 /* Second half: labels and sub-labels from the current parameters (eq. 4 third

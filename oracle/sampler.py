@@ -19,8 +19,13 @@ Follows Section 2 of the paper in its order and notation:
 Readings where the paper is silent or garbled (each one is the same on the
 CUDA side):
 
-* restricted Gibbs: labels range over the K existing clusters only; new
-  clusters come from splits (Section 2.2-2.3).  pi_{K+1} is drawn but unused;
+* restricted Gibbs by default: labels range over the K existing clusters
+  only; new clusters come from splits (Section 2.2-2.3).  pi_{K+1} is drawn
+  but unused.  With ``open_new_cluster`` the K+1 candidate of eq. 4 is kept:
+  the sweep treats it as one more cluster without cells (its theta and
+  theta-bar are therefore drawn from the Dirichlet(lambda) prior and its
+  weight is pi_{K+1}), all cells that choose it form one new cluster, and
+  there is no candidate when K = kmax;
 * eq. 8's n-bar_{r,not i} in a parallel sweep: the sweep-start sub-cluster
   count minus the indicator that cell i sat in (c_i, r) at sweep start and
   keeps its cluster; if both weights are zero they are taken as equal;
@@ -149,12 +154,13 @@ class Sampler:
     """FP64 Para-DPMM chain over a cells x genes CSR count matrix."""
 
     def __init__(self, indptr, indices, data, N, D, alpha, beta, seed=42, chain_id=0,
-                 kmax=256, split_q=True):
+                 kmax=256, split_q=True, open_new_cluster=False):
         self.X = csr_matrix(indptr, indices, data, N, D)
         self.N, self.D = int(N), int(D)
         self.alpha, self.beta = float(alpha), float(beta)
         self.seed, self.chain_id, self.kmax = int(seed), int(chain_id), int(kmax)
         self.split_q = bool(split_q)
+        self.open_new_cluster = bool(open_new_cluster)
         self.K = 1
         self.labels = np.zeros(self.N, dtype=np.int64)
         self.sub = fair_coin_sublabels(np.arange(self.N), self.seed, self.chain_id, 0,
@@ -182,17 +188,26 @@ class Sampler:
 
     # -- one sweep (eq. 4 + eq. 8 + bookkeeping) ---------------------------
     def draw_params(self):
+        """pi and theta of eq. 4 for the sweep's clusters: the K current ones,
+        plus the K+1 candidate (a cluster without cells) when it is open.
+        Returns log pi with one entry per cluster and a last entry for the
+        unused remainder (-inf when the candidate takes pi_{K+1})."""
         nsub, Ssub = self.stats()
         logpi = draw_pi(nsub.sum(axis=1), self.alpha, self.seed, self.chain_id, self.t)
+        if self.open_new_cluster and self.K < self.kmax:
+            Ssub = np.concatenate([Ssub, np.zeros((1, 2, self.D), dtype=Ssub.dtype)])
+            logpi = np.concatenate([logpi, [-np.inf]])
         logtheta = draw_theta(Ssub, self.beta, self.seed, self.chain_id, self.t)
         return logpi, logtheta
 
     def assign_and_update(self, logpi, logtheta):
-        nsub, _ = self.stats()
+        Ks = logpi.size - 1                 # the sweep's clusters (K, or K + 1 when open)
+        nsub = np.zeros((Ks, 2), dtype=np.int64)
+        nsub[:self.K] = self.stats()[0]
         labels, sub, logq, _ = assign(self.X, logpi, logtheta, self.labels, self.sub, nsub,
                                       self.seed, self.chain_id, self.t)
-        sumlogq = np.bincount(labels, weights=logq, minlength=self.K)
-        labels, self.K, (sumlogq,) = compact(labels, self.K, sumlogq)
+        sumlogq = np.bincount(labels, weights=logq, minlength=Ks)
+        labels, self.K, (sumlogq,) = compact(labels, Ks, sumlogq)
         self.labels, self.sub, self.sumlogq = labels, sub, sumlogq
         self._reset_empty_subclusters()
         self.t += 1

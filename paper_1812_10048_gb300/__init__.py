@@ -305,13 +305,14 @@ class Sampler:
 
     def __init__(self, indptr, indices, data, N, D, alpha, beta, *, kmax=256, seed=42,
                  chain_id=0, engine=ENGINE_AUTO, split_q=True, hastings="integrated",
-                 stream=None):
+                 open_new_cluster=False, stream=None):
         self.N, self.D, self.kmax = int(N), int(D), int(kmax)
         if hastings not in ("integrated", "instantiated"):
             raise ValueError("hastings must be 'integrated' or 'instantiated'")
         opts = dpmm_default_opts(kmax=kmax, seed=seed, chain_id=chain_id, engine=engine,
                                  split_q=int(bool(split_q)),
-                                 hastings=int(hastings == "instantiated"))
+                                 hastings=int(hastings == "instantiated"),
+                                 open_new_cluster=int(bool(open_new_cluster)))
         self.ctx = dpmm_init(indptr, indices, data, N, D, alpha, beta, opts, stream)
 
     def close(self):

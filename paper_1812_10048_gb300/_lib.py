@@ -29,7 +29,8 @@ class DpmmError(RuntimeError):
 class dpmm_opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_int32), ("engine", ctypes.c_int32), ("split_q", ctypes.c_int32),
                 ("chain_id", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("hastings", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("hastings", ctypes.c_int32), ("open_new_cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _P = ctypes.c_void_p

@@ -167,6 +167,7 @@ ChainArgs dpmm::chain_args(const Ctx& c) {
     a.lg_beta = std::lgamma(c.beta);
     a.split_q = c.opts.split_q;
     a.hastings = c.opts.hastings;
+    a.open_new = c.opts.open_new_cluster;
     a.st = make_stream(c.opts.seed, c.opts.chain_id);
     return a;
 }
@@ -237,6 +238,7 @@ int enqueue_compaction(Ctx& c) {
 
 int enqueue_sweep(Ctx& c) {
     MARK(0);
+    CK(launch_open_slot(c));
     CK(launch_draw_params(c));
     int rc = enqueue_labelling(c);
     if (rc) return rc;
@@ -322,6 +324,8 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         return fail(DPMM_EINVAL, "chain_id = %d outside [0, 2^24)", o.chain_id);
     if (o.hastings != 0 && o.hastings != 1)
         return fail(DPMM_EINVAL, "hastings = %d, need 0 or 1", o.hastings);
+    if (o.open_new_cluster != 0 && o.open_new_cluster != 1)
+        return fail(DPMM_EINVAL, "open_new_cluster = %d, need 0 or 1", o.open_new_cluster);
 
     std::vector<int32_t> hptr, hidx, hval;
     int rc;
@@ -793,6 +797,7 @@ int dpmm_set_state(dpmm_ctx* ctx, const int32_t* labels, const uint8_t* sub, int
     c.sc_host->t = (uint32_t)t;
     c.sc_host->m = (uint32_t)m;
     c.sc_host->inst_fresh = 0;   // no sweep's draws belong to the new state
+    c.sc_host->open_slot = 0;
     CK(cudaMemcpy(c.sc, c.sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice));
     if ((rc = recount_all(c))) return rc;
     CK(cudaStreamSynchronize(c.stream));
@@ -813,6 +818,7 @@ int dpmm_get_stats(dpmm_ctx* ctx, uint32_t* nsub, uint32_t* Ssub, double* sumlog
 
 int dpmm_draw_params(dpmm_ctx* ctx) {
     CHECK_CHAIN(ctx);
+    CK(launch_open_slot(ctx->c));
     CK(launch_draw_params(ctx->c));
     return DPMM_OK;
 }

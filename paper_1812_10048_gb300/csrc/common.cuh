@@ -77,6 +77,8 @@ struct DevScalars {
     uint32_t n_apply;     // plans applied so far (sweep compactions and moves)
     int32_t inst_fresh;   // the last plan was a sweep's compaction: the sweep's
                           // pi / theta draws (pre-compaction rows) serve eq. 18
+    int32_t open_slot;    // cluster K - 1 is the eq. 4 K+1 candidate appended for
+                          // this sweep (no cells yet; cleared by every plan)
 };
 
 // The dense-tile engine serves 1 <= K <= kTileMaxK.
@@ -342,6 +344,7 @@ struct ChainArgs {
     double alpha, beta, log_alpha, lg_beta;
     int32_t split_q;
     int32_t hastings;     // 1: instantiated eq. 18 split ratio
+    int32_t open_new;     // 1: each sweep offers the eq. 4 K+1 candidate
     Stream st;
 };
 
@@ -497,6 +500,7 @@ cudaError_t with_table(const Ctx& c, F launch) {
 // ---------------------------------------------------------------------------
 cudaError_t configure_launches(Ctx& c);
 cudaError_t launch_draw_params(Ctx& c);
+cudaError_t launch_open_slot(Ctx& c);
 cudaError_t launch_assign(Ctx& c);
 cudaError_t launch_recount(Ctx& c);
 cudaError_t launch_sweep_stats(Ctx& c);

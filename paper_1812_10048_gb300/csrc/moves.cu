@@ -464,6 +464,7 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
             sc->any_reinit = any_reset;
             sc->any_relabel = (total != K) || any_reset;
             sc->inst_fresh = 1;   // desc maps each survivor to its pre-compaction row
+            sc->open_slot = 0;
             finish_plan(sc, bump);
         }
         return;
@@ -510,6 +511,7 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
             sc->any_reinit = A > 0;
             sc->any_relabel = A > 0;
             sc->inst_fresh = 0;
+            sc->open_slot = 0;
             finish_plan(sc, bump);
         }
         return;
@@ -574,6 +576,7 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
         sc->any_reinit = 0;
         sc->any_relabel = total != K;
         sc->inst_fresh = 0;
+        sc->open_slot = 0;
         finish_plan(sc, bump);
     }
 }

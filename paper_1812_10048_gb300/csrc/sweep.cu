@@ -76,13 +76,41 @@ __global__ void k_select_engine(const __grid_constant__ Tab tab) {
     fill_noise(tab, (int64_t)gridDim.x, (int64_t)blockIdx.x);
 }
 
+// The K+1 candidate of eq. 4 (chains with open_new): appended as cluster K
+// with no cells, so that the sweep's draws give it theta and theta-bar from
+// the Dirichlet(beta) prior (its gene sums are zero) and the alpha weight
+// pi_{K+1}, and the labelling, statistics and compaction treat it as one more
+// cluster; the compaction removes it if no cell chose it.  Not appended at
+// K = kmax or while an earlier candidate awaits its compaction.
+template <class Tab>
+__global__ void k_open_slot(const __grid_constant__ Tab tab) {
+    for (int b = blockIdx.x; b < tab.n(); b += gridDim.x) {
+        const ChainArgs& ch = tab[b];
+        DevScalars* sc = ch.sc;
+        const int K = sc->K;
+        const bool add = ch.open_new && !sc->open_slot && K < ch.kmax;
+        __syncthreads();
+        if (!add) continue;
+        uint32_t* S = ch.Ssub + (size_t)(2 * K) * ch.D;
+        for (int i = threadIdx.x; i < 2 * ch.D; i += blockDim.x) S[i] = 0u;
+        if (threadIdx.x < 2) ch.nsub[2 * K + threadIdx.x] = 0u;
+        if (threadIdx.x == 0) {
+            ch.sumlogq[K] = 0.0;
+            sc->K = K + 1;
+            sc->open_slot = 1;
+        }
+    }
+}
+
 // Rows 0 .. 3K-1 are theta rows (row 3k + p: cluster k for p = 0, its
 // sub-cluster p - 1 otherwise); row 3K is the pi row.  log G is kept in the
 // block's cache (D <= kDrawCache; else in the output slot), then normalised
-// into the output (log theta = log G - logsumexp).
+// into the output (log theta = log G - logsumexp).  With an appended K+1
+// candidate (open = 1) the alpha entry of pi is the candidate's weight and
+// there is no remainder entry (log pi_K = -inf).
 constexpr int kDrawCache = 8192;
-__device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, uint32_t t, int row,
-                                         float* red, float* lgc) {
+__device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, int open, uint32_t t,
+                                         int row, float* red, float* lgc) {
     const int D = ch.D, kmax = ch.kmax;
     const float beta = (float)ch.beta, alpha = (float)ch.alpha;
     const Stream& st = ch.st;
@@ -116,19 +144,21 @@ __device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, uint32_t t,
     } else {
         const uint32_t* nsub = ch.nsub;
         float* logpi = ch.logpi;
+        const int Kc = K - open;   // clusters with cells; entry Kc takes alpha
         float mx = -CUDART_INF_F;
-        for (int k = threadIdx.x; k <= K; k += blockDim.x) {
-            const float a = k < K ? (float)(nsub[2 * k] + nsub[2 * k + 1]) : alpha;
+        for (int k = threadIdx.x; k <= Kc; k += blockDim.x) {
+            const float a = k < Kc ? (float)(nsub[2 * k] + nsub[2 * k + 1]) : alpha;
             const float lg = log_gamma_draw(st, TAG_PI, a, (uint32_t)k, t);
             logpi[k] = lg;
             mx = fmaxf(mx, lg);
         }
         mx = block_reduce_max(mx, red);
         float s = 0.0f;
-        for (int k = threadIdx.x; k <= K; k += blockDim.x) s += expf(logpi[k] - mx);
+        for (int k = threadIdx.x; k <= Kc; k += blockDim.x) s += expf(logpi[k] - mx);
         s = block_reduce_sum(s, red);
         const float lse = mx + logf(s);
-        for (int k = threadIdx.x; k <= K; k += blockDim.x) logpi[k] -= lse;
+        for (int k = threadIdx.x; k <= Kc; k += blockDim.x) logpi[k] -= lse;
+        if (open && threadIdx.x == 0) logpi[K] = -CUDART_INF_F;
     }
 }
 
@@ -144,6 +174,7 @@ k_draw_params(const __grid_constant__ Tab tab) {
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
         const int K = ch.sc->K;
+        const int open = ch.open_new ? ch.sc->open_slot : 0;
         const uint32_t t = ch.sc->t;
         const int rows = 3 * K + 1;
         int64_t first = base + (((int64_t)blockIdx.x - base) % gridDim.x + gridDim.x) % gridDim.x;
@@ -153,7 +184,7 @@ k_draw_params(const __grid_constant__ Tab tab) {
                 if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
                 clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
             }
-            draw_row(ch, K, t, row, red, lgc);
+            draw_row(ch, K, open, t, row, red, lgc);
             __syncthreads();
         }
         base += rows;
@@ -764,6 +795,15 @@ cudaError_t configure_launches(Ctx& c) {
 cudaError_t launch_draw_params(Ctx& c) {
     return with_table(c, [&](auto tab) {
         k_draw_params<<<2 * c.num_sms, kDrawThreads, 0, c.stream>>>(tab);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_open_slot(Ctx& c) {
+    if (!c.opts.open_new_cluster) return cudaSuccess;
+    return with_table(c, [&](auto tab) {
+        const int blocks = c.nchains < 2 * c.num_sms ? c.nchains : 2 * c.num_sms;
+        k_open_slot<<<blocks, 256, 0, c.stream>>>(tab);
         return cudaGetLastError();
     });
 }

@@ -230,3 +230,79 @@ def test_full_chain_matches_exact_partition_posterior():
         key = canonical(s.labels)
         counts[key] = counts.get(key, 0) + 1
     assert total_variation(counts, parts, post, n) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# eq. 4 with the K+1 candidate open
+# ---------------------------------------------------------------------------
+def _zero_rows(n, D):
+    return np.zeros(n + 1, dtype=np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64)
+
+
+def test_open_candidate_takes_pi_k_plus_1_on_cells_without_counts():
+    """A cell without counts has p(x | theta) = 1 under every theta, so its
+    label is drawn from (pi_1, .., pi_K, pi_{K+1}) alone: the fraction of cells
+    that open the new cluster is pi_{K+1}, the alpha entry of eq. 4."""
+    from oracle.sampler import draw_pi
+    n, D, K = 20000, 4, 2
+    s = Sampler(*_zero_rows(n, D), n, D, 3000.0, 0.5, seed=5, open_new_cluster=True)
+    s.set_state(np.arange(n) % K, np.zeros(n, np.int64), K, t=3)
+    logpi, logtheta = s.draw_params()
+    assert logpi.size == K + 2 and logpi[-1] == -np.inf and logtheta.shape == (3 * (K + 1), D)
+    ref = draw_pi(np.full(K, n / K), 3000.0, 5, 0, 3)
+    np.testing.assert_array_equal(logpi[:K + 1], ref)
+    s.assign_and_update(logpi, logtheta)
+    assert s.K == K + 1                       # survivors keep their order: the new one is last
+    counts = np.bincount(s.labels, minlength=K + 1)
+    p = np.exp(logpi[:K + 1])
+    assert p[K] > 0.05
+    assert stats.chisquare(counts, p * n).pvalue > 1e-4
+
+
+def test_open_candidate_theta_is_drawn_from_the_prior():
+    """The candidate's theta and theta-bar rows are Dirichlet(lambda) draws
+    whatever the data: mean 1/D and variance (1/D)(1 - 1/D)/(D lambda + 1)
+    per gene over many sweeps."""
+    n, D, lam = 6, 3, 0.7
+    x = np.array([[9, 0, 1], [7, 1, 0], [8, 0, 2], [0, 5, 5], [1, 6, 4], [0, 4, 6]])
+    indptr = np.arange(n + 1) * D
+    s = Sampler(indptr, np.tile(np.arange(D), n), x.ravel(), n, D, 1.0, lam, seed=2,
+                open_new_cluster=True)
+    draws = []
+    for t in range(1500):
+        s.t = t
+        _, logtheta = s.draw_params()
+        draws.append(np.exp(logtheta[3:6]))     # K = 1: rows 3..5 are the candidate's
+    th = np.concatenate(draws)                  # (3 * 1500, D) independent prior draws
+    m = th.shape[0]
+    var = (1 / D) * (1 - 1 / D) / (D * lam + 1)
+    assert np.all(np.abs(th.mean(0) - 1 / D) < 5 * math.sqrt(var / m))
+    assert np.all(np.abs(th.var(0) / var - 1) < 0.15)
+
+
+def test_open_chain_with_vanishing_alpha_is_the_restricted_chain(tiny_dataset):
+    """pi_{K+1} -> 0 closes the candidate: every other draw keeps its Philox
+    counter, so the open chain is the restricted chain exactly."""
+    ds = tiny_dataset
+    a = Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1e-30, 0.5, seed=4)
+    b = Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1e-30, 0.5, seed=4,
+                open_new_cluster=True)
+    for s in (a, b):
+        s.set_state(ds.labels, np.arange(ds.N) % 2, int(ds.labels.max()) + 1)
+    for _ in range(4):
+        a.sweep(); b.sweep()
+        a.split_merge(0); b.split_merge(0)
+    assert a.K == b.K
+    np.testing.assert_array_equal(a.labels, b.labels)
+    np.testing.assert_array_equal(a.sub, b.sub)
+    np.testing.assert_array_equal(a.sumlogq, b.sumlogq)
+
+
+def test_open_candidate_absent_at_capacity():
+    n, D = 8, 3
+    x = np.ones((n, D), dtype=np.int64)
+    s = Sampler(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D, 1.0, 0.5,
+                kmax=2, open_new_cluster=True)
+    s.set_state(np.arange(n) % 2, np.zeros(n, np.int64), 2)
+    logpi, logtheta = s.draw_params()
+    assert logpi.size == 3 and logtheta.shape[0] == 6
