@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="main", choices=["main", "batched", "large", "grad", "eb"],
+    ap.add_argument("--config", default="main", choices=["main", "batched", "large", "grad", "eb", "study", "local"],
                     help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
                          "as one batch; large: 1.3M x 2k")
     ap.add_argument("--workers", type=int, default=0,
@@ -625,12 +625,182 @@ def run_eb(args):
     return 0
 
 
+def _matched_labels(labels, truth):
+    """Each found cluster replaced by the generating cluster it overlaps most."""
+    K, T = int(labels.max()) + 1, int(truth.max()) + 1
+    ct = np.bincount(labels.astype(np.int64) * T + truth, minlength=K * T).reshape(K, T)
+    return ct.argmax(axis=1)[labels]
+
+
+def run_study(args):
+    """Synthetic analogues of the paper's studies, run as batches of chains.
+    (1) Hyper-parameter and repeats, 68k x 1k workload: for alpha in {0.1, 0.2,
+    0.5, 1} and each sampler form (restricted labels, and eq. 4's open K+1
+    candidate), 50 independent chains (chain_id 0..49) run `--steps` steps
+    (default 300); K, ARI against the generating labels, and per-cell
+    stability (the fraction of the 50 repeats that put the cell in its modal
+    cluster, clusters matched to the generating cluster they overlap most).
+    (2) Library size: S, M, L-shaped sets of three close cell types at 300 ..
+    30,000 counts per cell, 5 chains per dataset; ARI per depth.  (3) Local
+    Gibbs iterations per sweep L = 1, 2, 4 on S at 10,000 and M at 30,000
+    counts per cell: mean ARI of 20 chains along the chain and the time per
+    step."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    from oracle.ari import adjusted_rand_index
+    ds = synth.pbmc68k()
+    R = 50
+    steps = args.steps if "--steps" in sys.argv else 300
+    alphas = (0.1, 0.2, 0.5, 1.0)
+    data = [(ds.indptr, ds.indices, ds.data, ds.N)] * R
+    out = {}
+    t_all = time.time()
+    for form, open_new in (("restricted", False), ("open_candidate", True)):
+        for a in alphas:
+            bs = P.BatchSampler(data, ds.D, a, 0.1, kmax=64, seed=42, engine=P.ENGINE_AUTO,
+                                open_new_cluster=open_new)
+            st = torch.cuda.ExternalStream(bs.stream)
+            t0 = time.time()
+            bs.step(steps)
+            st.synchronize()
+            run_s = time.time() - t0
+            labs = [bs.chain(b).labels()[0] for b in range(R)]
+            bs.close()
+            Ks = [int(l.max()) + 1 for l in labs]
+            aris = [float(adjusted_rand_index(l, ds.labels)) for l in labs]
+            m = np.stack([_matched_labels(l, ds.labels) for l in labs])      # R x N
+            T = int(ds.labels.max()) + 1
+            cnt = np.zeros((T, ds.N), dtype=np.int32)
+            for r in range(R):
+                cnt[m[r], np.arange(ds.N)] += 1
+            stab = cnt.max(axis=0) / R
+            out.setdefault(form, {})[str(a)] = {
+                "K_median": float(np.median(Ks)), "K_range": [min(Ks), max(Ks)],
+                "ari_mean": round(float(np.mean(aris)), 4), "ari_min": round(float(min(aris)), 4),
+                "stability_mean": round(float(stab.mean()), 4),
+                "cells_stable_ge_0.9": round(float(np.mean(stab >= 0.9)), 4),
+                "batch_run_s": round(run_s, 3)}
+            print(form, a, out[form][str(a)], file=sys.stderr, flush=True)
+    # library size (the sequencing-depth study): three set shapes, five depths,
+    # close cell-type profiles; 5 chains per dataset, all depths in one batch
+    depth_out = {}
+    depths = (300, 1000, 3000, 5000, 10000, 30000)
+    Rd = 5
+    for name, (N, D) in (("S", (1200, 1000)), ("M", (3000, 3000)), ("L", (6000, 5000))):
+        dss = [synth.similar_types(N, D, 3, d) for d in depths]
+        data_d = [(x.indptr, x.indices, x.data, x.N) for x in dss for _ in range(Rd)]
+        bs = P.BatchSampler(data_d, D, 1.0, 0.1, kmax=64, seed=7, engine=P.ENGINE_AUTO)
+        st = torch.cuda.ExternalStream(bs.stream)
+        t0 = time.time()
+        bs.step(steps)
+        st.synchronize()
+        run_s = time.time() - t0
+        res = {}
+        for i, d in enumerate(depths):
+            labs = [bs.chain(i * Rd + r).labels()[0] for r in range(Rd)]
+            aris = [float(adjusted_rand_index(l, dss[i].labels)) for l in labs]
+            res[str(d)] = {"ari_mean": round(float(np.mean(aris)), 4),
+                           "ari_min": round(float(min(aris)), 4),
+                           "K": [int(l.max()) + 1 for l in labs]}
+        bs.close()
+        depth_out[name] = {"N": N, "D": D, "batch_run_s": round(run_s, 3), "by_depth": res}
+        print("depth", name, depth_out[name], file=sys.stderr, flush=True)
+    # local Gibbs iterations per sweep: S at 10,000 and M at 30,000 counts per
+    # cell (depths where the types get split), 20 chains per setting, mean
+    # ARI along the chain and the device time per chain step
+    local_out = {}
+    checkpoints = (2, 5, 10, 25, 50, 100)
+    for name, (N, D, depth) in (("S@10000", (1200, 1000, 10000)),
+                                ("M@30000", (3000, 3000, 30000))):
+        dsm = synth.similar_types(N, D, 3, depth)
+        for L in (1, 2, 4):
+            data_l = [(dsm.indptr, dsm.indices, dsm.data, dsm.N)] * 20
+            bs = P.BatchSampler(data_l, dsm.D, 1.0, 0.1, kmax=64, seed=5,
+                                engine=P.ENGINE_AUTO, local_iters=L)
+            st = torch.cuda.ExternalStream(bs.stream)
+            bs.step(1)                       # graph capture outside the timing
+            st.synchronize()
+            done, trace, dev_s = 1, {}, 0.0
+            for c in checkpoints:
+                t0 = time.time()
+                bs.step(c - done)
+                st.synchronize()
+                dev_s += time.time() - t0
+                done = c
+                aris = [float(adjusted_rand_index(bs.chain(b).labels()[0], dsm.labels))
+                        for b in range(20)]
+                trace[str(c)] = round(float(np.mean(aris)), 4)
+            bs.close()
+            local_out.setdefault(name, {})[str(L)] = {
+                "ari_mean_at_step": trace,
+                "ms_per_chain_step": round(1e3 * dev_s / (20 * (done - 1)), 4)}
+            print("local", name, L, local_out[name][str(L)], file=sys.stderr, flush=True)
+    # the cost of a local iteration on one large chain: 68k x 1k, device time
+    # per step (CUDA events over 200 graph steps after 20 warm-up steps)
+    single = {}
+    for L in (1, 2, 4):
+        sg = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                       engine=P.ENGINE_AUTO, local_iters=L)
+        stg = torch.cuda.ExternalStream(sg.stream)
+        ms = time_steps(lambda: sg.step(1), stg, 200, 20, torch)
+        single[str(L)] = round(float(ms.mean()), 5)
+        sg.close()
+    local_out["pbmc68k_single_chain_ms_per_step"] = single
+    print("local single chain", single, file=sys.stderr, flush=True)
+    line = {"metric": "alpha / repeat, library-size and local-Gibbs studies (synthetic)",
+            "value": None, "unit": None, "n_gpus": 1, "steps": steps, "repeats": R,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "pbmc68k-synthetic (alpha study); similar_types S 1200x1000, "
+                                   "M 3000x3000, L 6000x5000, 3 types, sigma 0.05 (depth and "
+                                   "local-iteration studies)", "beta": 0.1, "kmax": 64,
+                       "alphas": list(alphas), "depths": list(depths)},
+            "alpha_study": out, "depth_study": depth_out, "local_iters_study": local_out,
+            "wall_s": round(time.time() - t_all, 1)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_local(args):
+    """One local Gibbs iteration (dpmm_local_gibbs, labels held: eq. 19
+    theta-bar draws, eq. 8 sub-labels, recount) on the 68k x 1k chain after
+    20 steps, device time per iteration with CUDA events over `--steps`
+    iterations (default 100) after `--warmup` (>= 3) untimed ones."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    ds = synth.pbmc68k()
+    s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                  engine=P.ENGINE_AUTO, local_iters=2)
+    s.step(20)
+    s.sync()
+    st = torch.cuda.ExternalStream(s.stream)
+    n = args.steps if "--steps" in sys.argv else 100
+    ms = time_steps(lambda: P.dpmm_local_gibbs(s.ctx, 1), st, n, max(3, args.warmup), torch)
+    line = {"metric": "local Gibbs iteration at 68k cells x 1k genes", "value": round(float(ms.mean()) * 1e3, 2),
+            "unit": "us per iteration", "n_gpus": 1, "steps": n, "warmup": max(3, args.warmup),
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "pbmc68k-synthetic", "N": int(ds.N), "D": int(ds.D),
+                       "K": int(s.labels_K())}}
+    s.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.config == "grad":
         return run_grad(args)
     if args.config == "eb":
         return run_eb(args)
+    if args.config == "study":
+        return run_study(args)
+    if args.config == "local":
+        return run_local(args)
     if args.config == "batched":
         return run_batched(args)
     if args.config == "large":

@@ -60,7 +60,12 @@ typedef struct dpmm_opts {
                           prior, weight pi_{K+1}); the cells that choose it
                           form one new cluster.  0 (default): labels range over
                           the K existing clusters (new clusters come from splits) */
-    int32_t reserved[6];
+    int32_t local_iters;  /* local Gibbs iterations per sweep, 1 (default, the
+                          paper's choice) .. 16; 0 reads as 1.  Iterations after
+                          the first hold the labels, redraw theta-bar (eq. 19)
+                          and then every sub-label (eq. 8); the split proposal
+                          term is the last iteration's.  Needs hastings = 0. */
+    int32_t reserved[5];
 } dpmm_opts;
 
 /* Fill *opts with the defaults above. */
@@ -216,6 +221,16 @@ int dpmm_get_stats(dpmm_ctx* ctx, uint32_t* nsub, uint32_t* Ssub, double* sumlog
  * candidate's theta rows are prior draws, log pi_{K-1} is its alpha weight and
  * log pi_K = -inf.  Follow it with dpmm_assign. */
 int dpmm_draw_params(dpmm_ctx* ctx);
+
+/* Local Gibbs iteration j (1 <= j < 16) of Section 2.3 on the current state,
+ * as a sweep with opts.local_iters > j runs it after its compaction: labels
+ * held, theta-bar of every sub-cluster drawn from eq. 19 given the current
+ * sub-labels (Philox tag 16 + 2 (j - 1)), then every sub-label from eq. 8
+ * (tag 17 + 2 (j - 1)), both with step t - 1 (the sweep just made); n-bar,
+ * S-bar and sum log q recounted.  DPMM_EINVAL if j is out of range, t = 0 or
+ * the chain was built with opts.local_iters = 1.
+ * Asynchronous after the check of t (which synchronises). */
+int dpmm_local_gibbs(dpmm_ctx* ctx, int32_t j);
 
 /* Second half: labels and sub-labels from the current parameters (eq. 4 third
  * line, eq. 8), statistics, empty-cluster removal; advances t. */

@@ -34,6 +34,13 @@ with key = (seed & 0xffffffff, seed >> 32).  Tags:
                       reset of sweep t (c1 = t), 2 after a split in call m
                       (c1 = m)
 
+Local Gibbs iterations j = 1, 2, .. after sweep t (Section 2.3; more than one
+only when asked for) use their own tags, c1 = t:
+
+    16 + 2 (j - 1)  eq. 19 sub-cluster Gamma draws: c0 = row * D + u with
+                    row = 3k + 1 + r, c3 = attempt
+    17 + 2 (j - 1)  eq. 8 sub-label Gumbels: c0 = i, c3 = 0, words 0, 1
+
 A 32-bit word w maps to the uniform ``((w >> 9) + 0.5) * 2**-23``, which lies
 in (0, 1) and is exactly representable in both FP32 and FP64, so both sides
 see the same uniform.
@@ -55,6 +62,20 @@ TAG_MOVE = 4
 TAG_PAIR = 5
 TAG_MERGE = 6
 TAG_SUBINIT = 7
+
+LOCAL_TAG0 = 16
+LOCAL_MAX_ITERS = 16
+
+
+def tag_local_theta(j):
+    """Tag of the sub-cluster Gamma draws of local Gibbs iteration j >= 1."""
+    return LOCAL_TAG0 + 2 * (j - 1)
+
+
+def tag_local_sub(j):
+    """Tag of the sub-label Gumbels of local Gibbs iteration j >= 1."""
+    return LOCAL_TAG0 + 2 * (j - 1) + 1
+
 
 SUBINIT_INIT = 0
 SUBINIT_RESET = 1

@@ -33,8 +33,11 @@ CUDA side):
 * after the label update, empty clusters are removed with survivors keeping
   their relative order; a cluster with two or more cells and an empty
   sub-cluster redraws its cells' sub-labels as fair coins;
+* ``local_iters`` local Gibbs iterations per sweep (default 1, the paper's
+  choice): iterations after the first hold the labels, redraw theta-bar
+  (eq. 19) and then the sub-labels (eq. 8), with their own Philox tags;
 * the split proposal probability q(S*|S) is the product of the eq. 8
-  probabilities of the latest sweep (a random re-initialisation contributes
+  probabilities of the latest local Gibbs iteration (a random re-initialisation contributes
   (1/2)^n; sub-labels set by a merge contribute 1);
 * a split moves sub-cluster 1 of cluster k to the new index K + j (j-th
   accepted split, ascending k); a merge of a < b keeps index a, with the
@@ -125,15 +128,26 @@ def assign(X, logpi, logtheta, labels_old, sub_old, nsub, seed, chain_id, t):
                     np.asarray(Xf @ logtheta[2::3].T)[cells, labels]], axis=1)
     stays = labels == labels_old
     w = np.stack([nsub[labels, 0] - (stays & (sub_old == 0)),
-                  nsub[labels, 1] - (stays & (sub_old == 1))], axis=1).astype(np.float64)
+                  nsub[labels, 1] - (stays & (sub_old == 1))], axis=1)
+    sub, logq = eq8_draw(w, lik, seed, chain_id, philox.TAG_SUBLABEL, t)
+    return labels.astype(np.int64), sub, logq, scores
+
+
+def eq8_draw(w, lik, seed, chain_id, tag, t):
+    """Eq. 8 by Gumbel-max: weights w[i, r] = n-bar_{r, not i} (both zero: taken
+    as equal), likelihood factors lik[i, r] = log p(x_i | theta-bar_r), Gumbels
+    from words 0, 1 of counter (i, t, tag, 0).  Returns the sub-labels and
+    log q_i, the log eq. 8 probability of each drawn sub-label."""
+    w = np.asarray(w, dtype=np.float64).copy()
     w[w.sum(axis=1) == 0] = 1.0
     with np.errstate(divide="ignore"):
         tr = np.log(w) + lik
-    words = philox.stream_words(seed, chain_id, philox.TAG_SUBLABEL, cells, t, 0)
+    cells = np.arange(w.shape[0])
+    words = philox.stream_words(seed, chain_id, tag, cells, t, 0)
     h = philox.uniform_to_gumbel(philox.word_to_uniform(words[:, :2]))
     sub = (tr[:, 1] + h[:, 1] > tr[:, 0] + h[:, 0]).astype(np.int64)
     logq = tr[cells, sub] - np.logaddexp(tr[:, 0], tr[:, 1])
-    return labels.astype(np.int64), sub, logq, scores
+    return sub, logq
 
 
 def compact(labels, K, *per_cluster):
@@ -154,13 +168,16 @@ class Sampler:
     """FP64 Para-DPMM chain over a cells x genes CSR count matrix."""
 
     def __init__(self, indptr, indices, data, N, D, alpha, beta, seed=42, chain_id=0,
-                 kmax=256, split_q=True, open_new_cluster=False):
+                 kmax=256, split_q=True, open_new_cluster=False, local_iters=1):
         self.X = csr_matrix(indptr, indices, data, N, D)
         self.N, self.D = int(N), int(D)
         self.alpha, self.beta = float(alpha), float(beta)
         self.seed, self.chain_id, self.kmax = int(seed), int(chain_id), int(kmax)
         self.split_q = bool(split_q)
         self.open_new_cluster = bool(open_new_cluster)
+        if not 1 <= int(local_iters) <= philox.LOCAL_MAX_ITERS:
+            raise ValueError("local_iters must be in [1, %d]" % philox.LOCAL_MAX_ITERS)
+        self.local_iters = int(local_iters)
         self.K = 1
         self.labels = np.zeros(self.N, dtype=np.int64)
         self.sub = fair_coin_sublabels(np.arange(self.N), self.seed, self.chain_id, 0,
@@ -215,6 +232,32 @@ class Sampler:
     def sweep(self):
         logpi, logtheta = self.draw_params()
         self.assign_and_update(logpi, logtheta)
+        for j in range(1, self.local_iters):
+            self.local_gibbs(j)
+
+    def local_gibbs(self, j):
+        """Local Gibbs iteration j >= 1 after the sweep just made (Section 2.3):
+        labels held, theta-bar of every sub-cluster drawn from eq. 19 given the
+        current sub-labels, then every sub-label drawn from eq. 8.  A
+        sub-cluster that empties stays empty until the next sweep's
+        compaction; the split proposal term becomes this iteration's log q."""
+        t = self.t - 1                           # the sweep's own counter
+        nsub, Ssub = self.stats()
+        K, D = self.K, self.D
+        conc = (self.beta + Ssub).reshape(2 * K, D)           # row 2k + r
+        rows = (3 * np.arange(K)[:, None] + 1 + np.arange(2)[None, :]).ravel()
+        index = (rows[:, None] * D + np.arange(D)[None, :]).ravel()
+        logg = log_gamma_draw(conc.ravel(), self.seed, self.chain_id, philox.tag_local_theta(j),
+                              index, t).reshape(2 * K, D)
+        logtb = logg - logsumexp(logg, axis=1, keepdims=True)
+        Xf = self.X.astype(np.float64)
+        cells = np.arange(self.N)
+        lik = np.stack([np.asarray(Xf @ logtb[0::2].T)[cells, self.labels],
+                        np.asarray(Xf @ logtb[1::2].T)[cells, self.labels]], axis=1)
+        w = nsub[self.labels] - np.stack([self.sub == 0, self.sub == 1], axis=1)
+        self.sub, logq = eq8_draw(w, lik, self.seed, self.chain_id, philox.tag_local_sub(j), t)
+        self.sumlogq = np.bincount(self.labels, weights=logq, minlength=K)
+        return logtb
 
     def _reset_empty_subclusters(self):
         nsub, _ = self.stats()

@@ -20,7 +20,7 @@ __all__ = [
     "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_set_hyper",
     "dpmm_eb_step", "empirical_bayes", "dpmm_init_batch",
     "dpmm_chain", "BatchSampler", "dpmm_get_state",
-    "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_assign", "dpmm_get_params",
+    "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_local_gibbs", "dpmm_assign", "dpmm_get_params",
     "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_tile_scores", "dpmm_debug_moves", "dpmm_logml_create",
     "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_logml_grad_noalloc",
     "dpmm_debug_philox",
@@ -200,6 +200,10 @@ def dpmm_draw_params(ctx):
     check(lib().dpmm_draw_params(ctx))
 
 
+def dpmm_local_gibbs(ctx, j):
+    check(lib().dpmm_local_gibbs(ctx, int(j)))
+
+
 def dpmm_assign(ctx):
     check(lib().dpmm_assign(ctx))
 
@@ -305,14 +309,15 @@ class Sampler:
 
     def __init__(self, indptr, indices, data, N, D, alpha, beta, *, kmax=256, seed=42,
                  chain_id=0, engine=ENGINE_AUTO, split_q=True, hastings="integrated",
-                 open_new_cluster=False, stream=None):
+                 open_new_cluster=False, local_iters=1, stream=None):
         self.N, self.D, self.kmax = int(N), int(D), int(kmax)
         if hastings not in ("integrated", "instantiated"):
             raise ValueError("hastings must be 'integrated' or 'instantiated'")
         opts = dpmm_default_opts(kmax=kmax, seed=seed, chain_id=chain_id, engine=engine,
                                  split_q=int(bool(split_q)),
                                  hastings=int(hastings == "instantiated"),
-                                 open_new_cluster=int(bool(open_new_cluster)))
+                                 open_new_cluster=int(bool(open_new_cluster)),
+                                 local_iters=int(local_iters))
         self.ctx = dpmm_init(indptr, indices, data, N, D, alpha, beta, opts, stream)
 
     def close(self):
@@ -387,15 +392,21 @@ class BatchSampler:
     one launch per kernel over all chains, one CUDA graph per step."""
 
     def __init__(self, datasets, D, alpha=1.0, beta=0.5, *, kmax=256, seed=42, chain_id=0,
-                 engine=ENGINE_AUTO, split_q=True, stream=None):
+                 engine=ENGINE_AUTO, split_q=True, hastings="integrated",
+                 open_new_cluster=False, local_iters=1, stream=None):
         """datasets: list of (indptr, indices, data, N); alpha / beta scalars or lists."""
         B = len(datasets)
         self.B, self.D, self.kmax = B, int(D), int(kmax)
         self.Ns = [int(d[3]) for d in datasets]
         al = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (B,))
         be = np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,))
+        if hastings not in ("integrated", "instantiated"):
+            raise ValueError("hastings must be 'integrated' or 'instantiated'")
         opts = dpmm_default_opts(kmax=kmax, seed=seed, chain_id=chain_id, engine=engine,
-                                 split_q=int(bool(split_q)))
+                                 split_q=int(bool(split_q)),
+                                 hastings=int(hastings == "instantiated"),
+                                 open_new_cluster=int(bool(open_new_cluster)),
+                                 local_iters=int(local_iters))
         self.ctx = dpmm_init_batch([d[:3] for d in datasets], self.Ns, D, al, be, opts, stream)
 
     def close(self):

@@ -30,7 +30,7 @@ class dpmm_opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_int32), ("engine", ctypes.c_int32), ("split_q", ctypes.c_int32),
                 ("chain_id", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("hastings", ctypes.c_int32), ("open_new_cluster", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("local_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _P = ctypes.c_void_p
@@ -62,6 +62,7 @@ SIGNATURES = {
     "dpmm_set_state": (ctypes.c_int, [_P, _P, _P, _I32, _I64, _I64, _P]),
     "dpmm_get_stats": (ctypes.c_int, [_P, _P, _P, _P]),
     "dpmm_draw_params": (ctypes.c_int, [_P]),
+    "dpmm_local_gibbs": (ctypes.c_int, [_P, ctypes.c_int32]),
     "dpmm_assign": (ctypes.c_int, [_P]),
     "dpmm_get_params": (ctypes.c_int, [_P, _P, _P]),
     "dpmm_set_params": (ctypes.c_int, [_P, _P, _P]),

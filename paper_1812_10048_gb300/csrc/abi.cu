@@ -244,6 +244,7 @@ int enqueue_sweep(Ctx& c) {
     if (rc) return rc;
     rc = enqueue_compaction(c);
     if (rc) return rc;
+    for (int32_t j = 1; j < c.opts.local_iters; ++j) CK(launch_local_iteration(c, j));
     MARK(4);
     return DPMM_OK;
 }
@@ -302,6 +303,7 @@ void dpmm_default_opts(dpmm_opts* o) {
     o->split_q = 1;
     o->chain_id = 0;
     o->seed = 42;
+    o->local_iters = 1;
 }
 
 int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, const int32_t* data,
@@ -326,6 +328,13 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         return fail(DPMM_EINVAL, "hastings = %d, need 0 or 1", o.hastings);
     if (o.open_new_cluster != 0 && o.open_new_cluster != 1)
         return fail(DPMM_EINVAL, "open_new_cluster = %d, need 0 or 1", o.open_new_cluster);
+    if (o.local_iters == 0) o.local_iters = 1;
+    if (o.local_iters < 1 || o.local_iters > kLocalMaxIters)
+        return fail(DPMM_EINVAL, "local_iters = %d outside [1, %d]", o.local_iters,
+                    kLocalMaxIters);
+    if (o.hastings && o.local_iters > 1)
+        return fail(DPMM_EINVAL, "hastings = 1 takes the sweep's own theta-bar: local_iters "
+                                 "must be 1");
 
     std::vector<int32_t> hptr, hidx, hval;
     int rc;
@@ -344,6 +353,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     c.N = N;
     c.D = D;
     c.nnz = nnz;
+    c.mean_row = nnz / N;
     c.alpha = alpha;
     c.beta = beta;
     c.opts = o;
@@ -584,7 +594,10 @@ int dpmm_init_batch(dpmm_ctx** out, int32_t B, const int32_t* const* indptr,
     c.tile_enabled = true;
     c.tile_any = false;
     std::vector<ChainArgs> tab;
+    int64_t sum_nnz = 0, sum_n = 0;
     for (dpmm_ctx* m : h->members) {
+        sum_nnz += m->c.nnz;
+        sum_n += m->c.N;
         c.tile_enabled = c.tile_enabled && m->c.tile_enabled;
         c.tile_any = c.tile_any || m->c.tile_enabled;
         if (m->c.tile_enabled) c.tile_C = m->c.tile_C;
@@ -600,6 +613,7 @@ int dpmm_init_batch(dpmm_ctx** out, int32_t B, const int32_t* const* indptr,
         return bail(fail(e == cudaErrorMemoryAllocation ? DPMM_ENOMEM : DPMM_ECUDA,
                          "batch table: %s", cudaGetErrorString(e)));
     c.nchains = B;
+    c.mean_row = sum_n > 0 ? sum_nnz / sum_n : 0;
     *out = h;
     return DPMM_OK;
 }
@@ -820,6 +834,20 @@ int dpmm_draw_params(dpmm_ctx* ctx) {
     CHECK_CHAIN(ctx);
     CK(launch_open_slot(ctx->c));
     CK(launch_draw_params(ctx->c));
+    return DPMM_OK;
+}
+
+int dpmm_local_gibbs(dpmm_ctx* ctx, int32_t j) {
+    CHECK_CHAIN(ctx);
+    Ctx& c = ctx->c;
+    if (j < 1 || j >= kLocalMaxIters)
+        return fail(DPMM_EINVAL, "local iteration %d outside [1, %d)", j, kLocalMaxIters);
+    if (c.opts.local_iters < 2)
+        return fail(DPMM_EINVAL, "local iterations need a chain built with opts.local_iters > 1");
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    if (c.sc_host->t == 0) return fail(DPMM_EINVAL, "local iteration before any sweep (t = 0)");
+    CK(launch_local_iteration(c, j));
     return DPMM_OK;
 }
 

@@ -27,6 +27,12 @@ enum Tag : uint32_t {
     TAG_MERGE = 6,     // merge accept (a, m, ., 0)
     TAG_SUBINIT = 7,   // fair-coin sub-labels (cell, step, ., kind)
 };
+// Local Gibbs iteration j >= 1 after sweep t (Section 2.3): sub-cluster Gamma
+// draws under tag kLocalTag0 + 2 (j - 1) (counter (3k + 1 + r) D + u, t, ., attempt),
+// sub-label Gumbels under tag kLocalTag0 + 2 (j - 1) + 1 (counter (cell, t, ., 0)).
+constexpr uint32_t kLocalTag0 = 16;
+constexpr int32_t kLocalMaxIters = 16;
+
 enum SubInit : uint32_t { SUBINIT_INIT = 0, SUBINIT_RESET = 1, SUBINIT_SPLIT = 2 };
 
 constexpr int kMaxGammaAttempts = 64;
@@ -103,6 +109,7 @@ struct Ctx {
     int64_t N = 0;
     int32_t D = 0;
     int64_t nnz = 0;
+    int64_t mean_row = 0;         // nnz / N over the chains this context walks
     double alpha = 1.0, beta = 1.0;
     dpmm_opts opts{};
     int32_t kmax = 0;
@@ -501,6 +508,7 @@ cudaError_t with_table(const Ctx& c, F launch) {
 cudaError_t configure_launches(Ctx& c);
 cudaError_t launch_draw_params(Ctx& c);
 cudaError_t launch_open_slot(Ctx& c);
+cudaError_t launch_local_iteration(Ctx& c, int32_t j);
 cudaError_t launch_assign(Ctx& c);
 cudaError_t launch_recount(Ctx& c);
 cudaError_t launch_sweep_stats(Ctx& c);

@@ -109,8 +109,8 @@ __global__ void k_open_slot(const __grid_constant__ Tab tab) {
 // candidate (open = 1) the alpha entry of pi is the candidate's weight and
 // there is no remainder entry (log pi_K = -inf).
 constexpr int kDrawCache = 8192;
-__device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, int open, uint32_t t,
-                                         int row, float* red, float* lgc) {
+__device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, int open, uint32_t theta_tag,
+                                         uint32_t t, int row, float* red, float* lgc) {
     const int D = ch.D, kmax = ch.kmax;
     const float beta = (float)ch.beta, alpha = (float)ch.alpha;
     const Stream& st = ch.st;
@@ -127,7 +127,7 @@ __device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, int open, u
         float mx = -CUDART_INF_F;
         for (int u = threadIdx.x; u < D; u += blockDim.x) {
             const uint32_t S = p == 0 ? S0[u] + S1[u] : (p == 1 ? S0[u] : S1[u]);
-            const float lg = log_gamma_draw(st, TAG_THETA, beta + (float)S,
+            const float lg = log_gamma_draw(st, theta_tag, beta + (float)S,
                                             (uint32_t)row * (uint32_t)D + (uint32_t)u, t);
             if (cached) lgc[u] = lg;
             else *slot(u) = lg;
@@ -184,7 +184,7 @@ k_draw_params(const __grid_constant__ Tab tab) {
                 if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
                 clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
             }
-            draw_row(ch, K, open, t, row, red, lgc);
+            draw_row(ch, K, open, TAG_THETA, t, row, red, lgc);
             __syncthreads();
         }
         base += rows;
@@ -194,6 +194,34 @@ k_draw_params(const __grid_constant__ Tab tab) {
     const int64_t free0 = base < gridDim.x ? base : 0;
     if ((int64_t)blockIdx.x >= free0)
         fill_noise(tab, (int64_t)gridDim.x - free0, (int64_t)blockIdx.x - free0);
+}
+
+// Local Gibbs iteration j >= 1 after a sweep (Section 2.3), first half: the
+// 2K sub-cluster rows theta-bar from eq. 19 given the current sub-labels,
+// under the iteration's tag and the sweep's own counter t - 1 (the
+// compaction has advanced t).  The block of a chain's first row clears its
+// n-bar / sum log q accumulators.
+template <class Tab>
+__global__ void __launch_bounds__(kDrawThreads)
+k_draw_local(const __grid_constant__ Tab tab, int32_t j) {
+    __shared__ float red[32];
+    __shared__ float lgc[kDrawCache];
+    const uint32_t tag = kLocalTag0 + 2u * (uint32_t)(j - 1);
+    int64_t base = 0;
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        const int K = ch.sc->K;
+        const uint32_t t = ch.sc->t - 1u;
+        const int rows = 2 * K;
+        int64_t first = base + (((int64_t)blockIdx.x - base) % gridDim.x + gridDim.x) % gridDim.x;
+        for (int64_t id = first; id < base + rows; id += gridDim.x) {
+            const int i = (int)(id - base);
+            if (i == 0) clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
+            draw_row(ch, K, 0, tag, t, 3 * (i >> 1) + 1 + (i & 1), red, lgc);
+            __syncthreads();
+        }
+        base += rows;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -240,10 +268,30 @@ __device__ __forceinline__ float2 sub_scores(const Csr& csr, int64_t beg, int64_
 }
 
 
-// eq. 8 draw for cell `cell` of cluster c given its two likelihood factors;
-// returns the sub-label and writes log q_i.
+// eq. 8 draw for cell `cell` of cluster c given its two likelihood factors,
+// Gumbels from counter (cell, step, tag, 0); returns the sub-label and writes
+// log q_i.
+__device__ __forceinline__ uint32_t draw_sublabel_n(const Stream& st, int64_t cell, int c,
+                                                    uint32_t old, uint32_t n0, uint32_t n1,
+                                                    float2 lik, uint32_t tag, uint32_t step,
+                                                    float* logq) {
+    const bool stays = state_label(old) == (uint32_t)c;
+    const uint32_t so = state_sub(old);
+    float w0 = (float)n0 - (float)(stays && so == 0);
+    float w1 = (float)n1 - (float)(stays && so == 1);
+    if (w0 + w1 == 0.0f) w0 = w1 = 1.0f;
+    const float l0 = w0 > 0.0f ? logf(w0) + lik.x : -CUDART_INF_F;
+    const float l1 = w1 > 0.0f ? logf(w1) + lik.y : -CUDART_INF_F;
+    const uint4 h = st.words(tag, (uint32_t)cell, step, 0u);
+    const uint32_t s = (l1 + gumbel(h.y) > l0 + gumbel(h.x)) ? 1u : 0u;
+    const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
+    *logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
+    return s;
+}
+
 __device__ __forceinline__ uint32_t draw_sublabel(const ChainArgs& a, int64_t cell, int c,
-                                                  float2 lik, uint32_t t, float* logq) {
+                                                  float2 lik, uint32_t tag, uint32_t step,
+                                                  float* logq) {
     const uint32_t old = a.state[cell];
     const bool stays = state_label(old) == (uint32_t)c;
     const uint32_t so = state_sub(old);
@@ -252,11 +300,164 @@ __device__ __forceinline__ uint32_t draw_sublabel(const ChainArgs& a, int64_t ce
     if (w0 + w1 == 0.0f) w0 = w1 = 1.0f;
     const float l0 = w0 > 0.0f ? logf(w0) + lik.x : -CUDART_INF_F;
     const float l1 = w1 > 0.0f ? logf(w1) + lik.y : -CUDART_INF_F;
-    const uint4 h = a.st.words(TAG_SUBLABEL, (uint32_t)cell, t, 0u);
+    const uint4 h = a.st.words(tag, (uint32_t)cell, step, 0u);
     const uint32_t s = (l1 + gumbel(h.y) > l0 + gumbel(h.x)) ? 1u : 0u;
     const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
     *logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
     return s;
+}
+
+// Local Gibbs iteration, second half: labels held, every cell's sub-label
+// drawn from eq. 8 under the new theta-bar (weights n-bar_{r, not i} from the
+// current counts).  LANES lanes per cell (chosen from the mean row length),
+// each lane with eight row entries in flight; the cells of all chains form one index range split into contiguous block ranges (a batch of
+// small chains keeps every warp busy), and the next cell's state and row
+// bounds are loaded before the current cell's contraction.  log q_i is summed
+// per (chain, cluster) in the block (FP64; the first kLocalSlots chains of
+// the block's range), then into the accumulator.  A chain with the blocked
+// copy also has its main S-bar rows cleared here (the tile statistics kernel
+// recounts into them; nothing reads them after the theta-bar draw).
+constexpr int kLocalThreads = 256;
+constexpr int kLocalSlots = 2;
+constexpr int kLocalInFlight = 8;
+
+template <int LANES>
+__device__ __forceinline__ float2 sub_scores_group(const Csr& csr, int64_t beg, int64_t end,
+                                                   const float2* __restrict__ Ls2, int kmax,
+                                                   int c, int sl, unsigned gmask) {
+    float t0 = 0.0f, t1 = 0.0f;
+    for (int64_t e0 = beg + sl; e0 < end; e0 += kLocalInFlight * LANES) {
+        int32_t u[kLocalInFlight], x[kLocalInFlight];
+#pragma unroll
+        for (int q = 0; q < kLocalInFlight; ++q) {
+            u[q] = 0;
+            x[q] = 0;
+            if (e0 + LANES * q < end) csr.get(e0 + LANES * q, u[q], x[q]);
+        }
+        float2 l[kLocalInFlight];
+#pragma unroll
+        for (int q = 0; q < kLocalInFlight; ++q)
+            l[q] = x[q] ? __ldg(Ls2 + (size_t)u[q] * kmax + c) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < kLocalInFlight; ++q) {
+            t0 = fmaf((float)x[q], l[q].x, t0);
+            t1 = fmaf((float)x[q], l[q].y, t1);
+        }
+    }
+#pragma unroll
+    for (int o = LANES / 2; o; o >>= 1) {
+        t0 += __shfl_xor_sync(gmask, t0, o);
+        t1 += __shfl_xor_sync(gmask, t1, o);
+    }
+    return make_float2(t0, t1);
+}
+
+template <int LANES, class Tab>
+__global__ void __launch_bounds__(kLocalThreads)
+k_local_sub(const __grid_constant__ Tab tab, int32_t j) {
+    __shared__ double bsq[kLocalSlots][kMaxKmax];
+    const uint32_t tag = kLocalTag0 + 2u * (uint32_t)(j - 1) + 1u;
+    const int lane = threadIdx.x & 31;
+    const int sl = lane % LANES;                                // lane within the cell group
+    const int grp = (int)(threadIdx.x / LANES);
+    const int ngrp = (int)(blockDim.x / LANES);
+    const unsigned gmask =
+        (LANES == 32 ? 0xFFFFFFFFu : ((1u << LANES) - 1u)) << (lane - sl);
+    int64_t total = 0;
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        if (ch.tile_enabled)
+            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                 i < (int64_t)2 * ch.sc->K * ch.D; i += (int64_t)gridDim.x * blockDim.x)
+                ch.Ssub[i] = 0u;
+        total += ch.N;
+    }
+    for (int i = threadIdx.x; i < kLocalSlots * kMaxKmax; i += blockDim.x) (&bsq[0][0])[i] = 0.0;
+    __syncthreads();
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t g0 = min(total, (int64_t)blockIdx.x * per), g1 = min(total, g0 + per);
+    int b0 = 0;
+    int64_t base0 = 0;
+    while (b0 + 1 < tab.n() && g0 >= base0 + tab[b0].N) base0 += tab[b0++].N;
+    int b = b0;
+    int64_t base = base0;
+    int64_t g = g0 + grp;
+    uint32_t st = 0u;
+    int64_t beg = 0, end = 0;
+    if (g < g1) {
+        while (g >= base + tab[b].N) base += tab[b++].N;
+        const ChainArgs& ch = tab[b];
+        st = ch.state[g - base];
+        beg = ch.csr.indptr[g - base];
+        end = ch.csr.indptr[g - base + 1];
+    }
+    while (g < g1) {
+        const ChainArgs& ch = tab[b];
+        const int64_t cell = g - base;
+        const int c = (int)state_label(st);
+        uint32_t n0 = 0u, n1 = 0u;
+        if (sl == 0) {
+            n0 = ch.nsub[2 * c];
+            n1 = ch.nsub[2 * c + 1];
+        }
+        const int64_t gn = g + ngrp;
+        int bn = b;
+        int64_t basen = base, begn = 0, endn = 0;
+        uint32_t stn = 0u;
+        if (gn < g1) {
+            while (gn >= basen + tab[bn].N) basen += tab[bn++].N;
+            const ChainArgs& cn = tab[bn];
+            stn = cn.state[gn - basen];
+            begn = cn.csr.indptr[gn - basen];
+            endn = cn.csr.indptr[gn - basen + 1];
+        }
+        const float2 lik = sub_scores_group<LANES>(
+            ch.csr, beg, end, reinterpret_cast<const float2*>(ch.Ls), ch.kmax, c, sl, gmask);
+        if (sl == 0) {
+            float logq;
+            const uint32_t s = draw_sublabel_n(ch.st, cell, c, st, n0, n1, lik, tag,
+                                               ch.sc->t - 1u, &logq);
+            ch.state[cell] = pack_state((uint32_t)c, s);
+            if (logq != 0.0f) {
+                if (b - b0 < kLocalSlots) atomicAdd(&bsq[b - b0][c], (double)logq);
+                else atomicAdd(&ch.acc_sumlogq[c], (double)logq);
+            }
+        }
+        g = gn;
+        b = bn;
+        base = basen;
+        st = stn;
+        beg = begn;
+        end = endn;
+    }
+    __syncthreads();
+    for (int q = 0; q < kLocalSlots && b0 + q < tab.n(); ++q) {
+        const ChainArgs& ch = tab[b0 + q];
+        const int K = ch.sc->K;
+        for (int k = threadIdx.x; k < K; k += blockDim.x)
+            if (bsq[q][k] != 0.0) atomicAdd(&ch.acc_sumlogq[k], bsq[q][k]);
+    }
+}
+
+// Local Gibbs iteration, bookkeeping: the recounted n-bar, S-bar and sum log q
+// become the main statistics (a CSR-counted S-bar moves out of its cleared
+// accumulator; the tile statistics kernel counted into the main rows).
+// Sub-clusters that emptied stay empty until the next sweep's compaction.
+template <class Tab>
+__global__ void k_local_commit(const __grid_constant__ Tab tab) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int b = 0; b < tab.n(); ++b) {
+        const ChainArgs& ch = tab[b];
+        const int K = ch.sc->K;
+        if (!ch.tile_enabled)
+            for (int64_t i = tid; i < (int64_t)2 * K * ch.D; i += stride) {
+                ch.Ssub[i] = ch.acc_Ssub[i];
+                ch.acc_Ssub[i] = 0u;
+            }
+        for (int64_t i = tid; i < 2 * K; i += stride) ch.nsub[i] = ch.acc_nsub[i];
+        for (int64_t i = tid; i < K; i += stride) ch.sumlogq[i] = ch.acc_sumlogq[i];
+    }
 }
 
 // Warp argmax of (value, index): largest value, lowest index on ties.
@@ -303,7 +504,7 @@ __device__ __forceinline__ void assign_cells(const ChainArgs& a, const float* L,
         const float2 lik = sub_scores(a.csr, beg, end, reinterpret_cast<const float2*>(a.Ls), a.kmax, c, lane);
         if (lane == 0) {
             float logq;
-            const uint32_t s = draw_sublabel(a, cell, c, lik, t, &logq);
+            const uint32_t s = draw_sublabel(a, cell, c, lik, TAG_SUBLABEL, t, &logq);
             a.state[cell] = pack_state((uint32_t)c, s);
             atomicAdd(&blk_sumlogq[c], (double)logq);
         }
@@ -678,7 +879,13 @@ k_stats(const __grid_constant__ Tab tab, int64_t priv_cap, int sweep) {
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
         const DevScalars* sc = ch.sc;
-        if (sweep) {
+        if (sweep == 2) {
+            // a local Gibbs iteration: the cells of a chain without the
+            // blocked copy into the accumulators
+            if (ch.tile_enabled) continue;
+            stats_cells(ch.csr, ch.state, nullptr, ch.acc_nsub, ch.acc_Ssub, ch.N, ch.D, sc->K,
+                        spriv, priv_cap);
+        } else if (sweep) {
             // a sweep's statistics into the accumulators, unless the CSR label
             // kernel added them (a chain with the blocked copy is counted by
             // the tile statistics kernel)
@@ -804,6 +1011,35 @@ cudaError_t launch_open_slot(Ctx& c) {
     return with_table(c, [&](auto tab) {
         const int blocks = c.nchains < 2 * c.num_sms ? c.nchains : 2 * c.num_sms;
         k_open_slot<<<blocks, 256, 0, c.stream>>>(tab);
+        return cudaGetLastError();
+    });
+}
+
+// One local Gibbs iteration j >= 1 (after the sweep's compaction).
+cudaError_t launch_local_iteration(Ctx& c, int32_t j) {
+    cudaError_t e = with_table(c, [&](auto tab) {
+        k_draw_local<<<2 * c.num_sms, kDrawThreads, 0, c.stream>>>(tab, j);
+        // lanes per cell: the power of two nearest below mean row length /
+        // kLocalInFlight, within [4, 32] (one or two passes per lane)
+        const int64_t mean = c.mean_row;
+        const dim3 grid(4 * c.num_sms);
+        if (mean < 8 * kLocalInFlight)
+            k_local_sub<4><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+        else if (mean < 16 * kLocalInFlight)
+            k_local_sub<8><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+        else if (mean < 32 * kLocalInFlight)
+            k_local_sub<16><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+        else
+            k_local_sub<32><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+        if (!c.tile_enabled)
+            k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
+                tab, (int64_t)(c.stats_smem / sizeof(uint32_t)), 2);
+        return cudaGetLastError();
+    });
+    if (e == cudaSuccess && (c.tile_enabled || c.tile_any)) e = launch_tile_stats(c);
+    if (e != cudaSuccess) return e;
+    return with_table(c, [&](auto tab) {
+        k_local_commit<<<2 * c.num_sms, 256, 0, c.stream>>>(tab);
         return cudaGetLastError();
     });
 }

@@ -51,14 +51,16 @@ def cluster_sizes(N, K, zipf=None):
 
 def make_dataset(N, D, K_true, *, gamma=0.1, lib_mu=np.log(1500.0), lib_sigma=0.5,
                  zipf=None, deep_frac=0.0, deep_range=(5000.0, 60000.0), seed=1001,
-                 chunk=16384):
+                 chunk=16384, profiles=None):
+    """profiles (K_true x D, rows summing to 1) replaces the Dir(gamma) profile draw."""
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = cluster_sizes(N, K_true, zipf)
     labels = np.repeat(np.arange(K_true), sizes)
     labels = labels[rng.permutation(N)]
-    g = rng.gamma(gamma, size=(K_true, D))
-    g[g.sum(axis=1) == 0, 0] = 1.0
-    profiles = g / g.sum(axis=1, keepdims=True)
+    if profiles is None:
+        g = rng.gamma(gamma, size=(K_true, D))
+        g[g.sum(axis=1) == 0, 0] = 1.0
+        profiles = g / g.sum(axis=1, keepdims=True)
     lib = np.maximum(1, np.rint(rng.lognormal(lib_mu, lib_sigma, size=N))).astype(np.int64)
     if deep_frac > 0:
         deep = rng.random(N) < deep_frac
@@ -171,6 +173,21 @@ def batched(B=64, seed=2000, workers=1):
         with _pool(workers) as ex:
             return list(ex.map(_one_dataset, kws))
     return [_one_dataset(kw) for kw in kws]
+
+
+def similar_types(N, D, K_true, depth, *, sigma=0.05, base_gamma=0.3, seed=1006):
+    """Cell types with close expression profiles, for the library-size study: a
+    shared base profile ~ Dir(base_gamma) times exp(sigma z_ku) with z standard
+    normal per type and gene, renormalised; library sizes LogNormal(log depth,
+    0.3).  The profiles do not depend on depth (same seed), so depth alone sets
+    how separable the types are."""
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    base = rng.gamma(base_gamma, size=D)
+    base /= base.sum()
+    prof = base[None, :] * np.exp(sigma * rng.standard_normal((K_true, D)))
+    prof /= prof.sum(axis=1, keepdims=True)
+    return make_dataset(N, D, K_true, lib_mu=np.log(depth), lib_sigma=0.3, seed=seed,
+                        profiles=prof)
 
 
 def grad_workload(seed=1005):

@@ -306,3 +306,77 @@ def test_open_candidate_absent_at_capacity():
     s.set_state(np.arange(n) % 2, np.zeros(n, np.int64), 2)
     logpi, logtheta = s.draw_params()
     assert logpi.size == 3 and logtheta.shape[0] == 6
+
+
+# ---------------------------------------------------------------------------
+# local Gibbs iterations after the first (Section 2.3)
+# ---------------------------------------------------------------------------
+def test_local_gibbs_draws_theta_bar_from_eq19_and_sublabels_from_eq8():
+    """Labels held, fixed sub-label pattern on 6 identical cells (3 in each
+    sub-cluster, so the n-bar_{r, not i} correction matters): over many
+    steps, theta-bar has the Dirichlet(beta + S-bar_r) posterior mean, each
+    cell's new sub-label is 1 with the eq. 8 probability computed from the
+    returned theta-bar, and log q_i is the log of that probability."""
+    n, D, lam = 6, 3, 0.5
+    row = np.array([2, 1, 3])
+    X = np.tile(row, (n, 1))
+    s = Sampler(np.arange(n + 1) * D, np.tile(np.arange(D), n), X.ravel(), n, D, 1.0, lam,
+                seed=9, local_iters=2)
+    sub0 = np.array([0, 0, 0, 1, 1, 1])
+    S = np.array([3 * row, 3 * row], dtype=float)             # S-bar_0, S-bar_1
+    post_mean = (lam + S) / (lam * D + S.sum(axis=1, keepdims=True))
+    steps = 3000
+    th_sum = np.zeros((2, D))
+    z_num, z_den = np.zeros(2), np.zeros(2)
+    for t in range(steps):
+        s.set_state(np.zeros(n, np.int64), sub0, 1, t=t + 1)
+        logtb = s.local_gibbs(1)
+        th_sum += np.exp(logtb)
+        lik = row @ logtb.T                                   # (2,)
+        for so in (0, 1):
+            w = np.array([3.0, 3.0]) - (np.arange(2) == so)
+            p1 = w[1] * np.exp(lik[1]) / (w[0] * np.exp(lik[0]) + w[1] * np.exp(lik[1]))
+            cells = np.nonzero(sub0 == so)[0]
+            got = s.sub[cells]
+            z_num[so] += np.sum(got - p1)
+            z_den[so] += len(cells) * p1 * (1 - p1)
+    assert np.all(np.abs(z_num / np.sqrt(z_den)) < 5)
+    var = post_mean * (1 - post_mean) / (lam * D + S.sum(axis=1, keepdims=True) + 1)
+    assert np.all(np.abs(th_sum / steps - post_mean) < 5 * np.sqrt(var / steps))
+
+
+def test_local_gibbs_log_q_is_the_log_eq8_probability():
+    n, D = 7, 4
+    rng = np.random.default_rng(3)
+    X = rng.integers(0, 5, size=(n, D))
+    s = Sampler(np.arange(n + 1) * D, np.tile(np.arange(D), n), X.ravel(), n, D, 1.0, 0.6,
+                seed=4, local_iters=3)
+    labels = np.array([0, 0, 0, 1, 1, 1, 1])
+    sub = np.array([0, 1, 1, 0, 0, 1, 0])
+    s.set_state(labels, sub, 2, t=5)
+    nsub, _ = s.stats()
+    logtb = s.local_gibbs(2)
+    lik = np.stack([(X @ logtb[0::2].T)[np.arange(n), labels],
+                    (X @ logtb[1::2].T)[np.arange(n), labels]], axis=1)
+    w = nsub[labels] - np.stack([sub == 0, sub == 1], axis=1)
+    with np.errstate(divide="ignore"):
+        lw = np.log(w.astype(float)) + lik
+    ref = lw[np.arange(n), s.sub] - np.logaddexp(lw[:, 0], lw[:, 1])
+    np.testing.assert_allclose(s.sumlogq, np.bincount(labels, weights=ref), rtol=1e-12)
+    np.testing.assert_array_equal(s.labels, labels)
+    assert s.K == 2
+
+
+def test_one_local_iteration_is_the_default_chain(tiny_dataset):
+    ds = tiny_dataset
+    a = Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, seed=8)
+    b = Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, seed=8, local_iters=1)
+    c = Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, seed=8, local_iters=3)
+    for s in (a, b, c):
+        s.sweep()
+    np.testing.assert_array_equal(a.labels, b.labels)
+    np.testing.assert_array_equal(a.sub, b.sub)
+    np.testing.assert_array_equal(a.labels, c.labels)     # later iterations hold the labels
+    assert not np.allclose(a.sumlogq, c.sumlogq)          # with new theta-bar draws
+    with pytest.raises(ValueError):
+        Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, local_iters=17)
