@@ -265,6 +265,20 @@ int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out
  */
 int dpmm_debug_tile_scores(dpmm_ctx* ctx, float* out);
 
+/*
+ * The dense-tile engine's blocked copy of the counts, as dpmm_init built it on
+ * the device: *T tiles of 128 cells, *C chunks of 64 genes, *n entries.
+ * Entries are grouped by segment s = tile * C + chunk and, inside a segment,
+ * by quarter q (32-cell row block), in CSR order inside a (segment, quarter)
+ * bucket; entry = row-in-tile << 22 | gene-in-chunk << 16 | count; every
+ * segment starts on a multiple of 4 entries (padding entries are 0).
+ * tile_ptr int32[4 T C + 1]: tile_ptr[4 s + q] = first entry of bucket
+ * (s, q), tile_ptr[4 T C] = *n.  With tile_ptr or tile_ent NULL only the sizes
+ * are returned.  DPMM_ESTATE if the chain has no blocked copy.  Synchronises.
+ */
+int dpmm_debug_tile_layout(dpmm_ctx* ctx, int32_t* T, int32_t* C, int64_t* n, int32_t* tile_ptr,
+                           uint32_t* tile_ent);
+
 /* Split/merge diagnostics of the last dpmm_split_merge call: chain (1 split,
  * 2 merge), and log H per cluster (split; NaN where no proposal) or per pair
  * (merge, with the pair's cluster indices a < b in pair_ab int32[2][n]).

@@ -20,7 +20,7 @@ __all__ = [
     "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_set_hyper",
     "dpmm_eb_step", "empirical_bayes", "dpmm_init_batch",
     "dpmm_chain", "BatchSampler", "dpmm_get_state",
-    "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_local_gibbs", "dpmm_assign", "dpmm_get_params",
+    "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_local_gibbs", "dpmm_assign", "dpmm_debug_tile_layout", "dpmm_get_params",
     "dpmm_set_params", "dpmm_debug_scores", "dpmm_debug_tile_scores", "dpmm_debug_moves", "dpmm_logml_create",
     "dpmm_logml_free", "dpmm_logml_forward", "dpmm_logml_backward", "dpmm_logml_grad_noalloc",
     "dpmm_debug_philox",
@@ -226,6 +226,18 @@ def dpmm_debug_scores(ctx, cells, K):
     out = np.empty((cells.size, 3 * K), dtype=np.float32)
     check(lib().dpmm_debug_scores(ctx, ptr(cells), int(cells.size), ptr(out)))
     return out
+
+
+def dpmm_debug_tile_layout(ctx):
+    """(T, C, tile_ptr int32[4 T C + 1], tile_ent uint32[n]) of the blocked copy."""
+    T, C, n = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    check(lib().dpmm_debug_tile_layout(ctx, ctypes.byref(T), ctypes.byref(C), ctypes.byref(n),
+                                       None, None))
+    tptr = np.empty(4 * T.value * C.value + 1, dtype=np.int32)
+    tent = np.empty(max(1, n.value), dtype=np.uint32)
+    check(lib().dpmm_debug_tile_layout(ctx, ctypes.byref(T), ctypes.byref(C), ctypes.byref(n),
+                                       ptr(tptr), ptr(tent)))
+    return T.value, C.value, tptr, tent[:n.value]
 
 
 def dpmm_debug_tile_scores(ctx, N, K):

@@ -62,6 +62,7 @@ SIGNATURES = {
     "dpmm_set_state": (ctypes.c_int, [_P, _P, _P, _I32, _I64, _I64, _P]),
     "dpmm_get_stats": (ctypes.c_int, [_P, _P, _P, _P]),
     "dpmm_draw_params": (ctypes.c_int, [_P]),
+    "dpmm_debug_tile_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "dpmm_local_gibbs": (ctypes.c_int, [_P, ctypes.c_int32]),
     "dpmm_assign": (ctypes.c_int, [_P]),
     "dpmm_get_params": (ctypes.c_int, [_P, _P, _P]),

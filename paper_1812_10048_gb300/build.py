@@ -10,7 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdpmm.so")
-SOURCES = ["abi.cu", "sweep.cu", "moves.cu", "logml.cu", "logml_noalloc.cu", "tile.cu"]
+SOURCES = ["abi.cu", "sweep.cu", "moves.cu", "logml.cu", "logml_noalloc.cu", "tile.cu",
+           "layout.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -3,6 +3,7 @@
 #include <curand_kernel.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -336,31 +337,37 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         return fail(DPMM_EINVAL, "hastings = 1 takes the sweep's own theta-bar: local_iters "
                                  "must be 1");
 
-    std::vector<int32_t> hptr, hidx, hval;
-    int rc;
-    if ((rc = fetch(hptr, indptr, (size_t)N + 1))) return rc;
-    const int64_t nnz = hptr[N];
-    if (nnz < 0) return fail(DPMM_EINVAL, "indptr[N] = %lld", (long long)nnz);
-    if (nnz > 0 && (!indices || !data)) return fail(DPMM_EINVAL, "indices/data are null");
-    if ((rc = fetch(hidx, indices, (size_t)nnz))) return rc;
-    if ((rc = fetch(hval, data, (size_t)nnz))) return rc;
-    int32_t max_count = 0;
-    if ((rc = check_csr(hptr, hidx, hval, N, D, &max_count))) return rc;
-
     dpmm_ctx* h = new (std::nothrow) dpmm_ctx();
     if (!h) return fail(DPMM_ENOMEM, "host allocation failed");
     Ctx& c = h->c;
     c.N = N;
     c.D = D;
-    c.nnz = nnz;
-    c.mean_row = nnz / N;
     c.alpha = alpha;
     c.beta = beta;
     c.opts = o;
     c.kmax = o.kmax;
-    c.packed = D <= 65536 && max_count <= 65535;
 
+    // scratch of the device-side CSR preparation (freed on every exit; the
+    // unpacked storage adopts the staging columns and counts)
+    int32_t* d_idx = nullptr;
+    int32_t* d_val = nullptr;
+    unsigned long long* d_colsum = nullptr;
+    CsrCheck* d_chk = nullptr;
+    int32_t* d_qcount = nullptr;
+    long long* d_scan = nullptr;
+    auto free_scratch = [&]() {
+        void* ps[] = {d_idx, d_val, d_colsum, d_chk, d_qcount, d_scan};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+        d_idx = d_val = nullptr;
+        d_colsum = nullptr;
+        d_chk = nullptr;
+        d_qcount = nullptr;
+        d_scan = nullptr;
+    };
     auto bail = [&](int code) {
+        if (c.stream) cudaStreamSynchronize(c.stream);
+        free_scratch();
         free_ctx(c);
         delete h;
         return code;
@@ -381,13 +388,62 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
         CKI(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
         c.own_stream = true;
     }
-    const size_t K2 = 2 * (size_t)c.kmax;
+
+    // ---- the CSR on the device: one copy of each array, then validation ----
     CKI(dalloc(&c.indptr, (size_t)N + 1));
+    CKI(cudaMemcpyAsync(c.indptr, indptr, sizeof(int32_t) * (N + 1), cudaMemcpyDefault, c.stream));
+    int32_t ends[2] = {0, 0};
+    CKI(cudaMemcpyAsync(&ends[0], c.indptr, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    CKI(cudaMemcpyAsync(&ends[1], c.indptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    CKI(cudaStreamSynchronize(c.stream));
+    if (ends[0] != 0) return bail(fail(DPMM_EINVAL, "indptr[0] = %d, expected 0", ends[0]));
+    const int64_t nnz = ends[1];
+    if (nnz < 0) return bail(fail(DPMM_EINVAL, "indptr[N] = %lld", (long long)nnz));
+    if (nnz > 0 && (!indices || !data)) return bail(fail(DPMM_EINVAL, "indices/data are null"));
+    c.nnz = nnz;
+    c.mean_row = nnz / N;
+    CKI(dalloc(&d_idx, (size_t)nnz));
+    CKI(dalloc(&d_val, (size_t)nnz));
+    if (nnz > 0) {
+        CKI(cudaMemcpyAsync(d_idx, indices, sizeof(int32_t) * nnz, cudaMemcpyDefault, c.stream));
+        CKI(cudaMemcpyAsync(d_val, data, sizeof(int32_t) * nnz, cudaMemcpyDefault, c.stream));
+    }
+    CKI(dalloc(&d_colsum, (size_t)D));
+    CKI(dalloc(&d_chk, 1));
+    CKI(cudaMemsetAsync(d_colsum, 0, sizeof(unsigned long long) * D, c.stream));
+    CsrCheck chk = {LLONG_MAX, LLONG_MAX, 0, INT_MAX};
+    CKI(cudaMemcpyAsync(d_chk, &chk, sizeof(CsrCheck), cudaMemcpyHostToDevice, c.stream));
+    CKI(launch_check_csr(c.indptr, d_idx, d_val, N, nnz, D, d_colsum, d_chk, c.num_sms,
+                         c.stream));
+    CKI(cudaMemcpyAsync(&chk, d_chk, sizeof(CsrCheck), cudaMemcpyDeviceToHost, c.stream));
+    CKI(cudaStreamSynchronize(c.stream));
+    if (chk.bad_row != LLONG_MAX)
+        return bail(fail(DPMM_EINVAL, "indptr decreases at row %lld", chk.bad_row));
+    if (chk.bad_entry != LLONG_MAX) {
+        int32_t u = 0, x = 0;
+        CKI(cudaMemcpy(&u, d_idx + chk.bad_entry, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        CKI(cudaMemcpy(&x, d_val + chk.bad_entry, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (u < 0 || u >= D)
+            return bail(fail(DPMM_EINVAL, "column index %d out of [0, %d) at entry %lld", u, D,
+                             chk.bad_entry));
+        return bail(fail(DPMM_EINVAL, "negative count %d at entry %lld", x, chk.bad_entry));
+    }
+    if (chk.overflow_gene != INT_MAX) {
+        unsigned long long sum = 0;
+        CKI(cudaMemcpy(&sum, d_colsum + chk.overflow_gene, sizeof(sum), cudaMemcpyDeviceToHost));
+        return bail(fail(DPMM_EOVERFLOW, "gene %d sums to %llu >= 2^32 (32-bit statistics)",
+                         chk.overflow_gene, sum));
+    }
+    c.packed = D <= 65536 && chk.max_count <= 65535;
+
+    const size_t K2 = 2 * (size_t)c.kmax;
     if (c.packed) {
         CKI(dalloc(&c.entries, (size_t)nnz));
+        CKI(launch_pack(d_idx, d_val, nnz, c.entries, c.num_sms, c.stream));
     } else {
-        CKI(dalloc(&c.cols, (size_t)nnz));
-        CKI(dalloc(&c.counts, (size_t)nnz));
+        c.cols = d_idx;
+        c.counts = d_val;
+        d_idx = d_val = nullptr;
     }
     CKI(dalloc(&c.state, (size_t)N));
     CKI(dalloc(&c.sc, 1));
@@ -412,79 +468,41 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     CKI(dalloc(&c.move_ticket, (size_t)c.kmax));
     CKI(cudaMemsetAsync(c.move_ticket, 0, sizeof(int32_t) * c.kmax, c.stream));
 
-    CKI(cudaMemcpyAsync(c.indptr, hptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice,
-                        c.stream));
-    if (c.packed) {
-        std::vector<uint32_t> packed((size_t)nnz);
-        for (int64_t e = 0; e < nnz; ++e)
-            packed[e] = ((uint32_t)hidx[e] << 16) | (uint32_t)hval[e];
-        CKI(cudaMemcpyAsync(c.entries, packed.data(), sizeof(uint32_t) * nnz,
-                            cudaMemcpyHostToDevice, c.stream));
-        CKI(cudaStreamSynchronize(c.stream));
-    } else if (nnz > 0) {
-        CKI(cudaMemcpyAsync(c.cols, hidx.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice,
-                            c.stream));
-        CKI(cudaMemcpyAsync(c.counts, hval.data(), sizeof(int32_t) * nnz,
-                            cudaMemcpyHostToDevice, c.stream));
-    }
     if (c.packed && o.engine != DPMM_ENGINE_CSR_FP32) {
-        // blocked copy for the dense-tile engine: entries grouped by segment
-        // (128-cell tile, 64-gene chunk) and, inside a segment, by quarter
-        // (32-cell row block) in cell order; every segment starts on a 16-byte
-        // boundary (padding entries have count 0) so that it moves as one
-        // bulk copy.  tile_ptr[4 s + q] = first entry of quarter q of segment
-        // s; tile_ptr[4 (s + 1)] = end of segment s, padding included.
+        // blocked copy for the dense-tile engine (layout.cu): entries grouped
+        // by segment (128-cell tile, 64-gene chunk) and, inside a segment, by
+        // quarter (32-cell row block) in cell order; every segment starts on a
+        // 16-byte boundary (padding entries have count 0) so that it moves as
+        // one bulk copy.  tile_ptr[4 s + q] = first entry of quarter q of
+        // segment s; tile_ptr[4 (s + 1)] = end of segment s, padding included.
         c.tile_T = (int32_t)((N + 127) / 128);
         c.tile_C = (D + 63) / 64;
-        const size_t TC = (size_t)c.tile_T * c.tile_C;
-        std::vector<int64_t> qcount(4 * TC, 0);
-        for (int64_t i = 0; i < N; ++i) {
-            const size_t tb = (size_t)(i >> 7) * c.tile_C;
-            const size_t q = (size_t)((i >> 5) & 3);
-            for (int32_t e = hptr[i]; e < hptr[i + 1]; ++e)
-                qcount[4 * (tb + (size_t)(hidx[e] >> 6)) + q]++;
-        }
-        std::vector<int64_t> qptr(4 * TC + 1, 0);
-        int64_t pos = 0, lmax = 4;
-        for (size_t sgm = 0; sgm < TC; ++sgm) {
-            const int64_t start = pos;
-            for (int q = 0; q < 4; ++q) {
-                qptr[4 * sgm + q] = pos;
-                pos += qcount[4 * sgm + q];
-            }
-            pos = (pos + 3) & ~(int64_t)3;
-            lmax = std::max(lmax, pos - start);
-        }
-        qptr[4 * TC] = pos;
-        if (pos > (int64_t)INT32_MAX)
+        const int64_t TC = (int64_t)c.tile_T * c.tile_C;
+        CKI(dalloc(&d_qcount, (size_t)(4 * TC)));
+        CKI(cudaMemsetAsync(d_qcount, 0, sizeof(int32_t) * 4 * TC, c.stream));
+        CKI(dalloc(&c.tile_ptr, (size_t)(4 * TC + 1)));
+        CKI(launch_tile_count(c.indptr, c.entries, N, c.tile_T, c.tile_C, d_qcount, c.num_sms,
+                              c.stream));
+        CKI(dalloc(&d_scan, 2));
+        CKI(launch_tile_scan(d_qcount, TC, c.tile_ptr, d_scan, c.stream));
+        long long scan[2] = {0, 0};
+        CKI(cudaMemcpyAsync(scan, d_scan, sizeof(scan), cudaMemcpyDeviceToHost, c.stream));
+        CKI(cudaStreamSynchronize(c.stream));
+        if (scan[0] > (long long)INT32_MAX)
             return bail(fail(DPMM_EOVERFLOW, "the dense-tile copy needs %lld entries (> 2^31 - 1)",
-                             (long long)pos));
-        std::vector<int32_t> tptr(4 * TC + 1);
-        for (size_t j = 0; j <= 4 * TC; ++j) tptr[j] = (int32_t)qptr[j];
-        std::vector<int64_t> cur(qptr.begin(), qptr.end() - 1);
-        std::vector<uint32_t> tent((size_t)pos, 0u);
-        for (int64_t i = 0; i < N; ++i) {
-            const size_t tb = (size_t)(i >> 7) * c.tile_C;
-            const size_t q = (size_t)((i >> 5) & 3);
-            const uint32_t r = (uint32_t)(i & 127);
-            for (int32_t e = hptr[i]; e < hptr[i + 1]; ++e)
-                tent[cur[4 * (tb + (size_t)(hidx[e] >> 6)) + q]++] =
-                    (r << 22) | ((uint32_t)(hidx[e] & 63) << 16) | (uint32_t)hval[e];
-        }
-        c.tile_Lslot = (int32_t)lmax;
-        CKI(dalloc(&c.tile_ent, (size_t)pos));
-        CKI(dalloc(&c.tile_ptr, 4 * TC + 1));
+                             scan[0]));
+        c.tile_Lslot = (int32_t)scan[1];
+        CKI(dalloc(&c.tile_ent, (size_t)scan[0]));
+        CKI(cudaMemsetAsync(c.tile_ent, 0, sizeof(uint32_t) * std::max<long long>(1, scan[0]),
+                            c.stream));
+        CKI(launch_tile_scatter(c.indptr, c.entries, N, c.tile_T, c.tile_C, c.tile_ptr,
+                                c.tile_ent, c.num_sms, c.stream));
         CKI(dalloc(&c.tile_B, tile_b_bytes(c.tile_C)));
         CKI(dalloc(&c.noise, (size_t)(kTileMaxK + 2) * (size_t)N));
-
-        CKI(cudaMemcpyAsync(c.tile_ptr, tptr.data(), sizeof(int32_t) * (4 * TC + 1),
-                            cudaMemcpyHostToDevice, c.stream));
-        if (pos)
-            CKI(cudaMemcpyAsync(c.tile_ent, tent.data(), sizeof(uint32_t) * (size_t)pos,
-                                cudaMemcpyHostToDevice, c.stream));
-        CKI(cudaStreamSynchronize(c.stream));
         c.tile_enabled = true;
     }
+    CKI(cudaStreamSynchronize(c.stream));
+    free_scratch();
     CKI(cudaMemsetAsync(c.acc_nsub, 0, sizeof(uint32_t) * K2, c.stream));
     CKI(cudaMemsetAsync(c.acc_Ssub, 0, sizeof(uint32_t) * K2 * D, c.stream));
     CKI(cudaMemsetAsync(c.acc_sumlogq, 0, sizeof(double) * c.kmax, c.stream));
@@ -925,6 +943,28 @@ int dpmm_debug_scores(dpmm_ctx* ctx, const int32_t* cells, int32_t n, float* out
     cudaFree(dcells);
     if (dout) cudaFree(dout);
     CK(e);
+    return DPMM_OK;
+}
+
+int dpmm_debug_tile_layout(dpmm_ctx* ctx, int32_t* T, int32_t* C, int64_t* n, int32_t* tile_ptr,
+                           uint32_t* tile_ent) {
+    CHECK_CHAIN(ctx);
+    Ctx& c = ctx->c;
+    if (!T || !C || !n) return fail(DPMM_EINVAL, "T/C/n are null");
+    if (!c.tile_enabled) return fail(DPMM_ESTATE, "the chain has no blocked copy");
+    const size_t nptr = 4 * (size_t)c.tile_T * c.tile_C + 1;
+    int32_t last = 0;
+    CK(cudaStreamSynchronize(c.stream));
+    CK(cudaMemcpy(&last, c.tile_ptr + nptr - 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    *T = c.tile_T;
+    *C = c.tile_C;
+    *n = last;
+    if (tile_ptr && tile_ent) {
+        CK(cudaMemcpy(tile_ptr, c.tile_ptr, sizeof(int32_t) * nptr, cudaMemcpyDefault));
+        if (last > 0)
+            CK(cudaMemcpy(tile_ent, c.tile_ent, sizeof(uint32_t) * (size_t)last,
+                          cudaMemcpyDefault));
+    }
     return DPMM_OK;
 }
 

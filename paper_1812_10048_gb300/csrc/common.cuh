@@ -502,11 +502,33 @@ cudaError_t with_table(const Ctx& c, F launch) {
     return launch(TabP{c.d_chains, c.nchains});
 }
 
+// Result of the device-side CSR validation (layout.cu): the first decreasing
+// row and the first bad entry (LLONG_MAX: none), the largest count, the first
+// gene whose counts sum to 2^32 or more (INT_MAX: none).
+struct CsrCheck {
+    long long bad_row;
+    long long bad_entry;
+    int32_t max_count;
+    int32_t overflow_gene;
+};
+
 // ---------------------------------------------------------------------------
-// Host-side launchers (sweep.cu, moves.cu).
+// Host-side launchers (sweep.cu, moves.cu, layout.cu).
 // ---------------------------------------------------------------------------
 cudaError_t configure_launches(Ctx& c);
 cudaError_t launch_draw_params(Ctx& c);
+cudaError_t launch_check_csr(const int32_t* indptr, const int32_t* idx, const int32_t* val,
+                             int64_t N, int64_t nnz, int32_t D, unsigned long long* colsum,
+                             CsrCheck* chk, int num_sms, cudaStream_t st);
+cudaError_t launch_pack(const int32_t* idx, const int32_t* val, int64_t nnz, uint32_t* entries,
+                        int num_sms, cudaStream_t st);
+cudaError_t launch_tile_count(const int32_t* indptr, const uint32_t* entries, int64_t N, int32_t T,
+                              int32_t C, int32_t* qcount, int num_sms, cudaStream_t st);
+cudaError_t launch_tile_scan(const int32_t* qcount, int64_t TC, int32_t* qptr, long long* out,
+                             cudaStream_t st);
+cudaError_t launch_tile_scatter(const int32_t* indptr, const uint32_t* entries, int64_t N,
+                                int32_t T, int32_t C, const int32_t* qptr, uint32_t* tent,
+                                int num_sms, cudaStream_t st);
 cudaError_t launch_open_slot(Ctx& c);
 cudaError_t launch_local_iteration(Ctx& c, int32_t j);
 cudaError_t launch_assign(Ctx& c);

@@ -144,3 +144,65 @@ def test_tile_engine_small_shapes(P):
     on, oS = sufficient_stats(csr_matrix(indptr, c, dense[r, c], N, D), labels, sub, K)
     np.testing.assert_array_equal(nsub, on)
     np.testing.assert_array_equal(Ssub, oS)
+
+
+# ---------------------------------------------------------------------------
+# blocked copy built on the device by dpmm_init
+# ---------------------------------------------------------------------------
+def blocked_reference(indptr, indices, data, N, D):
+    """The blocked copy from its definition: entries stably ordered by bucket
+    (tile * C + chunk, quarter), each segment padded to a multiple of 4."""
+    indptr = np.asarray(indptr, np.int64)
+    indices = np.asarray(indices, np.int64)
+    data = np.asarray(data, np.int64)
+    T, C = (N + 127) // 128, (D + 63) // 64
+    rows = np.repeat(np.arange(N), np.diff(indptr))
+    key = 4 * ((rows // 128) * C + indices // 64) + (rows // 32) % 4
+    order = np.argsort(key, kind="stable")
+    counts = np.bincount(key, minlength=4 * T * C).reshape(T * C, 4)
+    padded = (counts.sum(axis=1) + 3) // 4 * 4
+    seg0 = np.concatenate([[0], np.cumsum(padded)[:-1]])
+    tptr = np.empty(4 * T * C + 1, np.int64)
+    tptr[:-1] = (seg0[:, None] + np.concatenate([np.zeros((T * C, 1), np.int64),
+                                                 np.cumsum(counts, axis=1)[:, :3]], axis=1)).ravel()
+    tptr[-1] = padded.sum()
+    tent = np.zeros(int(padded.sum()), np.uint64)
+    ks = key[order]
+    first = np.searchsorted(ks, ks, side="left")
+    pos = tptr[ks] + (np.arange(ks.size) - first)
+    val = ((rows[order] % 128) << 22) | ((indices[order] % 64) << 16) | data[order]
+    tent[pos] = val
+    return T, C, tptr, tent.astype(np.uint32)
+
+
+def _layout_case(P, indptr, indices, data, N, D):
+    g = P.Sampler(indptr, indices, data, N, D, 1.0, 0.5, kmax=16, seed=1,
+                  engine=P.ENGINE_TILE_BF16)
+    T, C, tptr, tent = P.dpmm_debug_tile_layout(g.ctx)
+    rT, rC, rptr, rent = blocked_reference(indptr, indices, data, N, D)
+    assert (T, C) == (rT, rC)
+    np.testing.assert_array_equal(tptr, rptr)
+    np.testing.assert_array_equal(tent, rent)
+    g.close()
+
+
+def test_blocked_copy_matches_its_definition(P, tiny):
+    _layout_case(P, tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D)
+    # ragged: N not a multiple of 128 (a partial last quarter), D not a
+    # multiple of 64, empty rows, zero counts, a dense row
+    rng = np.random.default_rng(21)
+    N, D = 301, 70
+    dense = rng.integers(0, 4, size=(N, D)) * (rng.random((N, D)) < 0.2)
+    dense[::7] = 0
+    dense[5] = rng.integers(1, 300, size=D)
+    r, c = np.nonzero(dense)
+    indptr = np.concatenate([[0], np.cumsum(np.count_nonzero(dense, axis=1))]).astype(np.int32)
+    idx, val = c.astype(np.int32), dense[r, c].astype(np.int32)
+    val[3] = 0                                      # an explicit zero count
+    _layout_case(P, indptr, idx, val, N, D)
+
+
+def test_blocked_copy_at_the_bench_size(P):
+    from paper_1812_10048_gb300 import synth
+    ds = synth.pbmc68k()
+    _layout_case(P, ds.indptr, ds.indices, ds.data, ds.N, ds.D)
