@@ -144,63 +144,26 @@ struct MovePartial {
 // Every block draws the chain (a fair coin on the tag-4 stream unless `mode`
 // fixes it: 1 split, 2 merge); for the merge chain it ranks the K clusters by
 // their tag-5 keys, rank r joining pair r / 2 (the smaller index is a).  Block
-// 0 records the chain, the number of proposals and the pairs for the plan.
+// 0 of the chain's group records the chain, the number of proposals and the
+// pairs for the plan.
 //
-// Per (proposal, gene chunk): each warp sums over its genes the lgamma terms
-// of the Hastings ratio and the two gene totals.  Block b serves proposal
-// b / G, chunk b % G, with G chosen so that proposals x G fills the grid.  The
-// last block to finish a proposal (a ticket counter, no waiting) completes
-// it, its four warps evaluating the count and total terms side by side.
-__device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __restrict__ nsub,
+// Per (proposal, gene chunk) item: each warp sums over its genes the lgamma
+// terms of the Hastings ratio and the two gene totals.  A proposal has G
+// chunks, G fixed by D and the number of proposals alone, so that a chain
+// scored by a group of blocks (a batch) sums exactly as one scored by the
+// whole grid; the group's blocks take the items in turn.  The last item to
+// finish a proposal (a ticket counter, no waiting) completes it, its block's
+// four warps evaluating the count and total terms side by side.
+__device__ __forceinline__ void move_item(DevScalars* sc, const uint32_t* __restrict__ nsub,
                const uint32_t* __restrict__ Ssub, const double* __restrict__ sumlogq,
-               int32_t* __restrict__ pair_ab, const double* __restrict__ lg_base,
-               MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
+               const LgTab& tb, MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
                int32_t* __restrict__ decide, double* __restrict__ log_h, int32_t D,
-               double log_alpha, double beta, double lg_beta, int32_t split_q, int32_t mode,
-               Stream st, int32_t hastings, const float* __restrict__ Lc,
-               const float* __restrict__ Ls, const float* __restrict__ logpi,
-               const int32_t* __restrict__ desc, int32_t kmax) {
+               double log_alpha, double beta, double lg_beta, int32_t split_q, Stream st,
+               int32_t hastings, const float* __restrict__ Lc, const float* __restrict__ Ls,
+               const float* __restrict__ logpi, const int32_t* __restrict__ desc, int32_t kmax,
+               bool split, int e, int g, int G, uint32_t m0, const int* pair_s) {
     __shared__ double fin[kPartialWarps][2];
     __shared__ int last;
-    __shared__ uint32_t keys[kMaxKmax];
-    __shared__ int pair_s[2];
-    const LgTab tb = lg_tab_view(lg_base);
-    const int K = sc->K;
-    const uint32_t m0 = sc->m;
-    int chain = mode;
-    if (mode == 0) chain = word_uniform(st.words(TAG_MOVE, 0u, m0, 0u).x) < 0.5f ? 1 : 2;
-    const int E = chain == 1 ? K : K / 2;
-    const bool split = chain == 1;
-    const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
-    const int G = E > 0 ? max(1, min((int)gridDim.x / E, maxG)) : 1;
-    const int e = blockIdx.x / G, g = blockIdx.x - e * G;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->chain_sel = chain;
-        sc->n_entries = E;
-    }
-    if (!split && (e < E || blockIdx.x == 0)) {
-        for (int k = threadIdx.x; k < K; k += blockDim.x)
-            keys[k] = st.words(TAG_PAIR, (uint32_t)k, m0, 0u).x;
-        __syncthreads();
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            int rank = 0;
-            const uint32_t kk = keys[k];
-            for (int j = 0; j < K; ++j) rank += (keys[j] < kk) || (keys[j] == kk && j < k);
-            if (rank < 2 * E) {
-                if (blockIdx.x == 0) pair_ab[rank] = k;
-                if ((rank >> 1) == e) pair_s[rank & 1] = k;
-            }
-        }
-        __syncthreads();
-        if (blockIdx.x == 0) {
-            for (int p = threadIdx.x; p < E; p += blockDim.x) {
-                const int x = pair_ab[2 * p], y = pair_ab[2 * p + 1];
-                pair_ab[2 * p] = min(x, y);
-                pair_ab[2 * p + 1] = max(x, y);
-            }
-        }
-    }
-    if (E <= 0 || e >= E) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int Dc = (D + G - 1) / G;
     const int u0 = g * Dc, u1 = min(D, u0 + Dc);
@@ -256,7 +219,7 @@ __device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __res
     acc = warp_sum(acc);
     Ta = warp_sum(Ta);
     Tb = warp_sum(Tb);
-    if (lane == 0) part[blockIdx.x * kPartialWarps + w] = MovePartial{acc, Ta, Tb};
+    if (lane == 0) part[(size_t)(e * G + g) * kPartialWarps + w] = MovePartial{acc, Ta, Tb};
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -350,16 +313,82 @@ __device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __res
     }
 }
 
-// Every chain of the table in turn, each with the whole grid.
+__device__ __forceinline__ void move_chain(DevScalars* sc, const uint32_t* __restrict__ nsub,
+               const uint32_t* __restrict__ Ssub, const double* __restrict__ sumlogq,
+               int32_t* __restrict__ pair_ab, const double* __restrict__ lg_base,
+               MovePartial* __restrict__ part, int32_t* __restrict__ ticket,
+               int32_t* __restrict__ decide, double* __restrict__ log_h, int32_t D,
+               double log_alpha, double beta, double lg_beta, int32_t split_q, int32_t mode,
+               Stream st, int32_t hastings, const float* __restrict__ Lc,
+               const float* __restrict__ Ls, const float* __restrict__ logpi,
+               const int32_t* __restrict__ desc, int32_t kmax, int vb, int vg) {
+    __shared__ uint32_t keys[kMaxKmax];
+    __shared__ int32_t rnk[kMaxKmax];
+    __shared__ int pair_s[2];
+    const LgTab tb = lg_tab_view(lg_base);
+    const int K = sc->K;
+    const uint32_t m0 = sc->m;
+    int chain = mode;
+    if (mode == 0) chain = word_uniform(st.words(TAG_MOVE, 0u, m0, 0u).x) < 0.5f ? 1 : 2;
+    const int E = chain == 1 ? K : K / 2;
+    const bool split = chain == 1;
+    const int maxG = (D + kPartialThreads - 1) / kPartialThreads;
+    const int G = E > 0 ? max(1, min(kMaxPartials / E, maxG)) : 1;
+    if (vb == 0 && threadIdx.x == 0) {
+        sc->chain_sel = chain;
+        sc->n_entries = E;
+    }
+    if (!split && E > 0) {
+        for (int k = threadIdx.x; k < K; k += blockDim.x)
+            keys[k] = st.words(TAG_PAIR, (uint32_t)k, m0, 0u).x;
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            int rank = 0;
+            const uint32_t kk = keys[k];
+            for (int j = 0; j < K; ++j) rank += (keys[j] < kk) || (keys[j] == kk && j < k);
+            rnk[k] = rank;
+            if (vb == 0 && rank < 2 * E) pair_ab[rank] = k;
+        }
+        __syncthreads();
+        if (vb == 0) {
+            for (int p = threadIdx.x; p < E; p += blockDim.x) {
+                const int x = pair_ab[2 * p], y = pair_ab[2 * p + 1];
+                pair_ab[2 * p] = min(x, y);
+                pair_ab[2 * p + 1] = max(x, y);
+            }
+        }
+    }
+    for (int item = vb; item < E * G; item += vg) {
+        const int e = item / G, g = item - e * G;
+        if (!split) {
+            for (int k = threadIdx.x; k < K; k += blockDim.x)
+                if (rnk[k] < 2 * E && (rnk[k] >> 1) == e) pair_s[rnk[k] & 1] = k;
+            __syncthreads();
+        }
+        move_item(sc, nsub, Ssub, sumlogq, tb, part, ticket, decide, log_h, D, log_alpha, beta,
+                  lg_beta, split_q, st, hastings, Lc, Ls, logpi, desc, kmax, split, e, g, G, m0,
+                  pair_s);
+        __syncthreads();
+    }
+}
+
+// The chains of the table are spread over groups of blocks (one chain: the
+// whole grid), so that the chains of a batch are scored side by side.
 template <class Tab>
 __global__ void __launch_bounds__(kPartialThreads)
 k_move_partial(const __grid_constant__ Tab tab, int32_t mode) {
-    for (int b = 0; b < tab.n(); ++b) {
+    const int nb = tab.n();
+    const int ngroups = min(nb, (int)gridDim.x);
+    const int vg = (int)gridDim.x / ngroups;
+    const int group = (int)blockIdx.x / vg;
+    if (group >= ngroups) return;
+    const int vb = (int)blockIdx.x - group * vg;
+    for (int b = group; b < nb; b += ngroups) {
         const ChainArgs& ch = tab[b];
         move_chain(ch.sc, ch.nsub, ch.Ssub, ch.sumlogq, ch.pair_ab, ch.lg_table,
                    reinterpret_cast<MovePartial*>(ch.move_part), ch.move_ticket, ch.decide,
                    ch.log_h, ch.D, ch.log_alpha, ch.beta, ch.lg_beta, ch.split_q, mode, ch.st,
-                   ch.hastings, ch.Lc, ch.Ls, ch.logpi, ch.desc, ch.kmax);
+                   ch.hastings, ch.Lc, ch.Ls, ch.logpi, ch.desc, ch.kmax, vb, vg);
         __syncthreads();
     }
 }
