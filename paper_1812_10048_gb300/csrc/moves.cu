@@ -624,22 +624,29 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
 //   recounts its share of the cells of re-initialised clusters; block 0
 //   commits K = K_new and counts the phase.
 
-// Does chain ch's pending plan change anything?  (block-wide; same answer in
-// every block: an empty cluster or a sub-cluster reset; an accepted split
-// with room left; an accepted merge)
-__device__ __forceinline__ int plan_changes(const ChainArgs& ch, bool compact) {
-    const int K = ch.sc->K;
+// Does some chain's pending plan change anything?  (an empty cluster or a
+// sub-cluster reset; an accepted split with room left; an accepted merge.)
+// Warp w checks chains w, w + warps, ..., its lanes over the clusters; one
+// block-wide OR; the same answer in every block.
+template <class Tab>
+__device__ __forceinline__ int plan_changes(const Tab& tab, bool compact) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(blockDim.x >> 5);
     int change = 0;
-    if (compact) {
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            const uint32_t n0 = ch.acc_nsub[2 * k], n1 = ch.acc_nsub[2 * k + 1];
-            change |= (n0 + n1 == 0u) || (n0 + n1 >= 2u && (n0 == 0u || n1 == 0u));
+    for (int b = (int)(threadIdx.x >> 5); b < tab.n(); b += nw) {
+        const ChainArgs& ch = tab[b];
+        const int K = ch.sc->K;
+        if (compact) {
+            for (int k = lane; k < K; k += 32) {
+                const uint32_t n0 = ch.acc_nsub[2 * k], n1 = ch.acc_nsub[2 * k + 1];
+                change |= (n0 + n1 == 0u) || (n0 + n1 >= 2u && (n0 == 0u || n1 == 0u));
+            }
+        } else if (ch.sc->chain_sel == 1) {
+            if (K < ch.kmax)
+                for (int k = lane; k < K; k += 32) change |= ch.decide[k] != 0;
+        } else {
+            for (int k = lane; k < K / 2; k += 32) change |= ch.decide[k] != 0;
         }
-    } else if (ch.sc->chain_sel == 1) {
-        if (K < ch.kmax)
-            for (int k = threadIdx.x; k < K; k += blockDim.x) change |= ch.decide[k] != 0;
-    } else {
-        for (int k = threadIdx.x; k < K / 2; k += blockDim.x) change |= ch.decide[k] != 0;
     }
     return __syncthreads_or(change);
 }
@@ -657,8 +664,7 @@ k_plan_apply(const __grid_constant__ Tab tab, int32_t kind, GridBar* bar, int64_
     extern __shared__ __align__(16) uint32_t spriv[];
     __shared__ PlanSmem sm;
     const bool compact = kind == PLAN_COMPACT;
-    int any = 0;
-    for (int b = 0; b < tab.n(); ++b) any |= plan_changes(tab[b], compact);
+    const int any = plan_changes(tab, compact);
     // chain b is planned by block b % gridDim.x
     for (int b = blockIdx.x; b < tab.n(); b += gridDim.x) {
         plan_chain(tab[b], compact, sm);
