@@ -815,7 +815,7 @@ stats_tile_chain(const ChainArgs& ch, uint32_t (*cache)[128], uint32_t* priv, ui
     const int K = sc->K;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
-    if (tg >= nt) return;
+    if (tg >= nt || tg >= T) return;   // no tile of this chain for this block
     const int gene0 = c * 64;
     if (K > kTileMaxK) {
         // counts straight into the main rows (global atomics)
