@@ -79,10 +79,14 @@ void dpmm_default_opts(dpmm_opts* opts);
  *   data    int32[nnz], counts >= 0
  * alpha > 0 (DP concentration), beta > 0 (eq. 28 lambda).  opts may be NULL.
  * stream: a cudaStream_t to run on, or NULL for a stream owned by the context.
+ * The three arrays may be host or device memory: they are copied once on the
+ * context's stream (device arrays must be complete before the call), then
+ * validated and turned into the packed and blocked copies on the device.
  * The chain starts with K = 1 (all cells in cluster 0) and fair-coin
  * sub-labels.  Errors: DPMM_EINVAL (malformed CSR, D < 1, N < 1, alpha or
- * beta not positive, kmax out of range), DPMM_ENOMEM, DPMM_ECUDA.
- * Synchronises the stream before returning.
+ * beta not positive, kmax out of range), DPMM_EOVERFLOW (a gene whose counts
+ * sum to 2^32 or more; a blocked copy above 2^31 - 1 entries), DPMM_ENOMEM,
+ * DPMM_ECUDA.  Synchronises the stream before returning.
  */
 int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices,
               const int32_t* data, int64_t N, int32_t D, double alpha, double beta,

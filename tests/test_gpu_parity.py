@@ -404,3 +404,34 @@ def _assign_parity(P, tiny, K, engine):
     np.testing.assert_array_equal(Ssub, oS)
     if Kg == o.K and np.array_equal(lab, o.labels) and np.array_equal(sb, o.sub):
         np.testing.assert_allclose(sq, o.sumlogq, rtol=1e-4, atol=1e-2)
+
+
+def test_init_from_device_and_pinned_arrays(P, tiny):
+    """dpmm_init takes host, pinned host or device arrays: the chains are
+    identical, and a bad entry in device memory is reported as from the host."""
+    import torch
+    args = (tiny.N, tiny.D, 1.0, 0.5)
+    kw = dict(seed=5, kmax=32)
+    a = P.Sampler(tiny.indptr, tiny.indices, tiny.data, *args, **kw)
+    dev = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32)).cuda()
+           for x in (tiny.indptr, tiny.indices, tiny.data)]
+    pin = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32)).pin_memory()
+           for x in (tiny.indptr, tiny.indices, tiny.data)]
+    torch.cuda.synchronize()
+    b = P.Sampler(dev[0], dev[1], dev[2], *args, **kw)
+    c = P.Sampler(pin[0], pin[1], pin[2], *args, **kw)
+    for s in (a, b, c):
+        s.step(6)
+    for x, y, z in zip(a.get_state(), b.get_state(), c.get_state()):
+        np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(x, z)
+    bad = dev[1].clone()
+    bad[17] = tiny.D
+    torch.cuda.synchronize()
+    with pytest.raises(P.DpmmError, match="column index .* at entry 17"):
+        P.Sampler(dev[0], bad, dev[2], *args, **kw)
+    badv = dev[2].clone()
+    badv[3] = -2
+    torch.cuda.synchronize()
+    with pytest.raises(P.DpmmError, match="negative count -2 at entry 3"):
+        P.Sampler(dev[0], dev[1], badv, *args, **kw)
