@@ -380,3 +380,42 @@ def test_one_local_iteration_is_the_default_chain(tiny_dataset):
     assert not np.allclose(a.sumlogq, c.sumlogq)          # with new theta-bar draws
     with pytest.raises(ValueError):
         Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, local_iters=17)
+
+
+# ---------------------------------------------------------------------------
+# helpers of the sweep, pinned directly
+# ---------------------------------------------------------------------------
+def test_compact_keeps_survivors_in_order():
+    from oracle.sampler import compact
+    labels = np.array([4, 0, 4, 2, 0, 4])          # clusters 1 and 3 are empty
+    per = np.array([10.0, 11.0, 12.0, 13.0, 14.0])
+    new, K, (kept,) = compact(labels, 5, per)
+    assert K == 3
+    np.testing.assert_array_equal(new, [2, 0, 2, 1, 0, 2])
+    np.testing.assert_array_equal(kept, [10.0, 12.0, 14.0])
+
+
+def test_fair_coin_sublabels_are_fair_and_independent_across_kinds():
+    from oracle.sampler import fair_coin_sublabels
+    cells = np.arange(200000)
+    a = fair_coin_sublabels(cells, 7, 0, 3, philox.SUBINIT_RESET)
+    b = fair_coin_sublabels(cells, 7, 0, 3, philox.SUBINIT_SPLIT)
+    c = fair_coin_sublabels(cells, 7, 0, 4, philox.SUBINIT_RESET)
+    for x in (a, b, c):
+        assert set(np.unique(x)) <= {0, 1}
+        assert abs(x.mean() - 0.5) < 5 * np.sqrt(0.25 / cells.size)
+    for x, y in ((a, b), (a, c)):
+        r = np.corrcoef(x, y)[0, 1]
+        assert abs(r) < 5 / np.sqrt(cells.size)
+
+
+def test_label_gumbels_follow_the_gumbel_law_and_word_layout():
+    from oracle.sampler import label_gumbels
+    N, K = 40000, 6
+    g = label_gumbels(N, K, 3, 1, 9)
+    for k in range(K):
+        assert stats.kstest(g[:, k], "gumbel_r").pvalue > 1e-4
+    # column k is word k % 4 of call k // 4 on counter (cell, t, tag 0, k // 4)
+    w = philox.stream_words(3, 1, philox.TAG_LABEL, np.arange(N), 9, 1)
+    np.testing.assert_array_equal(g[:, 5], philox.uniform_to_gumbel(philox.word_to_uniform(w[:, 1])))
+    assert abs(np.corrcoef(g[:, 0], g[:, 4])[0, 1]) < 5 / np.sqrt(N)
