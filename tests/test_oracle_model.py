@@ -214,3 +214,22 @@ def test_instantiated_split_with_posterior_proposal_densities_is_the_collapsed_r
     crp = np.log(alpha) + lg(n0) + lg(n1) - lg(nk)
     col = log_hastings_split(n0, n1, S0, S1, alpha, lam, 0.0)
     assert abs((inst - eq14 - q) - (col - crp)) < 1e-9 * max(1.0, abs(col))
+
+
+def test_hastings_ratios_match_the_hand_derived_golden_values():
+    """tests/golden/hastings_small.txt: exact ratios derived by hand for tiny
+    split and merge proposals (derivations in the file)."""
+    import os
+    from fractions import Fraction as F
+    path = os.path.join(os.path.dirname(__file__), "golden", "hastings_small.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 5
+    for kind, n0, n1, s0, s1, alpha, beta, q, H in rows:
+        S0 = np.array([int(v) for v in s0.split(",")], dtype=float)
+        S1 = np.array([int(v) for v in s1.split(",")], dtype=float)
+        a, b = float(F(alpha)), float(F(beta))
+        if kind == "split":
+            got = log_hastings_split(int(n0), int(n1), S0, S1, a, b, math.log(F(q)))
+        else:
+            got = log_hastings_merge(int(n0), int(n1), S0, S1, a, b)
+        assert abs(got - math.log(F(H))) < 1e-12, (kind, n0, n1, s0, s1, got, math.log(F(H)))
