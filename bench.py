@@ -346,7 +346,7 @@ def run_ours(args, rank, world, local):
 
 
 # ---------------------------------------------------------------------------
-# Other workloads (their own JSON line; the driver's default run is "main")
+# Other workloads (their own JSON line; the default run is "main")
 # ---------------------------------------------------------------------------
 def time_steps(step_fn, stream, steps, warmup, torch, flush=None):
     """Per-step device times of step_fn() on `stream` after `warmup` untimed steps."""

@@ -4,7 +4,7 @@
 // callers cannot allocate: a framework whose caching allocator already owns
 // the device memory (a cudaMalloc of its own can fail or implicitly
 // synchronise the whole device), or latency-critical code that must not call
-// the driver's allocator (cudaMalloc / cudaFree synchronise the device and can
+// the CUDA allocator (cudaMalloc / cudaFree synchronise the device and can
 // take milliseconds).  dpmm_logml_grad_noalloc() serves them: it keeps its
 // scratch (the statistics n_k, S_ku, T_k and small staging buffers) in one
 // file-scope __device__ array below, and calls no cudaMalloc, cudaFree or any
