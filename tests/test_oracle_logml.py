@@ -114,3 +114,23 @@ def test_eb_step_clamps_and_ascends():
         cur = log_ml(n, S, la, np.full(D, lb))
         assert cur >= prev - 1e-12
         prev = cur
+
+
+def test_log_ml_and_gradients_match_the_hand_derived_golden_values():
+    """tests/golden/logml_small.txt: exact values derived by hand."""
+    import math
+    import os
+    from fractions import Fraction as F
+    from oracle.logml import log_ml, log_ml_grad
+    path = os.path.join(os.path.dirname(__file__), "golden", "logml_small.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 3
+    for case, n, S, alpha, beta, lml, ga, gb in rows:
+        n = np.array([float(v) for v in n.split("|")])
+        S = np.array([[float(v) for v in r.split(",")] for r in S.split("|")])
+        la = math.log(float(F(alpha)))
+        lb = np.log(np.array([float(F(v)) for v in beta.split(",")]))
+        assert abs(log_ml(n, S, la, lb) - math.log(F(lml))) < 1e-12, case
+        g_a, g_b = log_ml_grad(n, S, la, lb)
+        assert abs(g_a - float(F(ga))) < 1e-12, case
+        np.testing.assert_allclose(g_b, [float(F(v)) for v in gb.split(",")], atol=1e-12)
