@@ -79,3 +79,19 @@ def test_options_struct_layout_matches_the_header(tmp_path):
     assert int(out["sizeof"]) == ctypes.sizeof(dpmm_opts)
     for f in fields:
         assert int(out[f]) == getattr(dpmm_opts, f).offset, f
+
+
+def test_binding_argument_counts_match_the_prototypes():
+    """Every prototype in include/dpmm.h has as many parameters as its ctypes
+    signature (a wrong count would pass garbage through the C ABI)."""
+    from paper_1812_10048_gb300 import _lib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "dpmm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"\b(dpmm_\w+)\s*\(([^;{]*?)\)\s*;", text)
+    assert len(protos) >= 30
+    for name, params in protos:
+        params = " ".join(params.split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert name in _lib.SIGNATURES, name
+        assert len(_lib.SIGNATURES[name][1]) == n, (name, n, len(_lib.SIGNATURES[name][1]))
