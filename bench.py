@@ -661,7 +661,8 @@ def run_study(args):
     30,000 counts per cell, 5 chains per dataset; ARI per depth.  (3) Local
     Gibbs iterations per sweep L = 1, 2, 4 on S at 10,000 and M at 30,000
     counts per cell: mean ARI of 20 chains along the chain and the time per
-    step."""
+    step.  (4) The collapsed split ratio against the instantiated eq. 18 one
+    on the 68k x 1k workload: K and ARI along two chains of each."""
     import torch
     from paper_1812_10048_gb300 import build as _build
     _build.build()
@@ -767,6 +768,29 @@ def run_study(args):
         sg.close()
     local_out["pbmc68k_single_chain_ms_per_step"] = single
     print("local single chain", single, file=sys.stderr, flush=True)
+    # collapsed (default) against the instantiated eq. 18 split ratio on the
+    # 68k x 1k workload: K every 10 steps and ARI every 40, two seeds
+    hastings_out = {}
+    for mode in ("integrated", "instantiated"):
+        for seed in (1, 2):
+            sh = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256,
+                           seed=seed, hastings=mode)
+            sh.step(3)
+            sh.sync()
+            t0 = time.perf_counter()
+            Ks, aris = [], {}
+            for blk in range(40):
+                sh.step(10)
+                lab, K = sh.labels()
+                Ks.append(int(K))
+                if blk % 4 == 3:
+                    aris[str(10 * (blk + 1) + 3)] = round(float(adjusted_rand_index(lab, ds.labels)), 4)
+            sh.sync()
+            hastings_out[f"{mode}/seed{seed}"] = {
+                "K_every_10_steps": Ks, "ari_at_step": aris,
+                "wall_s_400_steps": round(time.perf_counter() - t0, 3)}
+            sh.close()
+            print("hastings", mode, seed, Ks[-1], aris["403"], file=sys.stderr, flush=True)
     line = {"metric": "alpha / repeat, library-size and local-Gibbs studies (synthetic)",
             "value": None, "unit": None, "n_gpus": 1, "steps": steps, "repeats": R,
             "dtype": "bf16", "data": "synthetic",
@@ -775,6 +799,7 @@ def run_study(args):
                                    "local-iteration studies)", "beta": 0.1, "kmax": 64,
                        "alphas": list(alphas), "depths": list(depths)},
             "alpha_study": out, "depth_study": depth_out, "local_iters_study": local_out,
+            "hastings_study": hastings_out,
             "wall_s": round(time.time() - t_all, 1)}
     print(json.dumps(line), flush=True)
     return 0
