@@ -233,3 +233,32 @@ def test_hastings_ratios_match_the_hand_derived_golden_values():
         else:
             got = log_hastings_merge(int(n0), int(n1), S0, S1, a, b)
         assert abs(got - math.log(F(H))) < 1e-12, (kind, n0, n1, s0, s1, got, math.log(F(H)))
+
+
+@pytest.mark.parametrize("beta", [0.1, 0.5, 1.0])
+def test_eq18_as_printed_favours_a_split_the_collapsed_ratio_rejects(beta):
+    """Eq. 18 with the sweep-style readings (theta drawn from the eq. 28
+    posteriors) against the collapsed ratio, for a fair-coin split of ONE
+    generating cluster of a 4,000 x 1,000 synthetic matrix: eq. 18 is
+    thousands of nats above zero (the extra Dirichlet density of the new
+    theta dominates), the collapsed ratio thousands below."""
+    from paper_1812_10048_gb300 import synth
+    from oracle.model import log_hastings_split_instantiated
+    ds = synth.make_dataset(4000, 1000, 4, seed=3)
+    X = sp.csr_matrix((ds.data, ds.indices, ds.indptr), shape=(ds.N, ds.D)).toarray()
+    rng = np.random.default_rng(0)
+    idx = np.nonzero(ds.labels == 0)[0]
+    side = rng.integers(0, 2, idx.size)
+    S0, S1 = X[idx[side == 0]].sum(0), X[idx[side == 1]].sum(0)
+    n0, n1 = int((side == 0).sum()), int((side == 1).sum())
+
+    def logdir(c):
+        g = np.maximum(rng.gamma(c), 1e-300)
+        return np.log(g) - np.log(g.sum())
+
+    lk, l0, l1 = logdir(beta + S0 + S1), logdir(beta + S0), logdir(beta + S1)
+    D = ds.D
+    dirichlet_term = gammaln(D * beta) - D * gammaln(beta) + (beta - 1) * (l0.sum() + l1.sum() - lk.sum())
+    inst = log_hastings_split_instantiated(n0, n1, S0, S1, lk, l0, l1, np.log(0.25), 1.0, beta, 0.0)
+    col = log_hastings_split(n0, n1, S0, S1, 1.0, beta, 0.0)
+    assert dirichlet_term > 5000 and inst > 4000 and col < -2500, (dirichlet_term, inst, col)
