@@ -135,14 +135,15 @@ def partition_key(p, n):
 
 
 TINY_X = np.array([[4, 0, 1], [3, 1, 0], [0, 3, 2], [1, 4, 1], [2, 2, 2]])
+# six cells, three genes: 203 partitions, 31 of them into two blocks
+SIX_X = np.array([[4, 0, 1], [3, 1, 0], [0, 3, 2], [1, 4, 1], [2, 2, 2], [0, 1, 5]])
 
 
-def collapsed_gibbs_frequencies(x, alpha, beta, iters, seed):
-    """Neal (2000) Algorithm 3: textbook collapsed Gibbs; validates the enumerator."""
-    rng = np.random.default_rng(seed)
+def collapsed_gibbs_state(x, alpha, beta, iters, rng):
+    """Neal (2000) Algorithm 3: textbook collapsed Gibbs from one cluster;
+    returns the partition after `iters` passes (validates the enumerator)."""
     n = x.shape[0]
     lab = np.zeros(n, dtype=int)
-    counts = {}
     for _ in range(iters):
         for i in range(n):
             lab[i] = -1
@@ -157,21 +158,37 @@ def collapsed_gibbs_frequencies(x, alpha, beta, iters, seed):
             lp = np.array(lp)
             c = rng.choice(len(lp), p=np.exp(lp - logsumexp(lp)))
             lab[i] = blocks[c] if c < len(blocks) else (max(blocks) + 1 if blocks else 0)
-        key = canonical(lab)
+    return canonical(lab)
+
+
+def chi_square_against(counts, parts, post, n):
+    """Pearson chi-square p-value of partition counts of independent draws
+    against the enumerated probabilities (cells expecting fewer than 5 draws
+    pooled into one)."""
+    R = sum(counts.values())
+    obs = np.array([counts.get(partition_key(p, n), 0) for p in parts], dtype=float)
+    assert obs.sum() == R                 # every draw is one of the enumerated partitions
+    exp = post * R
+    small = exp < 5
+    if small.any():
+        obs = np.append(obs[~small], obs[small].sum())
+        exp = np.append(exp[~small], exp[small].sum())
+    return stats.chisquare(obs, exp).pvalue
+
+
+def test_enumerated_posterior_matches_collapsed_gibbs_on_six_cells():
+    """Independent textbook collapsed-Gibbs chains (8 passes each) on six
+    cells land on the 203 partitions with the enumerated eq. 26 / eq. 28 /
+    CRP posterior probabilities (chi-square)."""
+    n = SIX_X.shape[0]
+    parts, post = exact_partition_posterior(SIX_X, 1.0, 0.5)
+    assert len(parts) == 203
+    rng = np.random.default_rng(0)
+    counts = {}
+    for _ in range(1500):
+        key = collapsed_gibbs_state(SIX_X, 1.0, 0.5, 8, rng)
         counts[key] = counts.get(key, 0) + 1
-    return counts
-
-
-def total_variation(counts, parts, post, n):
-    tot = sum(counts.values())
-    emp = np.array([counts.get(partition_key(p, n), 0) / tot for p in parts])
-    return 0.5 * np.abs(emp - post).sum()
-
-
-def test_enumerated_posterior_matches_collapsed_gibbs():
-    parts, post = exact_partition_posterior(TINY_X, 1.0, 0.5)
-    counts = collapsed_gibbs_frequencies(TINY_X, 1.0, 0.5, 6000, seed=0)
-    assert total_variation(counts, parts, post, TINY_X.shape[0]) < 0.04
+    assert chi_square_against(counts, parts, post, n) > 1e-3
 
 
 def k_restricted_posterior(x, K, alpha, beta):
@@ -182,54 +199,76 @@ def k_restricted_posterior(x, K, alpha, beta):
     return parts, post
 
 
-def test_sweep_is_exact_gibbs_for_fixed_K_posterior():
-    """With K held fixed, the eq. 4 sweep (pi | c, theta | c, then all c_i | pi, theta
-    in parallel) is a Gibbs sampler for p(c | x, K non-empty clusters).  Label draws
-    that empty a cluster are redrawn with fresh counters (rejection sampling of the
-    restricted conditional), so the chain's partition frequencies must match the
-    enumerated posterior over partitions into exactly K blocks."""
+def fixed_k_sweeps(X, K, alpha, beta, labels, seed, sweeps):
+    """The eq. 4 sweep with K held fixed (pi | c, theta | c, then all c_i | pi,
+    theta in parallel): label draws that empty a cluster are redrawn with
+    fresh counters, pi and theta held (rejection sampling of the restricted
+    conditional).  Returns the canonical partition after `sweeps` sweeps."""
     from oracle.sampler import draw_pi, draw_theta
-    x = TINY_X
-    n, D = x.shape
-    K, alpha, beta = 2, 1.0, 0.5
-    X = csr_matrix(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D)
-    parts, post = k_restricted_posterior(x, K, alpha, beta)
-    labels = np.array([0, 0, 1, 1, 1])
+    n = X.shape[0]
     sub = np.zeros(n, dtype=np.int64)
-    counts, s, iters = {}, 0, 5000
-    for t in range(iters):
+    s = 0
+    for t in range(sweeps):
         nsub, Ssub = sufficient_stats(X, labels, sub, K)
-        logpi = draw_pi(nsub.sum(axis=1), alpha, 0, 0, t)
-        logtheta = draw_theta(Ssub, beta, 0, 0, t)
-        while True:                      # redraw c only, pi and theta held fixed
-            new, _, _, _ = assign(X, logpi, logtheta, labels, sub, nsub, 0, 0, s)
+        logpi = draw_pi(nsub.sum(axis=1), alpha, seed, 0, t)
+        logtheta = draw_theta(Ssub, beta, seed, 0, t)
+        while True:
+            new, _, _, _ = assign(X, logpi, logtheta, labels, sub, nsub, seed, 0, s)
             s += 1
             if np.bincount(new, minlength=K).min() > 0:
                 break
         labels = new
-        key = canonical(labels)
+    return canonical(labels)
+
+
+@pytest.mark.parametrize("base", [100000, 200000])
+def test_sweep_is_exact_gibbs_for_fixed_K_posterior_on_six_cells(base):
+    """With K held fixed, the eq. 4 sweep is a Gibbs sampler for p(c | x, K
+    non-empty clusters) (Section 2.2: cells are conditionally independent
+    given pi and theta).  1,200 independent chains (their own Philox seeds,
+    random two-block starts, 8 sweeps each) must land on the 31 two-block
+    partitions of six cells with the enumerated posterior probabilities
+    (chi-square, p > 0.001).  Four sweeps are measurably too few to forget
+    the start; six already pass."""
+    x = SIX_X
+    n, D = x.shape
+    K, alpha, beta = 2, 1.0, 0.5
+    X = csr_matrix(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D)
+    parts, post = k_restricted_posterior(x, K, alpha, beta)
+    assert len(parts) == 31
+    rng = np.random.default_rng(base)
+    counts = {}
+    for r in range(1200):
+        while True:
+            labels = rng.integers(0, K, n)
+            if np.bincount(labels, minlength=K).min() > 0:
+                break
+        key = fixed_k_sweeps(X, K, alpha, beta, labels, base + r, 8)
         counts[key] = counts.get(key, 0) + 1
-    # 5000 correlated steps leave TV ~0.02 of sampling noise; redrawing pi and theta
-    # together with rejected labels (a biased restricted conditional) gives ~0.1.
-    assert total_variation(counts, parts, post, n) < 0.05
+    assert chi_square_against(counts, parts, post, n) > 1e-3
 
 
 @pytest.mark.xfail(strict=True, reason=(
     "finding: the paper's chain (parallel restricted Gibbs that may empty clusters, "
     "plus separate split-only and merge-only MH chains) is not invariant for the "
-    "DPMM posterior on 5-cell data; it over-weights coarse partitions"))
-def test_full_chain_matches_exact_partition_posterior():
-    x = TINY_X
+    "DPMM posterior on six-cell data; it over-weights coarse partitions"))
+def test_full_chain_matches_exact_partition_posterior_on_six_cells():
+    """Independent full chains (sweep + coin-selected split/merge, 12 steps
+    each from K = 1) against the enumerated posterior over all 203
+    partitions (chi-square)."""
+    x = SIX_X
     n, D = x.shape
     parts, post = exact_partition_posterior(x, 1.0, 0.5)
-    s = Sampler(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D, 1.0, 0.5, seed=11)
     counts = {}
-    for _ in range(3000):
-        s.sweep()
-        s.split_merge(0)
+    for r in range(500):
+        s = Sampler(np.arange(n + 1) * D, np.tile(np.arange(D), n), x.ravel(), n, D, 1.0, 0.5,
+                    seed=11 + r)
+        for _ in range(12):
+            s.sweep()
+            s.split_merge(0)
         key = canonical(s.labels)
         counts[key] = counts.get(key, 0) + 1
-    assert total_variation(counts, parts, post, n) < 0.05
+    assert chi_square_against(counts, parts, post, n) > 1e-3
 
 
 # ---------------------------------------------------------------------------
