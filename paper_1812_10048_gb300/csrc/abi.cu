@@ -105,7 +105,7 @@ void free_ctx(Ctx& c) {
     for (cudaEvent_t& e : c.ev)
         if (e) cudaEventDestroy(e);
     void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
-                    c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_sumlogq, c.logpi, c.Lc, c.Ls,
+                    c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_logq, c.logpi, c.Lc, c.Ls,
                     c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
                     c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B, c.noise,
                     c.gbar, c.d_chains};
@@ -141,7 +141,7 @@ ChainArgs dpmm::chain_args(const Ctx& c) {
     a.sumlogq = c.sumlogq;
     a.acc_nsub = c.acc_nsub;
     a.acc_Ssub = c.acc_Ssub;
-    a.acc_sumlogq = c.acc_sumlogq;
+    a.acc_logq = c.acc_logq;
     a.logpi = c.logpi;
     a.Lc = c.Lc;
     a.Ls = c.Ls;
@@ -453,7 +453,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     CKI(dalloc(&c.sumlogq, (size_t)c.kmax));
     CKI(dalloc(&c.acc_nsub, K2));
     CKI(dalloc(&c.acc_Ssub, K2 * D));
-    CKI(dalloc(&c.acc_sumlogq, (size_t)c.kmax));
+    CKI(dalloc(&c.acc_logq, (size_t)c.kmax));
     CKI(dalloc(&c.logpi, (size_t)c.kmax + 1));
     CKI(dalloc(&c.Lc, (size_t)c.kmax * D));
     CKI(dalloc(&c.Ls, K2 * D));
@@ -505,7 +505,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     free_scratch();
     CKI(cudaMemsetAsync(c.acc_nsub, 0, sizeof(uint32_t) * K2, c.stream));
     CKI(cudaMemsetAsync(c.acc_Ssub, 0, sizeof(uint32_t) * K2 * D, c.stream));
-    CKI(cudaMemsetAsync(c.acc_sumlogq, 0, sizeof(double) * c.kmax, c.stream));
+    CKI(cudaMemsetAsync(c.acc_logq, 0, sizeof(unsigned long long) * c.kmax, c.stream));
     CKI(cudaMemsetAsync(c.sumlogq, 0, sizeof(double) * c.kmax, c.stream));
     CKI(cudaMemsetAsync(c.reinit, 0, c.kmax, c.stream));
     std::memset(c.sc_host, 0, sizeof(DevScalars));

@@ -132,7 +132,7 @@ struct Ctx {
     double* sumlogq = nullptr;    // [kmax]
     uint32_t* acc_nsub = nullptr;
     uint32_t* acc_Ssub = nullptr;
-    double* acc_sumlogq = nullptr;
+    unsigned long long* acc_logq = nullptr;  // sum log q, exact units of 2^-32
 
     // parameters
     float* logpi = nullptr;       // [kmax + 1]
@@ -192,6 +192,22 @@ struct Ctx {
     bool graph_profiled = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
+
+// ---------------------------------------------------------------------------
+// Sum of log q_i accumulators.  A sweep adds every cell's log q_i (FP32) into
+// its cluster's accumulator as an integer number of 2^-32 units (64-bit two's
+// complement, rounded to nearest): integer additions give the same total in
+// any order, so the per-cluster sums (and every split decision that reads
+// them) are reproducible bit for bit whatever the schedule of the atomics.
+// The sum is read back as FP64; each cell's rounding is below 2^-33.
+// ---------------------------------------------------------------------------
+constexpr double kLogqScale = 4294967296.0;
+__device__ __forceinline__ unsigned long long logq_fixed(float logq) {
+    return (unsigned long long)__double2ll_rn((double)logq * kLogqScale);
+}
+__host__ __device__ __forceinline__ double logq_value(unsigned long long acc) {
+    return (double)(long long)acc * (1.0 / kLogqScale);
+}
 
 // ---------------------------------------------------------------------------
 // Device helpers.
@@ -328,7 +344,7 @@ struct ChainArgs {
     double* sumlogq;
     uint32_t* acc_nsub;
     uint32_t* acc_Ssub;
-    double* acc_sumlogq;
+    unsigned long long* acc_logq;
     float* logpi;
     float* Lc;
     float* Ls;

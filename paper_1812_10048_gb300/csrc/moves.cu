@@ -444,7 +444,7 @@ struct PlanSmem {
 
 __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub,
                            double* __restrict__ sumlogq, uint32_t* __restrict__ acc_nsub,
-                           double* __restrict__ acc_sumlogq,
+                           const unsigned long long* __restrict__ acc_logq,
                            const int32_t* __restrict__ decide,
                            const int32_t* __restrict__ pair_ab, uint32_t* __restrict__ lmap,
                            int32_t* __restrict__ desc, uint8_t* __restrict__ reinit,
@@ -467,7 +467,7 @@ __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ 
         if (k < K) {
             n0 = acc_nsub[2 * k];
             n1 = acc_nsub[2 * k + 1];
-            sq = acc_sumlogq[k];
+            sq = logq_value(acc_logq[k]);
         }
         const bool keep = n0 + n1 > 0;
         const int j = block_exclusive_scan(keep ? 1 : 0, tmp, &total);
@@ -653,7 +653,7 @@ __device__ __forceinline__ int plan_changes(const Tab& tab, bool compact) {
 
 __device__ __forceinline__ void plan_chain(const ChainArgs& ch, bool compact, PlanSmem& sm) {
     plan_block(ch.sc, compact ? PLAN_COMPACT : PLAN_SPLIT, ch.nsub, ch.sumlogq, ch.acc_nsub,
-               ch.acc_sumlogq, ch.decide, ch.pair_ab, ch.lmap, ch.desc, ch.reinit, ch.kmax,
+               ch.acc_logq, ch.decide, ch.pair_ab, ch.lmap, ch.desc, ch.reinit, ch.kmax,
                compact ? &ch.sc->t : &ch.sc->m, sm);
 }
 

@@ -59,9 +59,9 @@ __device__ __forceinline__ void select_engine(DevScalars* sc, int K, int32_t til
 // The sweep's n-bar and sum log q accumulators start at zero (they are added
 // into by the label and statistics kernels and read by the compaction).
 __device__ __forceinline__ void clear_accumulators(int K, uint32_t* acc_nsub,
-                                                   double* acc_sumlogq) {
+                                                   unsigned long long* acc_logq) {
     for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) acc_nsub[i] = 0u;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) acc_sumlogq[i] = 0.0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) acc_logq[i] = 0ull;
 }
 
 template <class Tab>
@@ -71,7 +71,7 @@ __global__ void k_select_engine(const __grid_constant__ Tab tab) {
         const int K = ch.sc->K;
         __syncthreads();
         if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
-        clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
+        clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
     }
     fill_noise(tab, (int64_t)gridDim.x, (int64_t)blockIdx.x);
 }
@@ -182,7 +182,7 @@ k_draw_params(const __grid_constant__ Tab tab) {
             const int row = (int)(id - base);
             if (row == 0) {
                 if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
-                clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
+                clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
             }
             draw_row(ch, K, open, TAG_THETA, t, row, red, lgc);
             __syncthreads();
@@ -216,7 +216,7 @@ k_draw_local(const __grid_constant__ Tab tab, int32_t j) {
         int64_t first = base + (((int64_t)blockIdx.x - base) % gridDim.x + gridDim.x) % gridDim.x;
         for (int64_t id = first; id < base + rows; id += gridDim.x) {
             const int i = (int)(id - base);
-            if (i == 0) clear_accumulators(K, ch.acc_nsub, ch.acc_sumlogq);
+            if (i == 0) clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
             draw_row(ch, K, 0, tag, t, 3 * (i >> 1) + 1 + (i & 1), red, lgc);
             __syncthreads();
         }
@@ -355,7 +355,7 @@ __device__ __forceinline__ float2 sub_scores_group(const Csr& csr, int64_t beg, 
 template <int LANES, class Tab>
 __global__ void __launch_bounds__(kLocalThreads)
 k_local_sub(const __grid_constant__ Tab tab, int32_t j) {
-    __shared__ double bsq[kLocalSlots][kMaxKmax];
+    __shared__ unsigned long long bsq[kLocalSlots][kMaxKmax];
     const uint32_t tag = kLocalTag0 + 2u * (uint32_t)(j - 1) + 1u;
     const int lane = threadIdx.x & 31;
     const int sl = lane % LANES;                                // lane within the cell group
@@ -372,7 +372,7 @@ k_local_sub(const __grid_constant__ Tab tab, int32_t j) {
                 ch.Ssub[i] = 0u;
         total += ch.N;
     }
-    for (int i = threadIdx.x; i < kLocalSlots * kMaxKmax; i += blockDim.x) (&bsq[0][0])[i] = 0.0;
+    for (int i = threadIdx.x; i < kLocalSlots * kMaxKmax; i += blockDim.x) (&bsq[0][0])[i] = 0ull;
     __syncthreads();
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t g0 = min(total, (int64_t)blockIdx.x * per), g1 = min(total, g0 + per);
@@ -418,9 +418,10 @@ k_local_sub(const __grid_constant__ Tab tab, int32_t j) {
             const uint32_t s = draw_sublabel_n(ch.st, cell, c, st, n0, n1, lik, tag,
                                                ch.sc->t - 1u, &logq);
             ch.state[cell] = pack_state((uint32_t)c, s);
-            if (logq != 0.0f) {
-                if (b - b0 < kLocalSlots) atomicAdd(&bsq[b - b0][c], (double)logq);
-                else atomicAdd(&ch.acc_sumlogq[c], (double)logq);
+            const unsigned long long q = logq_fixed(logq);
+            if (q) {
+                if (b - b0 < kLocalSlots) atomicAdd(&bsq[b - b0][c], q);
+                else atomicAdd(&ch.acc_logq[c], q);
             }
         }
         g = gn;
@@ -435,7 +436,7 @@ k_local_sub(const __grid_constant__ Tab tab, int32_t j) {
         const ChainArgs& ch = tab[b0 + q];
         const int K = ch.sc->K;
         for (int k = threadIdx.x; k < K; k += blockDim.x)
-            if (bsq[q][k] != 0.0) atomicAdd(&ch.acc_sumlogq[k], bsq[q][k]);
+            if (bsq[q][k]) atomicAdd(&ch.acc_logq[k], bsq[q][k]);
     }
 }
 
@@ -456,7 +457,7 @@ __global__ void k_local_commit(const __grid_constant__ Tab tab) {
                 ch.acc_Ssub[i] = 0u;
             }
         for (int64_t i = tid; i < 2 * K; i += stride) ch.nsub[i] = ch.acc_nsub[i];
-        for (int64_t i = tid; i < K; i += stride) ch.sumlogq[i] = ch.acc_sumlogq[i];
+        for (int64_t i = tid; i < K; i += stride) ch.sumlogq[i] = logq_value(ch.acc_logq[i]);
     }
 }
 
@@ -477,7 +478,7 @@ __device__ __forceinline__ int warp_argmax(float best, int bestk) {
 // K > 32: lanes own clusters lane, lane + 32, ...; the row is contracted once
 // per chunk of 32 clusters and the running Gumbel-max kept across chunks.
 __device__ __forceinline__ void assign_cells(const ChainArgs& a, const float* L, int ldL, int K,
-                                             uint32_t t, double* blk_sumlogq) {
+                                             uint32_t t, unsigned long long* blk_logq) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -506,7 +507,7 @@ __device__ __forceinline__ void assign_cells(const ChainArgs& a, const float* L,
             float logq;
             const uint32_t s = draw_sublabel(a, cell, c, lik, TAG_SUBLABEL, t, &logq);
             a.state[cell] = pack_state((uint32_t)c, s);
-            atomicAdd(&blk_sumlogq[c], (double)logq);
+            atomicAdd(&blk_logq[c], logq_fixed(logq));
         }
     }
 }
@@ -625,7 +626,8 @@ template <int P>
 __device__ __forceinline__ void assign_cells_v2(const ChainArgs& a, const float* sLc, int Kp,
                                                 const float2* Ls2, int ldS, int K, uint32_t t,
                                                 const float* spi, const float* slw,
-                                                double* wsq, uint32_t* wn, uint32_t* sS) {
+                                                unsigned long long* wsq, uint32_t* wn,
+                                                uint32_t* sS) {
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int64_t warp0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
@@ -637,7 +639,7 @@ __device__ __forceinline__ void assign_cells_v2(const ChainArgs& a, const float*
     const int sub_word = col - K;                       // 0 or 1 on those lanes
     const bool packed = a.csr.entries != nullptr;
     constexpr int R = P <= 16 ? kRowRegs : kRowRegs / 2;   // register budget at 1024 threads
-    double* my_sq = wsq + (size_t)wid * K;
+    unsigned long long* my_sq = wsq + (size_t)wid * K;
     uint32_t* my_n = wn + (size_t)wid * 2 * K;
     for (int64_t cell = warp0; cell < a.N; cell += nwarps) {
         const int64_t beg = a.csr.indptr[cell], end = a.csr.indptr[cell + 1];
@@ -736,7 +738,7 @@ __device__ __forceinline__ void assign_cells_v2(const ChainArgs& a, const float*
             const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
             const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
             a.state[cell] = pack_state((uint32_t)c, s);
-            my_sq[c] += (double)logq;
+            my_sq[c] += logq_fixed(logq);
             my_n[2 * c + s] += 1u;
         }
         if (sS) {
@@ -767,9 +769,9 @@ __device__ __forceinline__ void assign_chain(const ChainArgs& a, int64_t smem_by
     const int nw = K <= 32 ? (int)(blockDim.x >> 5) : 0;
     // small per-block arrays first: per-warp sum log q and n-bar, block sum log q,
     // log pi and the sweep-start n-bar
-    double* wsq = reinterpret_cast<double*>(smem_raw);                  // [nw][K]
-    double* blk_sumlogq = wsq + (size_t)nw * K;                          // [K]
-    uint32_t* wn = reinterpret_cast<uint32_t*>(blk_sumlogq + K);         // [nw][2K]
+    unsigned long long* wsq = reinterpret_cast<unsigned long long*>(smem_raw);   // [nw][K]
+    unsigned long long* blk_logq = wsq + (size_t)nw * K;                         // [K]
+    uint32_t* wn = reinterpret_cast<uint32_t*>(blk_logq + K);            // [nw][2K]
     float* spi = reinterpret_cast<float*>(wn + (size_t)nw * 2 * K);      // [K]
     float* slw = spi + K;                                                // [K][2][2]
     const size_t head = ((size_t)(reinterpret_cast<unsigned char*>(slw + 4 * K) - smem_raw) + 15) &
@@ -777,10 +779,10 @@ __device__ __forceinline__ void assign_chain(const ChainArgs& a, int64_t smem_by
     unsigned char* rest = smem_raw + head;
     const int64_t avail = smem_bytes - (int64_t)head;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        blk_sumlogq[k] = 0.0;
+        blk_logq[k] = 0ull;
         spi[k] = a.logpi[k];
     }
-    for (int i = threadIdx.x; i < nw * K; i += blockDim.x) wsq[i] = 0.0;
+    for (int i = threadIdx.x; i < nw * K; i += blockDim.x) wsq[i] = 0ull;
     for (int i = threadIdx.x; i < nw * 2 * K; i += blockDim.x) wn[i] = 0u;
     // eq. 8 weights: log n-bar_{k,r} and log(n-bar_{k,r} - 1); log 0 = -inf
     for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
@@ -830,9 +832,9 @@ __device__ __forceinline__ void assign_chain(const ChainArgs& a, int64_t smem_by
             }
         }
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            double v = 0.0;
+            unsigned long long v = 0ull;
             for (int w = 0; w < nw; ++w) v += wsq[w * K + k];
-            blk_sumlogq[k] = v;
+            blk_logq[k] = v;
         }
     } else {
         // large K: lanes own clusters, table in shared memory when it fits
@@ -847,11 +849,11 @@ __device__ __forceinline__ void assign_chain(const ChainArgs& a, int64_t smem_by
         __syncthreads();
         const float* L = in_smem ? sL : a.Lc;
         const int ldL = in_smem ? K : a.kmax;
-        assign_cells(a, L, ldL, K, t, blk_sumlogq);
+        assign_cells(a, L, ldL, K, t, blk_logq);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x)
-        if (blk_sumlogq[k] != 0.0) atomicAdd(&a.acc_sumlogq[k], blk_sumlogq[k]);
+        if (blk_logq[k]) atomicAdd(&a.acc_logq[k], blk_logq[k]);
 }
 
 

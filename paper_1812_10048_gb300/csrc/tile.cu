@@ -321,11 +321,12 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
     uint8_t* stage_hib = reinterpret_cast<uint8_t*>(stop + 2);      // [kMaxStages][4]
     float* spi = reinterpret_cast<float*>(stage_hib + 4 * kMaxStages);  // [K]
     float* slw = spi + kTileMaxK;                                   // [4K]
-    float* wsq = slw + 4 * kTileMaxK;                               // [4][K]
-    float* xbest = wsq + 4 * kTileMaxK;                             // [2][128] half 1 -> half 0
+    float* xbest = slw + 4 * kTileMaxK;                             // [2][128] half 1 -> half 0
     int* xc = reinterpret_cast<int*>(xbest + 256);                  // [2][128]
     float* xg0 = reinterpret_cast<float*>(xc + 256);                // [2][128]
     float* xg1 = xg0 + 256;                                         // [2][128]
+    unsigned long long* wsq =                                       // [4][K] sum log q
+        reinterpret_cast<unsigned long long*>(((reinterpret_cast<uintptr_t>(xg1 + 256)) + 7) & ~(uintptr_t)7);
 
     if (tid < 4 * kMaxStages) stage_hib[tid] = 0;
     {
@@ -626,7 +627,7 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                 slw[2 * i] = n > 0.0f ? logf(n) : -CUDART_INF_F;
                 slw[2 * i + 1] = n > 1.0f ? logf(n - 1.0f) : -CUDART_INF_F;
             }
-            for (int i = tid; i < 4 * K; i += 32 * kEpiWarps) wsq[i] = 0.0f;
+            for (int i = tid; i < 4 * K; i += 32 * kEpiWarps) wsq[i] = 0ull;
             tc::named_bar(kBarEpi, 32 * kEpiWarps);
             for (int ti = 0; ti < cnt; ++ti, ++it) {
                 const int tile = first + ti * (int)gridDim.x;
@@ -732,7 +733,7 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
                     const float mx = fmaxf(l0, l1), mn = fminf(l0, l1);
                     const float logq = (s ? l1 : l0) - (mx + log1pf(expf(mn - mx)));
                     ch.state[cell] = pack_state((uint32_t)c, s);
-                    atomicAdd(&wsq[qw * K + c], logq);
+                    atomicAdd(&wsq[qw * K + c], logq_fixed(logq));
                 }
                 tc::named_bar(kBarLabel, 128);
                 if (tid == 0) tc::mbar_arrive(&acc_empty[buf]);
@@ -742,8 +743,8 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
             tc::named_bar(kBarEpi, 32 * kEpiWarps);
             if (!dbg)
                 for (int k = tid; k < K; k += 32 * kEpiWarps) {
-                    const double v = (double)wsq[k] + wsq[K + k] + wsq[2 * K + k] + wsq[3 * K + k];
-                    if (v != 0.0) atomicAdd(&ch.acc_sumlogq[k], v);
+                    const unsigned long long v = wsq[k] + wsq[K + k] + wsq[2 * K + k] + wsq[3 * K + k];
+                    if (v) atomicAdd(&ch.acc_logq[k], v);
                 }
         }
     }

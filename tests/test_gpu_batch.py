@@ -1,9 +1,10 @@
 """Batched chains (dpmm_init_batch): one launch per kernel over all chains.
 
 Each chain of a batch must evolve exactly as the single chain with the same
-data, seed and chain id: identical labels, sub-labels, K, counters and
-(integer) statistics.  The per-cluster sum of log q is an FP64 sum of FP32
-atomics whose order is not fixed, so it is compared within rounding.
+data, seed and chain id: identical labels, sub-labels, K, counters, integer
+statistics and per-cluster sums of log q (accumulated as exact integers of
+2^-32, so the order of the additions does not matter).  Two chains of a
+batch are also checked against the FP64 oracle directly.
 """
 
 import numpy as np
@@ -48,7 +49,7 @@ def compare(P, batch, singles, D):
         ns, Ss, qs = s.stats()
         np.testing.assert_array_equal(nb, ns)
         np.testing.assert_array_equal(Sb, Ss)
-        np.testing.assert_allclose(qb, qs, rtol=1e-5, atol=1e-3)
+        np.testing.assert_array_equal(qb, qs)
 
 
 @pytest.mark.parametrize("engine", ["auto", "csr"])
@@ -103,4 +104,73 @@ def test_batch_context_rejects_per_chain_calls(P):
     v.close()                      # a view: the batch keeps the chain
     labels, K = batch.chain(1).labels()
     assert labels.shape == (ds[1][3],) and K >= 1
+    batch.close()
+
+
+@pytest.mark.parametrize("engine", ["auto", "csr"])
+def test_two_batch_chains_match_the_oracle(P, engine):
+    """Chains 0 and 2 of a four-chain batch, started from oracle states: one
+    batched sweep gives every cell the FP64 oracle's label and sub-label from
+    the parameters the batch drew (except near-ties), with exact statistics;
+    one batched split and one merge move from the GPU's state give the
+    oracle's log H (FP64, 1e-10) and the oracle's moves exactly."""
+    from oracle.sampler import Sampler as OracleSampler, sufficient_stats
+    from .parity import bf16_bound, check_assign, decisions_from_oracle, fp32_bound
+    eng = {"auto": P.ENGINE_AUTO, "csr": P.ENGINE_CSR_FP32}[engine]
+    ds = datasets()
+    D = 300
+    batch = P.BatchSampler(ds, D, 1.0, 0.5, kmax=32, seed=21, chain_id=0, engine=eng)
+    oracles = {}
+    for b in (0, 2):
+        ip, ix, dt, N = ds[b]
+        o = OracleSampler(ip, ix, dt, N, D, 1.0, 0.5, seed=21, chain_id=b, kmax=32)
+        for _ in range(3):
+            o.sweep()
+            o.split_merge(0)
+        P.dpmm_set_state(batch.chain(b).ctx, o.labels, o.sub, o.K, o.t, o.m, o.sumlogq)
+        oracles[b] = o
+    batch.sweep(1)
+    for b, o in oracles.items():
+        v = batch.chain(b)
+        K0, t0 = o.K, o.t
+        labels, sub, K, t, m = v.get_state()
+        assert t == t0 + 1
+        logpi32, logtheta32 = P.dpmm_get_params(v.ctx, K0, D)
+        logpi, logtheta = logpi32.astype(np.float64), logtheta32.astype(np.float64)
+        X = o.X.astype(np.float64)
+        bound = bf16_bound(X, logtheta) if engine == "auto" else fp32_bound(X, logtheta)
+        ref = decisions_from_oracle(o, logpi, logtheta, bound)
+        nsub, Ssub, sq = v.stats()
+        check_assign(ref, K0, K, labels, sub, sq, o.seed, o.chain_id, t0)
+        on, oS = sufficient_stats(o.X, labels, sub, K)
+        np.testing.assert_array_equal(nsub, on)
+        np.testing.assert_array_equal(Ssub, oS)
+        o.set_state(labels, sub, K, t, m, sq)
+    for mode in (1, 2):
+        P.dpmm_split_merge(batch.ctx, mode, want_count=False)
+        for b, o in oracles.items():
+            v = batch.chain(b)
+            chain, log_h, pair_ab = P.dpmm_debug_moves(v.ctx, 32)
+            assert chain == mode
+            if mode == 1:
+                ref = o.split_log_hastings()
+                assert np.array_equal(np.isnan(log_h), np.isnan(ref))
+                ok = ~np.isnan(ref)
+                np.testing.assert_allclose(log_h[ok], ref[ok], rtol=1e-10, atol=1e-8)
+            else:
+                pairs = o.merge_pairs()
+                np.testing.assert_array_equal(pair_ab,
+                                              np.array(pairs, dtype=np.int32).reshape(-1, 2))
+                np.testing.assert_allclose(log_h, o.merge_log_hastings(pairs), rtol=1e-10,
+                                           atol=1e-8)
+            o.split_merge(mode)
+            labels, sub, K, t, m = v.get_state()
+            assert (K, m) == (o.K, o.m)
+            np.testing.assert_array_equal(labels, o.labels)
+            np.testing.assert_array_equal(sub, o.sub)
+            nsub, Ssub, sq = v.stats()
+            on, oS = o.stats()
+            np.testing.assert_array_equal(nsub, on)
+            np.testing.assert_array_equal(Ssub, oS)
+            np.testing.assert_allclose(sq, o.sumlogq, rtol=1e-9, atol=1e-9)
     batch.close()
