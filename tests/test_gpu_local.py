@@ -76,10 +76,15 @@ def test_one_local_iteration_matches_oracle(P, tiny, engine, j):
     on, oS = sufficient_stats(o.X, labels, sub, K)
     np.testing.assert_array_equal(nsub, on)
     np.testing.assert_array_equal(Ssub, oS)
-    ok = ~mism
-    ref_q = np.bincount(labels[ok], weights=exp_logq[ok], minlength=K)
-    if not mism.any():
-        np.testing.assert_allclose(sumlogq, ref_q, rtol=1e-3, atol=1e-2)
+    # per cluster without a near-tie flip: the FP64 sum within the summed
+    # per-cell bound of the FP32 sub-scores and logarithms
+    tol_i = 1e-5 * np.abs(lik).max(axis=1) + 1e-3 + 1e-6 * np.abs(exp_logq) + 1e-6
+    dirty = np.bincount(labels[mism], minlength=K) > 0
+    ref_q = np.bincount(labels, weights=exp_logq, minlength=K)
+    tol = np.bincount(labels, weights=tol_i, minlength=K)
+    err = np.abs(sumlogq - ref_q)
+    assert np.all(err[~dirty] <= tol[~dirty]), (err[~dirty], tol[~dirty])
+    assert (~dirty).sum() >= 1
 
 
 def test_local_iterations_chain_keeps_statistics_exact(P, tiny):
