@@ -369,9 +369,11 @@ int dpmm_eb_step(dpmm_ctx* ctx, double eta_alpha, double eta_beta, double max_st
  * latency-critical code that must not call cudaMalloc / cudaFree, which
  * synchronise the device).  The paper has no counterpart: it is a property of
  * this library's interface, not of the method.
- *   indptr, indices, data, labels: DEVICE pointers (CSR as in dpmm_init, labels
- *     int32[N] in [0, K)); log_beta float[D], logml double, grad_log_alpha
- *     double and grad_log_beta float[D] may be host or device pointers.
+ *   indptr, indices, data, labels: DEVICE pointers of the current device (CSR
+ *     as in dpmm_init, labels int32[N] in [0, K)); host memory or another
+ *     GPU's memory returns DPMM_EINVAL; log_beta float[D], logml double,
+ *     grad_log_alpha double and grad_log_beta float[D] may be host or device
+ *     pointers.
  *   Limits: 1 <= D <= 65536, 1 <= K <= 1024, K * D <= 1048576; larger sizes
  *     return DPMM_EINVAL without touching the GPU.
  * Scratch lives in a static device array of about 4.6 MB that every GPU loading
@@ -381,7 +383,8 @@ int dpmm_eb_step(dpmm_ctx* ctx, double eta_alpha, double eta_beta, double max_st
  * GPU work overlaps race and must be serialised by the caller.  The first call
  * on a device looks up the array's device address (once per device); make that
  * first call before any stream capture.  Malformed CSR rows, columns or labels
- * are skipped on the device and reported as DPMM_EINVAL.  Runs on `stream`
+ * are skipped on the device and reported as DPMM_EINVAL; a cluster whose
+ * count of one gene reaches 2^32 gives DPMM_EOVERFLOW.  Runs on `stream`
  * (NULL: the legacy default stream) and synchronises it before returning.
  */
 int dpmm_logml_grad_noalloc(const int32_t* indptr, const int32_t* indices, const int32_t* data,

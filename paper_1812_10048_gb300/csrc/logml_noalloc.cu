@@ -66,19 +66,24 @@ cudaError_t scratch_base(int dev, unsigned char** base) {
     return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// True for device memory of device `dev` (the current one) and for managed
+// memory; false for host memory and for another GPU's memory, which the
+// kernels could reach only through peer access.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) ||
+           a.type == cudaMemoryTypeManaged;
 }
 
 // n_k, S_ku, T_k of the labelled cells, like k_lml_stats, but the arrays come
 // from a caller that was not validated on the host: rows with a decreasing
 // indptr or one beyond indptr[N], columns outside [0, D), negative counts and
-// labels outside [0, K) are skipped and reported in *flag.
+// labels outside [0, K) are skipped and reported in *flag (bit 0: row or
+// label, bit 1: entry); a gene total S_ku that wraps 2^32 sets bit 2.
 __global__ void k_lml_stats_checked(const int32_t* __restrict__ indptr,
                                     const int32_t* __restrict__ cols,
                                     const int32_t* __restrict__ counts,
@@ -97,7 +102,7 @@ __global__ void k_lml_stats_checked(const int32_t* __restrict__ indptr,
             continue;
         }
         unsigned long long rowsum = 0;
-        bool bad = false;
+        bool bad = false, wrap = false;
         for (int64_t e = beg + lane; e < end; e += 32) {
             const int32_t u = cols[e], x = counts[e];
             if (u < 0 || u >= D || x < 0) {
@@ -105,11 +110,13 @@ __global__ void k_lml_stats_checked(const int32_t* __restrict__ indptr,
                 continue;
             }
             if (x) {
-                atomicAdd(&S[(size_t)k * D + u], (uint32_t)x);
+                const uint32_t old = atomicAdd(&S[(size_t)k * D + u], (uint32_t)x);
+                if (old + (uint32_t)x < old) wrap = true;
                 rowsum += (unsigned long long)x;
             }
         }
         if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(flag, 2u);
+        if (__any_sync(0xFFFFFFFFu, wrap) && lane == 0) atomicOr(flag, 4u);
         rowsum = warp_sum(rowsum);
         if (lane == 0) {
             atomicAdd(&n[k], 1u);
@@ -135,13 +142,15 @@ extern "C" int dpmm_logml_grad_noalloc(const int32_t* indptr, const int32_t* ind
         return noalloc_fail(DPMM_EINVAL,
                             "dpmm_logml_grad_noalloc: need 1 <= D <= 65536, 1 <= K <= 1024 and "
                             "K * D <= 1048576 (size of the static scratch)");
-    if (!on_device(indptr) || !on_device(indices) || !on_device(data) || !on_device(labels))
-        return noalloc_fail(DPMM_EINVAL,
-                            "dpmm_logml_grad_noalloc: indptr, indices, data and labels must be "
-                            "device pointers");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess && dev >= kMaxDevices) e = cudaErrorInvalidDevice;
+    if (e != cudaSuccess) return noalloc_fail(DPMM_ECUDA, cudaGetErrorString(e));
+    if (!on_device(indptr, dev) || !on_device(indices, dev) || !on_device(data, dev) ||
+        !on_device(labels, dev))
+        return noalloc_fail(DPMM_EINVAL,
+                            "dpmm_logml_grad_noalloc: indptr, indices, data and labels must be "
+                            "device pointers of the current device");
+    if (dev >= kMaxDevices) e = cudaErrorInvalidDevice;
     unsigned char* base = nullptr;
     if (e == cudaSuccess) e = scratch_base(dev, &base);
     LmlPlan p;
@@ -188,6 +197,9 @@ extern "C" int dpmm_logml_grad_noalloc(const int32_t* indptr, const int32_t* ind
     if (!e) e = cudaMemcpyAsync(&hflag, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, p.stream);
     if (!e) e = cudaStreamSynchronize(p.stream);
     if (e != cudaSuccess) return noalloc_fail(DPMM_ECUDA, cudaGetErrorString(e));
+    if (hflag & 4u)
+        return noalloc_fail(DPMM_EOVERFLOW,
+                            "dpmm_logml_grad_noalloc: a cluster's count of one gene reaches 2^32");
     if (hflag)
         return noalloc_fail(DPMM_EINVAL,
                             (hflag & 1u) ? "dpmm_logml_grad_noalloc: label outside [0, K) or "
