@@ -39,7 +39,7 @@ extern "C" {
 #define DPMM_ETIMEOUT -6    /* a bounded device-side wait gave up */
 #define DPMM_ESTATE -7      /* call not valid in the context's current state */
 
-#define DPMM_ENGINE_AUTO 0      /* pick per sweep from K and the row lengths */
+#define DPMM_ENGINE_AUTO 0      /* pick per sweep from K and the count density (measured) */
 #define DPMM_ENGINE_CSR_FP32 1  /* warp-per-cell CSR contraction, FP32 */
 #define DPMM_ENGINE_TILE_BF16 2 /* dense 128-cell tiles on tcgen05, BF16 hi/lo */
 
@@ -179,6 +179,15 @@ int dpmm_phase_times(dpmm_ctx* ctx, float* ms, int32_t n);
  * Synchronises.
  */
 int dpmm_plans_applied(dpmm_ctx* ctx, int64_t* n);
+
+/*
+ * Label engine of the chain's latest sweep: *tile_used = 1 for the dense-tile
+ * tensor-core engine, 0 for the FP32 CSR engine.  With DPMM_ENGINE_AUTO the
+ * tile engine labels 1 <= K <= 40 clusters, except K <= 2 on count matrices of
+ * density 12% or more, where the CSR engine was measured faster.
+ * Instrumentation only (the paper has no counterpart).  Synchronises.
+ */
+int dpmm_debug_engine(dpmm_ctx* ctx, int32_t* tile_used);
 
 /* Block until all work enqueued on the context's stream is done. */
 int dpmm_sync(dpmm_ctx* ctx);

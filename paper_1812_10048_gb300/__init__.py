@@ -17,7 +17,8 @@ from ._lib import (DpmmError, ENGINE_AUTO, ENGINE_CSR_FP32, ENGINE_TILE_BF16, ch
 __all__ = [
     "DpmmError", "Sampler", "LogML", "dpmm_default_opts", "dpmm_init", "dpmm_free", "dpmm_sweep",
     "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
-    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_logml_grad", "dpmm_set_hyper",
+    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_debug_engine", "dpmm_logml_grad",
+    "dpmm_set_hyper",
     "dpmm_eb_step", "empirical_bayes", "dpmm_init_batch",
     "dpmm_chain", "BatchSampler", "dpmm_get_state",
     "dpmm_set_state", "dpmm_get_stats", "dpmm_draw_params", "dpmm_local_gibbs", "dpmm_assign", "dpmm_debug_tile_layout", "dpmm_get_params",
@@ -111,6 +112,13 @@ def dpmm_plans_applied(ctx):
     n = ctypes.c_int64(0)
     check(lib().dpmm_plans_applied(ctx, ctypes.byref(n)))
     return n.value
+
+
+def dpmm_debug_engine(ctx):
+    """1 if the chain's latest sweep used the dense-tile engine, else 0."""
+    v = ctypes.c_int32(0)
+    check(lib().dpmm_debug_engine(ctx, ctypes.byref(v)))
+    return int(v.value)
 
 
 def dpmm_logml_grad(ctx, log_alpha, log_beta, labels=None, K=0, grad=True):

@@ -48,6 +48,7 @@ SIGNATURES = {
     "dpmm_labels": (ctypes.c_int, [_P, _P, _P]),
     "dpmm_sync": (ctypes.c_int, [_P]),
     "dpmm_plans_applied": (ctypes.c_int, [_P, _P]),
+    "dpmm_debug_engine": (ctypes.c_int, [_P, _P]),
     "dpmm_init_batch": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "dpmm_chain": (ctypes.c_int, [_P, _I32, _P]),
     "dpmm_logml_grad": (ctypes.c_int, [_P, _P, _I32, ctypes.c_double, _P, _P, _P, _P]),

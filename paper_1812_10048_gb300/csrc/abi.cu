@@ -158,6 +158,14 @@ ChainArgs dpmm::chain_args(const Ctx& c) {
     a.tile_C = c.tile_C;
     a.tile_T = c.tile_T;
     a.tile_Lslot = c.tile_Lslot;
+    // one chain: a statistics item per block of the launch (tile groups of
+    // the gene chunks, see k_stats_tile)
+    a.stat_groups = c.tile_enabled ? std::max(1, std::min(c.tile_T, tile_stat_groups(c))) : 0;
+    // engine choice by measured density (constants in common.cuh); the tile
+    // engine forced by the caller labels every 1 <= K <= 40
+    const double density = (c.N > 0 && c.D > 0) ? (double)c.nnz / ((double)c.N * c.D) : 0.0;
+    a.tile_kmin = (c.opts.engine == DPMM_ENGINE_AUTO && density >= kTileDenseCut) ? kTileDenseKmin
+                                                                                   : 1;
     a.tile_ent = c.tile_ent;
     a.tile_ptr = c.tile_ptr;
     a.noise = c.noise;
@@ -606,6 +614,7 @@ int dpmm_init_batch(dpmm_ctx** out, int32_t B, const int32_t* const* indptr,
     c.assign_smem = m0.assign_smem;
     c.stats_blocks = m0.stats_blocks;
     c.stats_smem = m0.stats_smem;
+    c.local_smem = m0.local_smem;
     c.apply_blocks = m0.apply_blocks;
     c.apply_smem = m0.apply_smem;
     c.tile_C = m0.tile_C;
@@ -621,6 +630,22 @@ int dpmm_init_batch(dpmm_ctx** out, int32_t B, const int32_t* const* indptr,
         if (m->c.tile_enabled) c.tile_C = m->c.tile_C;
         c.max_Lslot = std::max(c.max_Lslot, m->c.tile_Lslot);
         tab.push_back(*m->c.h_chain0);
+    }
+    {
+        // statistics items of the batch: each chain's gene chunks split into
+        // tile groups of about S tiles, S chosen so that the whole batch makes
+        // about two items per block of the launch (the chains are counted side
+        // by side; a small chain is one item per chunk)
+        int64_t sumT = 0;
+        for (const ChainArgs& a : tab) sumT += a.tile_enabled ? a.tile_T : 0;
+        const int C = std::max(1, c.tile_C);
+        const int nt = std::max(1, (2 * c.num_sms) / C);   // tile_stat_groups of a batch
+        const int64_t S = std::max<int64_t>(1, (sumT * C + 2 * (int64_t)nt * C - 1) /
+                                                   (2 * (int64_t)nt * C));
+        for (ChainArgs& a : tab)
+            if (a.tile_enabled)
+                a.stat_groups = (int32_t)std::max<int64_t>(
+                    1, std::min<int64_t>({(a.tile_T + S - 1) / S, (int64_t)a.tile_T, (int64_t)nt}));
     }
     cudaError_t e;
     if ((e = dalloc(&c.gbar, 1)) || (e = dalloc(&c.d_chains, (size_t)B)) ||
@@ -756,6 +781,15 @@ int dpmm_plans_applied(dpmm_ctx* ctx, int64_t* n) {
         if ((rc = sync_scalars(m->c))) return rc;
         *n += (int64_t)m->c.sc_host->n_apply;
     }
+    return DPMM_OK;
+}
+
+int dpmm_debug_engine(dpmm_ctx* ctx, int32_t* tile_used) {
+    CHECK_CHAIN(ctx);
+    if (!tile_used) return fail(DPMM_EINVAL, "tile_used is NULL");
+    int rc = sync_scalars(ctx->c);
+    if (rc) return rc;
+    *tile_used = ctx->c.sc_host->tile_used;
     return DPMM_OK;
 }
 

@@ -89,6 +89,14 @@ struct DevScalars {
 
 // The dense-tile engine serves 1 <= K <= kTileMaxK.
 constexpr int kTileMaxK = 40;
+// Engine choice measured on one GB300 (68,000 x 1,000, one sweep from a fixed
+// K-cluster state, densities 5.7% - 22.8%, K = 2 .. 40): the dense-tile engine
+// is faster for every K >= 5 at every density and for K <= 2 below ~12%
+// density; at K <= 2 and density >= kTileDenseCut the CSR engine is (up to 10%)
+// faster.  So the automatic choice takes the tile engine for K >= 3 always and
+// for K <= 2 only below that density.
+constexpr double kTileDenseCut = 0.12;
+constexpr int kTileDenseKmin = 3;
 
 // ---------------------------------------------------------------------------
 // The context (owned by the C ABI layer).
@@ -157,6 +165,7 @@ struct Ctx {
     int stats_blocks = 0;
     size_t assign_smem = 0;
     size_t stats_smem = 0;
+    size_t local_smem = 0;          // local Gibbs sub-label kernel (theta-bar table)
 
     // dense-tile engine: counts blocked by (128-cell tile, 64-gene chunk)
     bool tile_enabled = false;
@@ -359,6 +368,8 @@ struct ChainArgs {
     int32_t* move_ticket;
     // dense-tile engine (tile_enabled = 0: not built for this chain)
     int32_t tile_enabled, tile_C, tile_T, tile_Lslot;
+    int32_t stat_groups;  // tile groups per gene chunk in the statistics launch
+    int32_t tile_kmin;    // smallest K the dense-tile engine labels (engine choice)
     uint32_t* tile_ent;
     int32_t* tile_ptr;
     float* noise;
@@ -480,7 +491,7 @@ __device__ __forceinline__ void stats_cells(const Csr& csr, const uint32_t* __re
 // would draw itself; it reads them before its accumulators are ready.
 __device__ __forceinline__ void noise_cells(const ChainArgs& ch, int64_t first, int64_t stride) {
     const int K = ch.sc->K;
-    if (!ch.tile_enabled || K < 1 || K > kTileMaxK) return;
+    if (!ch.tile_enabled || K < ch.tile_kmin || K > kTileMaxK) return;
     const uint32_t t = ch.sc->t;
     const int64_t N = ch.N;
     float* __restrict__ out = ch.noise;

@@ -742,9 +742,13 @@ k_plan_apply(const __grid_constant__ Tab tab, int32_t kind, GridBar* bar, int64_
         volatile DevScalars* vs = ch.sc;
         if (!vs->apply) continue;
         const int Kn = vs->K_new;
-        stats_cells(ch.csr, ch.state, ch.reinit, ch.nsub, ch.Ssub, ch.N, ch.D, Kn, spriv,
-                    priv_cap);
-        __syncthreads();
+        // (a plan that re-initialises no cluster has nothing to recount: every
+        // block skips the clear and flush of its private counters)
+        if (vs->any_reinit) {
+            stats_cells(ch.csr, ch.state, ch.reinit, ch.nsub, ch.Ssub, ch.N, ch.D, Kn, spriv,
+                        priv_cap);
+            __syncthreads();
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ch.sc->K = Kn;
             if (compact) ch.sc->t += 1u;

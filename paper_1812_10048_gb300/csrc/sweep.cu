@@ -51,9 +51,10 @@ __device__ __forceinline__ float block_reduce_sum(float v, float* red) {
 }
 
 // Labelling engine of this sweep: the dense-tile engine when it is built and
-// 1 <= K <= kTileMaxK, else the CSR engine.
-__device__ __forceinline__ void select_engine(DevScalars* sc, int K, int32_t tile_enabled) {
-    sc->tile_used = tile_enabled && K >= 1 && K <= kTileMaxK;
+// tile_kmin <= K <= kTileMaxK, else the CSR engine (tile_kmin from the
+// chain's measured density, see chain_args).
+__device__ __forceinline__ void select_engine(DevScalars* sc, int K, const ChainArgs& ch) {
+    sc->tile_used = ch.tile_enabled && K >= ch.tile_kmin && K <= kTileMaxK;
 }
 
 // The sweep's n-bar and sum log q accumulators start at zero (they are added
@@ -70,7 +71,7 @@ __global__ void k_select_engine(const __grid_constant__ Tab tab) {
         const ChainArgs& ch = tab[b];
         const int K = ch.sc->K;
         __syncthreads();
-        if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
+        if (threadIdx.x == 0) select_engine(ch.sc, K, ch);
         clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
     }
     fill_noise(tab, (int64_t)gridDim.x, (int64_t)blockIdx.x);
@@ -181,7 +182,7 @@ k_draw_params(const __grid_constant__ Tab tab) {
         for (int64_t id = first; id < base + rows; id += gridDim.x) {
             const int row = (int)(id - base);
             if (row == 0) {
-                if (threadIdx.x == 0) select_engine(ch.sc, K, ch.tile_enabled);
+                if (threadIdx.x == 0) select_engine(ch.sc, K, ch);
                 clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
             }
             draw_row(ch, K, open, TAG_THETA, t, row, red, lgc);
@@ -309,22 +310,26 @@ __device__ __forceinline__ uint32_t draw_sublabel(const ChainArgs& a, int64_t ce
 
 // Local Gibbs iteration, second half: labels held, every cell's sub-label
 // drawn from eq. 8 under the new theta-bar (weights n-bar_{r, not i} from the
-// current counts).  LANES lanes per cell (chosen from the mean row length),
-// each lane with eight row entries in flight; the cells of all chains form one index range split into contiguous block ranges (a batch of
-// small chains keeps every warp busy), and the next cell's state and row
-// bounds are loaded before the current cell's contraction.  log q_i is summed
-// per (chain, cluster) in the block (FP64; the first kLocalSlots chains of
-// the block's range), then into the accumulator.  A chain with the blocked
-// copy also has its main S-bar rows cleared here (the tile statistics kernel
+// current counts).  The chains of the table are taken in turn.  A chain's
+// cells are dealt round-robin to groups of LANES lanes (LANES chosen from the
+// mean row length); the lanes of a group keep eight row entries each in
+// flight, and the group's first lane draws the cell's sub-label and log q_i.
+// The chain's theta-bar pairs of its K clusters are staged in shared memory
+// as a [D][K] table when they fit (by the blocks that hold cells of the
+// chain), so each gather is a shared-memory load instead of an 8-byte load
+// 2 KB away from its neighbour in the gene-major global table.  A cell's sums
+// depend only on its row, so a chain gives the same sub-labels alone or in a
+// batch.  log q_i is summed per cluster in the block (exact integer units,
+// see logq_fixed), then into the accumulator.  A chain with the blocked copy
+// also has its main S-bar rows cleared here (the tile statistics kernel
 // recounts into them; nothing reads them after the theta-bar draw).
-constexpr int kLocalThreads = 256;
-constexpr int kLocalSlots = 2;
+constexpr int kLocalThreads = 1024;
 constexpr int kLocalInFlight = 8;
 
 template <int LANES>
 __device__ __forceinline__ float2 sub_scores_group(const Csr& csr, int64_t beg, int64_t end,
-                                                   const float2* __restrict__ Ls2, int kmax,
-                                                   int c, int sl, unsigned gmask) {
+                                                   const float2* __restrict__ L, int ld, int c,
+                                                   int sl, unsigned gmask) {
     float t0 = 0.0f, t1 = 0.0f;
     for (int64_t e0 = beg + sl; e0 < end; e0 += kLocalInFlight * LANES) {
         int32_t u[kLocalInFlight], x[kLocalInFlight];
@@ -337,7 +342,7 @@ __device__ __forceinline__ float2 sub_scores_group(const Csr& csr, int64_t beg, 
         float2 l[kLocalInFlight];
 #pragma unroll
         for (int q = 0; q < kLocalInFlight; ++q)
-            l[q] = x[q] ? __ldg(Ls2 + (size_t)u[q] * kmax + c) : make_float2(0.0f, 0.0f);
+            l[q] = x[q] ? L[(int64_t)u[q] * ld + c] : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int q = 0; q < kLocalInFlight; ++q) {
             t0 = fmaf((float)x[q], l[q].x, t0);
@@ -353,90 +358,96 @@ __device__ __forceinline__ float2 sub_scores_group(const Csr& csr, int64_t beg, 
 }
 
 template <int LANES, class Tab>
-__global__ void __launch_bounds__(kLocalThreads)
-k_local_sub(const __grid_constant__ Tab tab, int32_t j) {
-    __shared__ unsigned long long bsq[kLocalSlots][kMaxKmax];
+__global__ void __launch_bounds__(kLocalThreads, 1)
+k_local_sub(const __grid_constant__ Tab tab, int32_t j, int64_t smem_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_local[];
+    unsigned long long* bsq = reinterpret_cast<unsigned long long*>(smem_local);   // [kMaxKmax]
+    float2* sL = reinterpret_cast<float2*>(smem_local + 8 * kMaxKmax);             // [D][K]
+    if (smem_bytes < (int64_t)8 * kMaxKmax) {
+        // launched without room for the per-cluster sums: report, touch nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&tab[0].sc->error, DPMM_ECAPACITY);
+        return;
+    }
     const uint32_t tag = kLocalTag0 + 2u * (uint32_t)(j - 1) + 1u;
     const int lane = threadIdx.x & 31;
     const int sl = lane % LANES;                                // lane within the cell group
-    const int grp = (int)(threadIdx.x / LANES);
-    const int ngrp = (int)(blockDim.x / LANES);
-    const unsigned gmask =
-        (LANES == 32 ? 0xFFFFFFFFu : ((1u << LANES) - 1u)) << (lane - sl);
-    int64_t total = 0;
+    const unsigned gmask = (LANES == 32 ? 0xFFFFFFFFu : ((1u << LANES) - 1u)) << (lane - sl);
+    const int64_t ngb = blockDim.x / LANES;                     // groups per block
+    const int64_t G = (int64_t)gridDim.x * ngb;
+    const int64_t gid = (int64_t)blockIdx.x * ngb + threadIdx.x / LANES;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
         if (ch.tile_enabled)
-            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-                 i < (int64_t)2 * ch.sc->K * ch.D; i += (int64_t)gridDim.x * blockDim.x)
-                ch.Ssub[i] = 0u;
-        total += ch.N;
+            for (int64_t i = tid; i < (int64_t)2 * ch.sc->K * ch.D; i += nthr) ch.Ssub[i] = 0u;
     }
-    for (int i = threadIdx.x; i < kLocalSlots * kMaxKmax; i += blockDim.x) (&bsq[0][0])[i] = 0ull;
-    __syncthreads();
-    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-    const int64_t g0 = min(total, (int64_t)blockIdx.x * per), g1 = min(total, g0 + per);
-    int b0 = 0;
-    int64_t base0 = 0;
-    while (b0 + 1 < tab.n() && g0 >= base0 + tab[b0].N) base0 += tab[b0++].N;
-    int b = b0;
-    int64_t base = base0;
-    int64_t g = g0 + grp;
-    uint32_t st = 0u;
-    int64_t beg = 0, end = 0;
-    if (g < g1) {
-        while (g >= base + tab[b].N) base += tab[b++].N;
+    int64_t base = 0;
+    for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
-        st = ch.state[g - base];
-        beg = ch.csr.indptr[g - base];
-        end = ch.csr.indptr[g - base + 1];
-    }
-    while (g < g1) {
-        const ChainArgs& ch = tab[b];
-        const int64_t cell = g - base;
-        const int c = (int)state_label(st);
-        uint32_t n0 = 0u, n1 = 0u;
-        if (sl == 0) {
-            n0 = ch.nsub[2 * c];
-            n1 = ch.nsub[2 * c + 1];
+        const int K = ch.sc->K, D = ch.D, kmax = ch.kmax;
+        const int64_t N = ch.N;
+        const uint32_t t = ch.sc->t - 1u;
+        const int64_t first = base + ((gid - base) % G + G) % G;
+        const bool mine = first < base + N;
+        if (!__syncthreads_or(mine ? 1 : 0)) {
+            base += N;
+            continue;
         }
-        const int64_t gn = g + ngrp;
-        int bn = b;
-        int64_t basen = base, begn = 0, endn = 0;
-        uint32_t stn = 0u;
-        if (gn < g1) {
-            while (gn >= basen + tab[bn].N) basen += tab[bn++].N;
-            const ChainArgs& cn = tab[bn];
-            stn = cn.state[gn - basen];
-            begn = cn.csr.indptr[gn - basen];
-            endn = cn.csr.indptr[gn - basen + 1];
-        }
-        const float2 lik = sub_scores_group<LANES>(
-            ch.csr, beg, end, reinterpret_cast<const float2*>(ch.Ls), ch.kmax, c, sl, gmask);
-        if (sl == 0) {
-            float logq;
-            const uint32_t s = draw_sublabel_n(ch.st, cell, c, st, n0, n1, lik, tag,
-                                               ch.sc->t - 1u, &logq);
-            ch.state[cell] = pack_state((uint32_t)c, s);
-            const unsigned long long q = logq_fixed(logq);
-            if (q) {
-                if (b - b0 < kLocalSlots) atomicAdd(&bsq[b - b0][c], q);
-                else atomicAdd(&ch.acc_logq[c], q);
+        const bool staged = (int64_t)8 * kMaxKmax + (int64_t)D * K * 8 <= smem_bytes;
+        const float2* __restrict__ Ls2 = reinterpret_cast<const float2*>(ch.Ls);
+        for (int i = threadIdx.x; i < K; i += blockDim.x) bsq[i] = 0ull;
+        if (staged)
+            for (int64_t i = threadIdx.x; i < (int64_t)D * K; i += blockDim.x) {
+                const int64_t u = i / K, k = i - u * K;
+                sL[i] = __ldg(Ls2 + u * kmax + k);
             }
+        __syncthreads();
+        const float2* L = staged ? sL : Ls2;
+        const int ld = staged ? K : kmax;
+        int64_t cell = first - base;
+        uint32_t st = 0u;
+        int64_t beg = 0, end = 0;
+        if (cell < N) {
+            st = ch.state[cell];
+            beg = ch.csr.indptr[cell];
+            end = ch.csr.indptr[cell + 1];
         }
-        g = gn;
-        b = bn;
-        base = basen;
-        st = stn;
-        beg = begn;
-        end = endn;
-    }
-    __syncthreads();
-    for (int q = 0; q < kLocalSlots && b0 + q < tab.n(); ++q) {
-        const ChainArgs& ch = tab[b0 + q];
-        const int K = ch.sc->K;
+        while (cell < N) {
+            const int c = (int)state_label(st);
+            uint32_t n0 = 0u, n1 = 0u;
+            if (sl == 0) {
+                n0 = ch.nsub[2 * c];
+                n1 = ch.nsub[2 * c + 1];
+            }
+            // the next cell's state and row bounds load while this one is contracted
+            const int64_t cn = cell + G;
+            uint32_t stn = 0u;
+            int64_t begn = 0, endn = 0;
+            if (cn < N) {
+                stn = ch.state[cn];
+                begn = ch.csr.indptr[cn];
+                endn = ch.csr.indptr[cn + 1];
+            }
+            const float2 lik = sub_scores_group<LANES>(ch.csr, beg, end, L, ld, c, sl, gmask);
+            if (sl == 0) {
+                float logq;
+                const uint32_t s = draw_sublabel_n(ch.st, cell, c, st, n0, n1, lik, tag, t,
+                                                   &logq);
+                ch.state[cell] = pack_state((uint32_t)c, s);
+                const unsigned long long q = logq_fixed(logq);
+                if (q) atomicAdd(&bsq[c], q);
+            }
+            cell = cn;
+            st = stn;
+            beg = begn;
+            end = endn;
+        }
+        __syncthreads();
         for (int k = threadIdx.x; k < K; k += blockDim.x)
-            if (bsq[q][k]) atomicAdd(&ch.acc_logq[k], bsq[q][k]);
+            if (bsq[k]) atomicAdd(&ch.acc_logq[k], bsq[k]);
+        __syncthreads();
+        base += N;
     }
 }
 
@@ -798,7 +809,9 @@ __device__ __forceinline__ void assign_chain(const ChainArgs& a, int64_t smem_by
         float* sLc = reinterpret_cast<float*>(rest);
         const bool sub_in = bytes_c + bytes_s <= avail;
         float2* sLs = reinterpret_cast<float2*>(rest + bytes_c);
-        const bool fused = sub_in && bytes_c + bytes_s + bytes_st <= avail;
+        // a chain with the blocked copy is counted by the tile statistics
+        // kernel whichever engine labels it: no fused statistics then
+        const bool fused = sub_in && !a.tile_enabled && bytes_c + bytes_s + bytes_st <= avail;
         uint32_t* sS = fused ? reinterpret_cast<uint32_t*>(rest + bytes_c + bytes_s) : nullptr;
         for (int64_t i = threadIdx.x; i < (int64_t)D * Kp; i += blockDim.x) {
             const int64_t u = i / Kp, k = i - u * Kp;
@@ -996,6 +1009,17 @@ cudaError_t configure_launches(Ctx& c) {
         (e = cudaFuncSetAttribute(k_stats<TabP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)c.stats_smem)))
         return e;
+    c.local_smem = (size_t)optin;
+    {
+        const void* fns[8] = {(const void*)k_local_sub<4, TabV>, (const void*)k_local_sub<8, TabV>,
+                              (const void*)k_local_sub<16, TabV>, (const void*)k_local_sub<32, TabV>,
+                              (const void*)k_local_sub<4, TabP>, (const void*)k_local_sub<8, TabP>,
+                              (const void*)k_local_sub<16, TabP>, (const void*)k_local_sub<32, TabP>};
+        for (const void* f : fns)
+            if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)c.local_smem)))
+                return e;
+    }
     c.assign_blocks = c.num_sms;
     c.stats_blocks = c.num_sms;
     return cudaSuccess;
@@ -1024,15 +1048,16 @@ cudaError_t launch_local_iteration(Ctx& c, int32_t j) {
         // lanes per cell: the power of two nearest below mean row length /
         // kLocalInFlight, within [4, 32] (one or two passes per lane)
         const int64_t mean = c.mean_row;
-        const dim3 grid(4 * c.num_sms);
+        const dim3 grid(c.num_sms);
+        const int64_t sm = (int64_t)c.local_smem;
         if (mean < 8 * kLocalInFlight)
-            k_local_sub<4><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+            k_local_sub<4><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
         else if (mean < 16 * kLocalInFlight)
-            k_local_sub<8><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+            k_local_sub<8><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
         else if (mean < 32 * kLocalInFlight)
-            k_local_sub<16><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+            k_local_sub<16><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
         else
-            k_local_sub<32><<<grid, kLocalThreads, 0, c.stream>>>(tab, j);
+            k_local_sub<32><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
         if (!c.tile_enabled)
             k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
                 tab, (int64_t)(c.stats_smem / sizeof(uint32_t)), 2);

@@ -803,8 +803,11 @@ __device__ __forceinline__ void count_segments(T_* priv, int ld, uint32_t* pn, u
     }
 }
 
+// Item (chunk c, tile group tg of nt) of a chain: tiles tg, tg + nt, ... of
+// gene chunk c, counted into the block's private counters and flushed.
 __device__ __forceinline__ void
-stats_tile_chain(const ChainArgs& ch, uint32_t (*cache)[128], uint32_t* priv, uint32_t* pn) {
+stats_tile_item(const ChainArgs& ch, int c, int tg, int nt, uint32_t (*cache)[128],
+                uint32_t* priv, uint32_t* pn) {
     const DevScalars* sc = ch.sc;
     const uint32_t* __restrict__ state = ch.state;
     const uint32_t* __restrict__ ent = ch.tile_ent;
@@ -815,8 +818,6 @@ stats_tile_chain(const ChainArgs& ch, uint32_t (*cache)[128], uint32_t* priv, ui
     uint32_t* __restrict__ Ssub = ch.Ssub;
     const int K = sc->K;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int c = blockIdx.x % C, tg = blockIdx.x / C, nt = gridDim.x / C;
-    if (tg >= nt || tg >= T) return;   // no tile of this chain for this block
     const int gene0 = c * 64;
     if (K > kTileMaxK) {
         // counts straight into the main rows (global atomics)
@@ -838,17 +839,30 @@ stats_tile_chain(const ChainArgs& ch, uint32_t (*cache)[128], uint32_t* priv, ui
             if (pn[i]) atomicAdd(&acc_nsub[i], pn[i]);
 }
 
-// Every chain of the table in turn, each with the whole grid.
+// The items of every chain with the blocked copy (chain b: tile_C chunks x
+// stat_groups tile groups) form one list dealt round-robin to the blocks, so
+// the chains of a batch are counted side by side, each with as many items as
+// its size warrants; for one chain there is one item per block.
 template <class Tab>
 __global__ void __launch_bounds__(kStatsTileThreads)
 k_stats_tile(const __grid_constant__ Tab tab) {
     __shared__ uint32_t cache[kStatsTileThreads / 32][128];
     __shared__ uint32_t priv[2 * kTileMaxK * 64];
     __shared__ uint32_t pn[2 * kTileMaxK];
+    const int64_t G = gridDim.x;
+    int64_t base = 0;
     for (int b = 0; b < tab.n(); ++b) {
-        if (!tab[b].tile_enabled) continue;
-        stats_tile_chain(tab[b], cache, priv, pn);
-        __syncthreads();
+        const ChainArgs& ch = tab[b];
+        if (!ch.tile_enabled) continue;
+        const int C = ch.tile_C, g = ch.stat_groups;
+        const int64_t items = (int64_t)C * g;
+        const int64_t first = base + (((int64_t)blockIdx.x - base) % G + G) % G;
+        for (int64_t id = first; id < base + items; id += G) {
+            const int64_t i = id - base;
+            stats_tile_item(ch, (int)(i % C), (int)(i / C), g, cache, priv, pn);
+            __syncthreads();
+        }
+        base += items;
     }
 }
 

@@ -204,3 +204,57 @@ def test_blocked_copy_at_the_bench_size(P):
     from paper_1812_10048_gb300 import synth
     ds = synth.pbmc68k()
     _layout_case(P, ds.indptr, ds.indices, ds.data, ds.N, ds.D)
+
+
+def _engine_after_sweep(P, ds, K, engine):
+    rng = np.random.default_rng(K)
+    labels = rng.integers(0, K, size=ds.N)
+    labels[:K] = np.arange(K)
+    sub = rng.integers(0, 2, size=ds.N).astype(np.uint8)
+    g = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, kmax=64, seed=5,
+                  engine=engine)
+    P.dpmm_set_state(g.ctx, labels, sub, K, 3, 0)
+    g.sweep(1)
+    used = P.dpmm_debug_engine(g.ctx)
+    g.close()
+    return used
+
+
+def test_engine_choice_follows_the_measured_density_rule(P):
+    """Automatic engine: the tensor-core engine for 3 <= K <= 40 at any density
+    and for K <= 2 below 12% density; the CSR engine for K <= 2 at 12% or more
+    (where it was measured faster) and for K > 40.  A forced tile engine labels
+    every 1 <= K <= 40."""
+    from paper_1812_10048_gb300 import synth
+    dense = synth.tiny()                                     # ~29% of entries non-zero
+    sparse = synth.make_dataset(2000, 500, 4, gamma=0.05, lib_mu=np.log(40.0), lib_sigma=0.3,
+                                seed=77)
+    assert dense.density >= 0.12 and sparse.density < 0.12, (dense.density, sparse.density)
+    assert _engine_after_sweep(P, dense, 2, P.ENGINE_AUTO) == 0
+    assert _engine_after_sweep(P, dense, 3, P.ENGINE_AUTO) == 1
+    assert _engine_after_sweep(P, dense, 40, P.ENGINE_AUTO) == 1
+    assert _engine_after_sweep(P, dense, 41, P.ENGINE_AUTO) == 0
+    assert _engine_after_sweep(P, sparse, 2, P.ENGINE_AUTO) == 1
+    assert _engine_after_sweep(P, dense, 2, P.ENGINE_TILE_BF16) == 1
+    assert _engine_after_sweep(P, dense, 2, P.ENGINE_CSR_FP32) == 0
+
+
+def test_auto_engine_below_the_cut_matches_the_oracle(P, tiny):
+    """K = 2 on the dense tiny workload takes the CSR engine under AUTO: labels,
+    sub-labels and sums of log q are the FP64 decisions except near-ties of the
+    FP32 contraction; statistics exact."""
+    from oracle.sampler import sufficient_stats
+    from .parity import check_assign, decisions_from_oracle, fp32_bound
+    g, o, logpi, logtheta = injected(P, tiny, 2, seed=311, engine=P.ENGINE_AUTO)
+    ref = decisions_from_oracle(o, logpi, logtheta, fp32_bound(o.X.astype(np.float64), logtheta))
+    t0 = o.t
+    o.assign_and_update(logpi, logtheta)
+    P.dpmm_assign(g.ctx)
+    assert P.dpmm_debug_engine(g.ctx) == 0
+    lab, sb, Kg, t, m = g.get_state()
+    assert t == o.t and Kg == o.K
+    nsub, Ssub, sq = g.stats()
+    check_assign(ref, 2, Kg, lab, sb, sq, o.seed, o.chain_id, t0)
+    on, oS = sufficient_stats(o.X, lab, sb, Kg)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
