@@ -52,7 +52,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="main", choices=["main", "batched", "large", "grad", "eb", "study", "local"],
+    ap.add_argument("--no-all-cores", action="store_true",
+                    help="skip the oracle run on all host cores (one chain per core)")
+    ap.add_argument("--config", default="main",
+                    choices=["main", "batched", "large", "grad", "eb", "study", "local", "ari",
+                             "bf16err", "engines"],
                     help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
                          "as one batch; large: 1.3M x 2k")
     ap.add_argument("--workers", type=int, default=0,
@@ -208,7 +212,7 @@ def traffic_for(kernel, workload_name):
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_steps_per_sec(ds, state, seconds, cells=None):
+def oracle_steps_per_sec(ds, state, seconds, cells=None, chain_id=0):
     """Time oracle steps (sweep + split/merge) from the given state.
 
     With ``cells`` the oracle runs on the first ``cells`` rows only and the
@@ -218,7 +222,7 @@ def oracle_steps_per_sec(ds, state, seconds, cells=None):
     n = ds.N if cells is None else int(cells)
     indptr = ds.indptr[:n + 1]
     o = OracleSampler(indptr, ds.indices[:indptr[-1]], ds.data[:indptr[-1]], n, ds.D, 1.0, 0.1,
-                      seed=42)
+                      seed=42, chain_id=chain_id)
     lab = labels[:n]
     present = np.unique(lab)
     remap = np.full(K, -1)
@@ -233,6 +237,71 @@ def oracle_steps_per_sec(ds, state, seconds, cells=None):
         if el >= seconds or steps >= 1000:
             break
     return steps / el * (n / ds.N), steps, el, n
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_chain_worker(args):
+    """One oracle chain in its own process (chain_id c) for `seconds`."""
+    state, seconds, chain_id = args
+    from paper_1812_10048_gb300 import synth
+    ds = synth.pbmc68k()
+    t0 = time.perf_counter()
+    rate, steps, el, n = oracle_steps_per_sec(ds, state, seconds, chain_id=chain_id)
+    return rate, steps, el, time.perf_counter() - t0
+
+
+def oracle_all_cores(state, seconds):
+    """The oracle is single-threaded (scipy sparse products, numpy); on all host
+    cores it runs as one independent chain per core (spawned processes, one
+    BLAS thread each), and the aggregate is their summed sweeps per second."""
+    import multiprocessing as mp
+    import resource
+    n = os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                            "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ru0 = resource.getrusage(resource.RUSAGE_CHILDREN)
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(n) as pool:
+            res = pool.map(_oracle_chain_worker, [(state, seconds, c) for c in range(n)])
+        wall = time.perf_counter() - t0
+        ru1 = resource.getrusage(resource.RUSAGE_CHILDREN)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    cpu_s = (ru1.ru_utime - ru0.ru_utime) + (ru1.ru_stime - ru0.ru_stime)
+    return {"value": round(sum(r[0] for r in res), 4), "unit": UNIT, "cores": n,
+            "kind": "oracle",
+            "sample": f"{n} independent oracle chains (chain_id 0..{n - 1}), one process and one "
+                      f"BLAS thread each, {min(r[1] for r in res)}-{max(r[1] for r in res)} steps "
+                      f"(sweep + split/merge) each on the full 68,000-cell workload from the GPU "
+                      f"chain's state, ~{seconds:.0f} s of timing each; the value is their summed "
+                      f"sweeps/s",
+            "effective_cores": round(cpu_s / wall, 1), "wall_s": round(wall, 1)}
 
 
 # ---------------------------------------------------------------------------
@@ -484,6 +553,191 @@ def run_large(args):
                    "l2": "inputs (> 1 GB) larger than L2"},
         "forms": forms, "clocks": clk,
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ari(args):
+    """The 68k x 1k workload: the BF16 and FP32 GPU chains and the FP64 oracle
+    chain, each 500 steps (sweep + coin-selected move) from K = 1 with the same
+    seed; ARI of each against the generating labels and of the GPU chains'
+    labels against the oracle's.  The oracle chain runs on one host core
+    (about four minutes)."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from oracle.ari import adjusted_rand_index
+    from oracle.sampler import Sampler as OracleSampler
+    ds, _ = workload()
+    n_steps = args.steps if args.steps != 2000 else 500
+    res = {}
+    for name, eng in [("bf16", P.ENGINE_AUTO), ("fp32", P.ENGINE_CSR_FP32)]:
+        s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                      engine=eng)
+        s.step(n_steps)
+        lab, K = s.labels()
+        res[name] = (lab, K)
+        s.close()
+    t0 = time.perf_counter()
+    o = OracleSampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, seed=42)
+    k_trace = []
+    for i in range(n_steps):
+        o.sweep()
+        o.split_merge(0)
+        if i in (9, 24, 49, 99, 249, n_steps - 1):
+            k_trace.append((i + 1, o.K))
+    oracle_s = time.perf_counter() - t0
+    res["oracle"] = (o.labels, o.K)
+    ari = {n: round(adjusted_rand_index(l, ds.labels), 4) for n, (l, _) in res.items()}
+    line = {
+        "metric": "ARI after 500 steps at 68k cells x 1k genes: GPU chains vs the FP64 oracle chain",
+        "value": abs(ari["bf16"] - ari["oracle"]), "unit": "|ARI_bf16 - ARI_oracle| vs truth",
+        "higher_is_better": False, "steps": n_steps, "data": "synthetic",
+        "config": workload_config(ds),
+        "ari_vs_truth": ari,
+        "ari_vs_oracle_labels": {n: round(adjusted_rand_index(res[n][0], res["oracle"][0]), 4)
+                                 for n in ("bf16", "fp32")},
+        "ari_bf16_vs_fp32": round(adjusted_rand_index(res["bf16"][0], res["fp32"][0]), 4),
+        "K_final": {n: int(k) for n, (_, k) in res.items()},
+        "oracle_K_trace": k_trace,
+        "oracle_seconds": round(oracle_s, 1),
+        "note": "each chain from K = 1 with seed 42; the GPU draws theta in FP32, the oracle in "
+                "FP64, so the trajectories part after the first near-tie; ARI compares the "
+                "partitions reached",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bf16_error_report(P, ds, steps, sample, seed=42):
+    """From the state of a BF16 chain after `steps` steps: the tensor-core
+    scores of `sample` cells against FP64 scores of the same FP32 parameters
+    (max absolute error, and the largest error as a fraction of the per-cell
+    bound 2^-16 sum_u x_u |d_u|), and the fraction of all cells whose label
+    differs from the FP64 decision on the same Philox words (the label-flip
+    rate), with the FP32 CSR engine's rate beside it."""
+    from oracle.sampler import csr_matrix, label_gumbels
+    import scipy.sparse as sp
+    X = csr_matrix(ds.indptr, ds.indices, ds.data, ds.N, ds.D).astype(np.float64)
+    out = {}
+    for name, eng in [("bf16", P.ENGINE_TILE_BF16), ("fp32", P.ENGINE_CSR_FP32)]:
+        s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=seed,
+                      engine=P.ENGINE_AUTO)
+        s.step(steps)
+        labels0, sub0, K, t, m = s.get_state()
+        _, _, sq = s.stats()
+        g = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=seed,
+                      engine=eng)
+        P.dpmm_set_state(g.ctx, labels0, sub0, K, t, m, sq)
+        s.close()
+        P.dpmm_draw_params(g.ctx)
+        logpi32, logtheta32 = P.dpmm_get_params(g.ctx, K, ds.D)
+        P.dpmm_set_params(g.ctx, logpi32, logtheta32)
+        lp, lt = logpi32.astype(np.float64), logtheta32.astype(np.float64)
+        rec = {"K": int(K), "after_steps": steps}
+        if name == "bf16":
+            got = P.dpmm_debug_tile_scores(g.ctx, ds.N, K)        # [N][3K], centred
+            rng = np.random.default_rng(7)
+            cells = np.sort(rng.choice(ds.N, size=min(sample, ds.N), replace=False))
+            m_u = lt.mean(axis=0)
+            d = lt - m_u[None, :]
+            order = np.concatenate([np.arange(0, 3 * K, 3),
+                                    np.stack([np.arange(1, 3 * K, 3), np.arange(2, 3 * K, 3)],
+                                             1).ravel()])
+            Xs = X[cells]
+            ref = np.asarray(Xs @ d[order].T)
+            bound = 2.0 ** -16 * np.asarray(abs(Xs) @ np.abs(d[order]).T)
+            err = np.abs(got[cells].astype(np.float64) - ref)
+            rec.update({"sample_cells": int(cells.size),
+                        "max_abs_score_error": float(err.max()),
+                        "max_error_over_bound": float((err / np.maximum(bound, 1e-30)).max()),
+                        "median_abs_score_error": float(np.median(err)),
+                        "max_abs_score": float(np.abs(ref).max())})
+        # label flips over all cells: FP64 Gumbel-max from the same parameters
+        sc = np.asarray(X @ lt[0::3].T) + lp[None, :K]
+        v = sc + label_gumbels(ds.N, K, seed, 0, t)
+        fp64_lab = np.argmax(v, axis=1)
+        P.dpmm_assign(g.ctx)
+        lab, _, K1, _, _ = g.get_state()
+        if K1 == K:
+            rec["label_flip_rate"] = float(np.mean(lab != fp64_lab))
+            rec["label_flips"] = int(np.sum(lab != fp64_lab))
+        else:
+            rec["label_flip_rate"] = None
+            rec["note"] = "a cluster emptied; labels renumbered"
+        out[name] = rec
+        g.close()
+    return out
+
+
+def run_bf16err(args):
+    """Per configuration: the BF16 tensor-core scores' error against FP64 and
+    the label-flip rate (68k x 1k, and 1.3M x 2k with counts above 255)."""
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    ds68, _ = workload()
+    res = {"pbmc68k_68000x1000": bf16_error_report(P, ds68, 60, 20000)}
+    del ds68
+    dsl = synth.large(workers=args.workers or os.cpu_count())
+    res["large_1300000x2000"] = bf16_error_report(P, dsl, 40, 20000)
+    line = {"metric": "BF16 hi/lo score error vs FP64 and label-flip rate, per configuration",
+            "data": "synthetic", "results": res,
+            "bound": "per (cell, column): 2^-16 sum_u x_u |log theta_u - m_u| plus FP32 "
+                     "accumulation; a label may flip only where the top two perturbed scores "
+                     "lie closer than twice the bound"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_engines(args):
+    """Sweep time of the two label engines over density x K: 68,000 cells x
+    1,000 genes, library sizes chosen to give densities from ~3% to ~40%; for
+    each K the state is a fixed random partition into K clusters (labels decide
+    the cost, not the data's fit) and one sweep (draws, labels, statistics,
+    compaction) is timed from it, the state restored before every sweep."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    libs = [100, 300, 1000, 3000, 8000]
+    Ks = [2, 5, 10, 20, 30, 40]
+    reps = 20
+    rows = []
+    for L in libs:
+        ds = synth.make_dataset(68000, 1000, 10, gamma=0.05, lib_mu=np.log(float(L)), lib_sigma=0.6,
+                                seed=1100 + L)
+        for K in Ks:
+            rng = np.random.default_rng(K)
+            labels = rng.integers(0, K, size=ds.N)
+            labels[:K] = np.arange(K)
+            sub = rng.integers(0, 2, size=ds.N).astype(np.uint8)
+            rec = {"library": L, "density": round(ds.density, 4), "nnz": ds.nnz, "K": K}
+            for name, eng in [("tile_bf16", P.ENGINE_TILE_BF16), ("csr_fp32", P.ENGINE_CSR_FP32)]:
+                s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=64,
+                              seed=42, engine=eng)
+                st = torch.cuda.ExternalStream(s.stream)
+                ms = []
+                for r in range(reps + 3):
+                    P.dpmm_set_state(s.ctx, labels, sub, K, 5, 0)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    s.sweep(1)
+                    b.record(st)
+                    torch.cuda.synchronize()
+                    if r >= 3:
+                        ms.append(a.elapsed_time(b))
+                rec[name + "_ms"] = round(float(np.median(ms)), 4)
+                s.close()
+            rec["faster"] = "tile_bf16" if rec["tile_bf16_ms"] < rec["csr_fp32_ms"] else "csr_fp32"
+            rows.append(rec)
+            print(json.dumps(rec), flush=True)
+    line = {"metric": "sweep time of the label engines over density x K (68,000 x 1,000)",
+            "data": "synthetic", "rows": rows}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -841,6 +1095,12 @@ def main():
         return run_eb(args)
     if args.config == "study":
         return run_study(args)
+    if args.config == "engines":
+        return run_engines(args)
+    if args.config == "ari":
+        return run_ari(args)
+    if args.config == "bf16err":
+        return run_bf16err(args)
     if args.config == "local":
         return run_local(args)
     if args.config == "batched":
@@ -922,11 +1182,17 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         rate, n_steps, el, cells = oracle_steps_per_sec(ds, prim["state"], args.cpu_seconds)
+        model = cpu_model()
         line["cpu_baseline"] = {
             "value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n_steps} oracle steps (sweep + split/merge, FP64 numpy/scipy) on the "
                       f"full {cells}-cell workload from the GPU chain's state, {el:.1f} s",
+            "cpu_model": model,
         }
+        if not args.no_all_cores:
+            allc = oracle_all_cores(prim["state"], args.cpu_seconds)
+            allc["cpu_model"] = model
+            line["cpu_baseline_all_cores"] = allc
     print(json.dumps(line))
     return 0
 
