@@ -59,6 +59,9 @@ def parse():
                              "bf16err", "engines"],
                     help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
                          "as one batch; large: 1.3M x 2k")
+    ap.add_argument("--autotune", action="store_true",
+                    help="main / batched: choose the launch tuning by timing the live sampler "
+                         "before the warm-up (not cached); default: the built-in tuning")
     ap.add_argument("--workers", type=int, default=0,
                     help="processes drawing the batched / large data (0: all cores)")
     return ap.parse_args()
@@ -313,6 +316,11 @@ def timed_chain(P, ds, engine, args, rank, local, torch):
                   chain_id=rank, engine=engine)
     stream = torch.cuda.ExternalStream(s.stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    tuned = None
+    if args.autotune:
+        from paper_1812_10048_gb300 import autotune as AT
+        s.step(args.warmup)
+        tuned = AT.autotune(s, [ds.indptr], use_cache=False)
     s.step(args.warmup)
     s.sync()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -336,6 +344,7 @@ def timed_chain(P, ds, engine, args, rank, local, torch):
     labels, K = s.labels()
     state = s.get_state()
     _, _, sumlogq = s.stats()
+    tuning = P.dpmm_get_tuning(s.ctx)
     # phase times: the profiled graph has event records between the phases
     P.dpmm_profile(s.ctx, True)
     s.step(3)
@@ -355,7 +364,7 @@ def timed_chain(P, ds, engine, args, rank, local, torch):
     s.close()
     return {"total_ms": float(step_ms.sum()), "step_ms": step_ms, "phases": phases, "K": K,
             "labels": labels, "wall_s": wall, "clocks": clk, "applied": int(applied),
-            "profiled_ms_per_step": prof_ms / n_prof,
+            "profiled_ms_per_step": prof_ms / n_prof, "tuning": tuning, "autotune": tuned,
             "state": (state[0], state[1], state[2], state[3], state[4], sumlogq)}
 
 
@@ -457,6 +466,11 @@ def run_batched(args):
     for name, eng in [("bf16_batched", P.ENGINE_AUTO), ("fp32_batched", P.ENGINE_CSR_FP32)]:
         bs = P.BatchSampler(data, D, 1.0, 0.5, kmax=64, seed=42, engine=eng)
         st = torch.cuda.ExternalStream(bs.stream)
+        tuned = None
+        if args.autotune:
+            from paper_1812_10048_gb300 import autotune as AT
+            bs.step(warmup)
+            tuned = AT.autotune(bs, [d[0] for d in data], use_cache=False)
         if name == "bf16_batched":
             clocks.start()
         ms = time_steps(lambda: bs.step(1), st, steps, warmup, torch)
@@ -465,6 +479,8 @@ def run_batched(args):
         labels[name] = [bs.chain(b).labels()[0] for b in range(B)]
         forms[name] = {"chain_sweeps_per_s": round(B * steps / (ms.sum() / 1e3), 1),
                        "ms_per_batched_step": round(float(ms.mean()), 4),
+                       "launch_tuning": {"values": P.dpmm_get_tuning(bs.ctx),
+                                         "source": "autotuned" if tuned else "built-in defaults"},
                        "K": [int(bs.chain(b).labels_K()) for b in range(B)],
                        "mean_ari_vs_truth": round(float(np.mean([
                            adjusted_rand_index(labels[name][b], dss[b].labels)
@@ -1174,6 +1190,8 @@ def main():
             "algorithmic_bytes_per_step": int(step_bytes),
         },
         "forms": forms,
+        "launch_tuning": {"values": prim["tuning"],
+                          "source": "autotuned" if prim["autotune"] else "built-in defaults"},
         "e2e": r.get("e2e"),
         "gpu_launches": KERNELS_PER_STEP[r["primary"]] * steps,
         "clocks": prim["clocks"],

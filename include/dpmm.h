@@ -189,6 +189,37 @@ int dpmm_plans_applied(dpmm_ctx* ctx, int64_t* n);
  */
 int dpmm_debug_engine(dpmm_ctx* ctx, int32_t* tile_used);
 
+/*
+ * Launch tuning of a context (a single chain or a batch).  Each field picks how
+ * a kernel of the step spreads its work over the GPU; 0 keeps the built-in
+ * choice.  None of them changes any result (the same arithmetic in the same
+ * order per cell, tile and cluster; integer statistics), so a tuned chain is
+ * bit-identical to an untuned one.  The paper has no counterpart: these are
+ * properties of this implementation, chosen by measurement (the Python
+ * package's autotune module times the candidates and caches the fastest).
+ *   stats_blocks_per_sm  statistics kernel blocks per SM: 1, 2, 4 or 8
+ *                        (default 4 for one chain, 2 for a batch)
+ *   tile_stages          dense-tile label kernel A/B stages: 2, or 4 (four
+ *                        when they fit in shared memory, else two); default
+ *                        4 for one chain, 2 for a batch
+ *   tile_scatter         row entries a producer lane loads per batch: 8, 12 or
+ *                        16 (default 12)
+ *   draw_blocks_per_sm   parameter-draw kernel blocks per SM: 1 or 2 (default 2)
+ * Other values: DPMM_EINVAL.  dpmm_set_tuning drops the captured step graph
+ * (the next dpmm_step captures a new one).  dpmm_get_tuning returns the values
+ * in force (defaults resolved).
+ */
+typedef struct dpmm_tuning {
+    int32_t stats_blocks_per_sm;
+    int32_t tile_stages;
+    int32_t tile_scatter;
+    int32_t draw_blocks_per_sm;
+    int32_t reserved[4];
+} dpmm_tuning;
+
+int dpmm_set_tuning(dpmm_ctx* ctx, const dpmm_tuning* tuning);
+int dpmm_get_tuning(dpmm_ctx* ctx, dpmm_tuning* tuning);
+
 /* Block until all work enqueued on the context's stream is done. */
 int dpmm_sync(dpmm_ctx* ctx);
 

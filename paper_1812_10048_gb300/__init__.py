@@ -12,12 +12,13 @@ import ctypes
 import numpy as np
 
 from ._lib import (DpmmError, ENGINE_AUTO, ENGINE_CSR_FP32, ENGINE_TILE_BF16, check, dpmm_opts,
-                   lib, ptr)
+                   dpmm_tuning, lib, ptr)
 
 __all__ = [
     "DpmmError", "Sampler", "LogML", "dpmm_default_opts", "dpmm_init", "dpmm_free", "dpmm_sweep",
     "dpmm_split_merge", "dpmm_step", "dpmm_labels", "dpmm_sync", "dpmm_stream", "dpmm_profile",
-    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_debug_engine", "dpmm_logml_grad",
+    "dpmm_phase_times", "dpmm_plans_applied", "dpmm_debug_engine", "dpmm_set_tuning",
+    "dpmm_get_tuning", "TUNING_FIELDS", "dpmm_logml_grad",
     "dpmm_set_hyper",
     "dpmm_eb_step", "empirical_bayes", "dpmm_init_batch",
     "dpmm_chain", "BatchSampler", "dpmm_get_state",
@@ -112,6 +113,26 @@ def dpmm_plans_applied(ctx):
     n = ctypes.c_int64(0)
     check(lib().dpmm_plans_applied(ctx, ctypes.byref(n)))
     return n.value
+
+
+TUNING_FIELDS = ("stats_blocks_per_sm", "tile_stages", "tile_scatter", "draw_blocks_per_sm")
+
+
+def dpmm_set_tuning(ctx, **fields):
+    """Launch tuning of a context (see dpmm.h); unnamed fields keep 0 (default)."""
+    t = dpmm_tuning()
+    for k, v in fields.items():
+        if k not in TUNING_FIELDS:
+            raise ValueError(f"unknown tuning field {k!r}")
+        setattr(t, k, int(v))
+    check(lib().dpmm_set_tuning(ctx, ctypes.byref(t)))
+
+
+def dpmm_get_tuning(ctx):
+    """The launch tuning in force, as a dict."""
+    t = dpmm_tuning()
+    check(lib().dpmm_get_tuning(ctx, ctypes.byref(t)))
+    return {k: int(getattr(t, k)) for k in TUNING_FIELDS}
 
 
 def dpmm_debug_engine(ctx):

@@ -33,6 +33,12 @@ class dpmm_opts(ctypes.Structure):
                 ("local_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
+class dpmm_tuning(ctypes.Structure):
+    _fields_ = [("stats_blocks_per_sm", ctypes.c_int32), ("tile_stages", ctypes.c_int32),
+                ("tile_scatter", ctypes.c_int32), ("draw_blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
 _P = ctypes.c_void_p
 _I32, _I64, _U64, _F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
 
@@ -49,6 +55,8 @@ SIGNATURES = {
     "dpmm_sync": (ctypes.c_int, [_P]),
     "dpmm_plans_applied": (ctypes.c_int, [_P, _P]),
     "dpmm_debug_engine": (ctypes.c_int, [_P, _P]),
+    "dpmm_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(dpmm_tuning)]),
+    "dpmm_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(dpmm_tuning)]),
     "dpmm_init_batch": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "dpmm_chain": (ctypes.c_int, [_P, _I32, _P]),
     "dpmm_logml_grad": (ctypes.c_int, [_P, _P, _I32, ctypes.c_double, _P, _P, _P, _P]),

@@ -158,9 +158,6 @@ ChainArgs dpmm::chain_args(const Ctx& c) {
     a.tile_C = c.tile_C;
     a.tile_T = c.tile_T;
     a.tile_Lslot = c.tile_Lslot;
-    // one chain: a statistics item per block of the launch (tile groups of
-    // the gene chunks, see k_stats_tile)
-    a.stat_groups = c.tile_enabled ? std::max(1, std::min(c.tile_T, tile_stat_groups(c))) : 0;
     // engine choice by measured density (constants in common.cuh); the tile
     // engine forced by the caller labels every 1 <= K <= 40
     const double density = (c.N > 0 && c.D > 0) ? (double)c.nnz / ((double)c.N * c.D) : 0.0;
@@ -533,6 +530,7 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
                             c.stream));
         c.nchains = 1;
         c.max_Lslot = c.tile_Lslot;
+        c.tile_sumT = c.tile_enabled ? c.tile_T : 0;
     }
     if (c.tile_enabled) CKI(configure_tile(c));
     CKI(launch_lg_table(c));
@@ -631,22 +629,7 @@ int dpmm_init_batch(dpmm_ctx** out, int32_t B, const int32_t* const* indptr,
         c.max_Lslot = std::max(c.max_Lslot, m->c.tile_Lslot);
         tab.push_back(*m->c.h_chain0);
     }
-    {
-        // statistics items of the batch: each chain's gene chunks split into
-        // tile groups of about S tiles, S chosen so that the whole batch makes
-        // about two items per block of the launch (the chains are counted side
-        // by side; a small chain is one item per chunk)
-        int64_t sumT = 0;
-        for (const ChainArgs& a : tab) sumT += a.tile_enabled ? a.tile_T : 0;
-        const int C = std::max(1, c.tile_C);
-        const int nt = std::max(1, (2 * c.num_sms) / C);   // tile_stat_groups of a batch
-        const int64_t S = std::max<int64_t>(1, (sumT * C + 2 * (int64_t)nt * C - 1) /
-                                                   (2 * (int64_t)nt * C));
-        for (ChainArgs& a : tab)
-            if (a.tile_enabled)
-                a.stat_groups = (int32_t)std::max<int64_t>(
-                    1, std::min<int64_t>({(a.tile_T + S - 1) / S, (int64_t)a.tile_T, (int64_t)nt}));
-    }
+    for (const ChainArgs& a : tab) c.tile_sumT += a.tile_enabled ? a.tile_T : 0;
     cudaError_t e;
     if ((e = dalloc(&c.gbar, 1)) || (e = dalloc(&c.d_chains, (size_t)B)) ||
         (e = cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.stream)) ||
@@ -781,6 +764,48 @@ int dpmm_plans_applied(dpmm_ctx* ctx, int64_t* n) {
         if ((rc = sync_scalars(m->c))) return rc;
         *n += (int64_t)m->c.sc_host->n_apply;
     }
+    return DPMM_OK;
+}
+
+int dpmm_set_tuning(dpmm_ctx* ctx, const dpmm_tuning* t) {
+    CHECK_CTX(ctx);
+    if (!t) return fail(DPMM_EINVAL, "tuning is NULL");
+    auto in = [](int32_t v, std::initializer_list<int32_t> ok) {
+        for (int32_t o : ok)
+            if (v == o) return true;
+        return false;
+    };
+    if (!in(t->stats_blocks_per_sm, {0, 1, 2, 4, 8}))
+        return fail(DPMM_EINVAL, "stats_blocks_per_sm %d not in {0, 1, 2, 4, 8}",
+                    t->stats_blocks_per_sm);
+    if (!in(t->tile_stages, {0, 2, 4}))
+        return fail(DPMM_EINVAL, "tile_stages %d not in {0, 2, 4}", t->tile_stages);
+    if (!in(t->tile_scatter, {0, 8, 12, 16}))
+        return fail(DPMM_EINVAL, "tile_scatter %d not in {0, 8, 12, 16}", t->tile_scatter);
+    if (!in(t->draw_blocks_per_sm, {0, 1, 2}))
+        return fail(DPMM_EINVAL, "draw_blocks_per_sm %d not in {0, 1, 2}", t->draw_blocks_per_sm);
+    Ctx& c = ctx->c;
+    CK(cudaStreamSynchronize(c.stream));
+    c.tune_stats_per_sm = t->stats_blocks_per_sm;
+    c.tune_tile_stages = t->tile_stages;
+    c.tune_tile_scatter = t->tile_scatter;
+    c.tune_draw_per_sm = t->draw_blocks_per_sm;
+    if (c.step_exec) {
+        cudaGraphExecDestroy(c.step_exec);
+        c.step_exec = nullptr;
+    }
+    return DPMM_OK;
+}
+
+int dpmm_get_tuning(dpmm_ctx* ctx, dpmm_tuning* t) {
+    CHECK_CTX(ctx);
+    if (!t) return fail(DPMM_EINVAL, "tuning is NULL");
+    const Ctx& c = ctx->c;
+    std::memset(t, 0, sizeof(*t));
+    t->stats_blocks_per_sm = c.tune_stats_per_sm ? c.tune_stats_per_sm : (c.nchains > 1 ? 2 : 4);
+    t->tile_stages = tile_label_stages(c);
+    t->tile_scatter = c.tune_tile_scatter ? c.tune_tile_scatter : 12;
+    t->draw_blocks_per_sm = c.tune_draw_per_sm ? c.tune_draw_per_sm : 2;
     return DPMM_OK;
 }
 

@@ -175,6 +175,13 @@ struct Ctx {
     int32_t* tile_ptr = nullptr;    // [4 T C + 1] quarter starts
     unsigned char* tile_B = nullptr;  // per-sweep BF16 hi/lo table, [C][256 rows][64] swizzled
     float* noise = nullptr;         // [kTileMaxK + 2][N] the sweep's label noise (tile engine)
+    int64_t tile_sumT = 0;          // tiles over the chains this context walks
+    // launch tuning (dpmm_set_tuning; 0 = the built-in default).  None of these
+    // changes a result: they split the same arithmetic differently over blocks.
+    int32_t tune_stats_per_sm = 0;  // statistics blocks per SM (1, 2, 4, 8)
+    int32_t tune_tile_stages = 0;   // label-kernel A/B stages (2 or 4)
+    int32_t tune_tile_scatter = 0;  // producer entries per lane and batch (8, 12, 16)
+    int32_t tune_draw_per_sm = 0;   // draw-kernel blocks per SM (1 or 2)
 
 
     // chains this context's launches walk: itself (nchains = 1) or, for a
@@ -368,7 +375,6 @@ struct ChainArgs {
     int32_t* move_ticket;
     // dense-tile engine (tile_enabled = 0: not built for this chain)
     int32_t tile_enabled, tile_C, tile_T, tile_Lslot;
-    int32_t stat_groups;  // tile groups per gene chunk in the statistics launch
     int32_t tile_kmin;    // smallest K the dense-tile engine labels (engine choice)
     uint32_t* tile_ent;
     int32_t* tile_ptr;
@@ -578,6 +584,7 @@ cudaError_t launch_tile_label(Ctx& c, float* dbg);
 cudaError_t launch_tile_stats(Ctx& c);
 size_t tile_b_bytes(int32_t C);
 int32_t tile_stat_groups(const Ctx& c);
+int32_t tile_label_stages(const Ctx& c);
 cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, int N, float* C,
                                  int* err);
 

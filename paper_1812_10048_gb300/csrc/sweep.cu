@@ -1027,7 +1027,8 @@ cudaError_t configure_launches(Ctx& c) {
 
 cudaError_t launch_draw_params(Ctx& c) {
     return with_table(c, [&](auto tab) {
-        k_draw_params<<<2 * c.num_sms, kDrawThreads, 0, c.stream>>>(tab);
+        const int per_sm = c.tune_draw_per_sm ? c.tune_draw_per_sm : 2;
+        k_draw_params<<<per_sm * c.num_sms, kDrawThreads, 0, c.stream>>>(tab);
         return cudaGetLastError();
     });
 }

@@ -253,13 +253,16 @@ constexpr int kBLoadWarp = kMmaWarp + 2;
 constexpr int kTileThreadsP = (kMmaWarp + 3) * 32;
 constexpr int kBarEpi = 1, kBarLabel = 2;
 constexpr int kSmallBytes = 8192;
-constexpr int kScatter = 12;         // entries per producer lane and batch
+constexpr int kScatterDefault = 12;  // entries per producer lane and batch (tunable: 8, 12, 16)
 
 // dbg: optional [N][3K] centred scores of a single chain (no state or
 // statistics writes).
-template <class Tab>
+// kScatter: row entries a producer lane loads per batch; stages_pref: 2 to
+// use two A/B stages even when four fit (0: as many as fit).
+template <class Tab, int kScatter>
 __global__ void __launch_bounds__(kTileThreadsP, 1)
-k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes) {
+k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes,
+            int32_t stages_pref) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -289,7 +292,10 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes)
     const int64_t avail = smem_bytes - (int64_t)(base - smem_raw) - kSmallBytes;
     // a stage holds a chunk's A tiles (lo, hi) and its B operand: one MMA
     // commit per chunk frees both
-    const int nS = (int64_t)kMaxStages * (32768 + b_slot) + 2 * e_slot <= avail ? kMaxStages : 2;
+    const int nS = stages_pref != 2 &&
+                           (int64_t)kMaxStages * (32768 + b_slot) + 2 * e_slot <= avail
+                       ? kMaxStages
+                       : 2;
     const int nB = nS;
     const int nE_fit = (int)min((int64_t)kMaxESlots,
                                 (avail - (int64_t)nS * (32768 + b_slot)) / e_slot);
@@ -839,13 +845,16 @@ stats_tile_item(const ChainArgs& ch, int c, int tg, int nt, uint32_t (*cache)[12
             if (pn[i]) atomicAdd(&acc_nsub[i], pn[i]);
 }
 
-// The items of every chain with the blocked copy (chain b: tile_C chunks x
-// stat_groups tile groups) form one list dealt round-robin to the blocks, so
-// the chains of a batch are counted side by side, each with as many items as
-// its size warrants; for one chain there is one item per block.
+// The items of every chain with the blocked copy (chain b: tile_C chunks x g_b
+// tile groups) form one list dealt round-robin to the blocks, so the chains of
+// a batch are counted side by side, each with as many items as its size
+// warrants: g_b = ceil(T_b / S) clamped to [1, min(T_b, nt)], with nt the tile
+// groups per chunk of the launch and S the tiles per item that give the whole
+// table about two items per block (one item per block for a single chain).
+// The counts are integer sums, so the split into items changes nothing.
 template <class Tab>
 __global__ void __launch_bounds__(kStatsTileThreads)
-k_stats_tile(const __grid_constant__ Tab tab) {
+k_stats_tile(const __grid_constant__ Tab tab, int32_t nt, int64_t S) {
     __shared__ uint32_t cache[kStatsTileThreads / 32][128];
     __shared__ uint32_t priv[2 * kTileMaxK * 64];
     __shared__ uint32_t pn[2 * kTileMaxK];
@@ -854,7 +863,9 @@ k_stats_tile(const __grid_constant__ Tab tab) {
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
         if (!ch.tile_enabled) continue;
-        const int C = ch.tile_C, g = ch.stat_groups;
+        const int C = ch.tile_C;
+        const int g = (int)max((int64_t)1, min(((int64_t)ch.tile_T + S - 1) / S,
+                                               (int64_t)min(ch.tile_T, nt)));
         const int64_t items = (int64_t)C * g;
         const int64_t first = base + (((int64_t)blockIdx.x - base) % G + G) % G;
         for (int64_t id = first; id < base + items; id += G) {
@@ -867,21 +878,24 @@ k_stats_tile(const __grid_constant__ Tab tab) {
 }
 
 // Tile groups per gene chunk of the statistics launch: four blocks per SM
-// for one chain; two for a batch, whose chains the blocks take in turn (each
-// chain costs every block a clear and a flush of its counters).
+// for one chain, two for a batch, unless tuned (dpmm_set_tuning).
 int32_t tile_stat_groups(const Ctx& c) {
-    return max(1, ((c.nchains > 1 ? 2 : 4) * c.num_sms) / c.tile_C);
+    const int per_sm = c.tune_stats_per_sm ? c.tune_stats_per_sm : (c.nchains > 1 ? 2 : 4);
+    return max(1, (per_sm * c.num_sms) / max(1, c.tile_C));
 }
 
 size_t tile_b_bytes(int32_t C) { return (size_t)C * kBChunkBytes; }
 
 cudaError_t configure_tile(Ctx& c) {
-    cudaError_t e = cudaFuncSetAttribute(k_assign_tc<TabV>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)c.smem_optin);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_assign_tc<TabP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)c.smem_optin);
+    const void* fns[6] = {(const void*)k_assign_tc<TabV, 8>, (const void*)k_assign_tc<TabV, 12>,
+                          (const void*)k_assign_tc<TabV, 16>, (const void*)k_assign_tc<TabP, 8>,
+                          (const void*)k_assign_tc<TabP, 12>, (const void*)k_assign_tc<TabP, 16>};
+    for (const void* f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)c.smem_optin);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_build_b(Ctx& c, bool force) {
@@ -892,18 +906,39 @@ cudaError_t launch_build_b(Ctx& c, bool force) {
     });
 }
 
+// A/B stages of the label kernel: four for one chain; two for a batch, where
+// the shared memory freed goes to more row-segment slots (measured faster on
+// 64 datasets: 2.85 against 3.18 ms per step), unless tuned.
+int32_t tile_label_stages(const Ctx& c) {
+    return c.tune_tile_stages ? c.tune_tile_stages : (c.nchains > 1 ? 2 : 4);
+}
+
 cudaError_t launch_tile_label(Ctx& c, float* dbg) {
+    const int scatter = c.tune_tile_scatter ? c.tune_tile_scatter : kScatterDefault;
+    const int32_t stages = tile_label_stages(c);
     return with_table(c, [&](auto tab) {
-        k_assign_tc<<<c.num_sms, kTileThreadsP, c.smem_optin, c.stream>>>(
-            tab, dbg, (int64_t)c.smem_optin);
+        using T = decltype(tab);
+        const int64_t sm = (int64_t)c.smem_optin;
+        if (scatter == 8)
+            k_assign_tc<T, 8><<<c.num_sms, kTileThreadsP, c.smem_optin, c.stream>>>(
+                tab, dbg, sm, stages);
+        else if (scatter == 16)
+            k_assign_tc<T, 16><<<c.num_sms, kTileThreadsP, c.smem_optin, c.stream>>>(
+                tab, dbg, sm, stages);
+        else
+            k_assign_tc<T, 12><<<c.num_sms, kTileThreadsP, c.smem_optin, c.stream>>>(
+                tab, dbg, sm, stages);
         return cudaGetLastError();
     });
 }
 
 cudaError_t launch_tile_stats(Ctx& c) {
     const int nt = tile_stat_groups(c);   // tile groups per gene chunk
+    const int64_t C = std::max(1, c.tile_C);
+    const int64_t S = std::max<int64_t>(1, (c.tile_sumT * C + 2 * (int64_t)nt * C - 1) /
+                                               (2 * (int64_t)nt * C));
     return with_table(c, [&](auto tab) {
-        k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(tab);
+        k_stats_tile<<<nt * c.tile_C, kStatsTileThreads, 0, c.stream>>>(tab, nt, S);
         return cudaGetLastError();
     });
 }
