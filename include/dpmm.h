@@ -205,6 +205,14 @@ int dpmm_debug_engine(dpmm_ctx* ctx, int32_t* tile_used);
  *   tile_scatter         row entries a producer lane loads per batch: 8, 12 or
  *                        16 (default 12)
  *   draw_blocks_per_sm   parameter-draw kernel blocks per SM: 1 or 2 (default 2)
+ *   local_lanes          lanes per cell of the local Gibbs sub-label kernel's
+ *                        group form: 4, 8, 16 or 32 (default: the power of
+ *                        two nearest below the mean row length / 8, within
+ *                        [4, 32])
+ *   local_group_form     1: that kernel always takes the group form; 0
+ *                        (default): the streamed form wherever the chain has
+ *                        the packed rows and its theta-bar table leaves room
+ *                        for the ring in shared memory
  * Other values: DPMM_EINVAL.  dpmm_set_tuning drops the captured step graph
  * (the next dpmm_step captures a new one).  dpmm_get_tuning returns the values
  * in force (defaults resolved).
@@ -214,7 +222,9 @@ typedef struct dpmm_tuning {
     int32_t tile_stages;
     int32_t tile_scatter;
     int32_t draw_blocks_per_sm;
-    int32_t reserved[4];
+    int32_t local_lanes;
+    int32_t local_group_form;
+    int32_t reserved[2];
 } dpmm_tuning;
 
 int dpmm_set_tuning(dpmm_ctx* ctx, const dpmm_tuning* tuning);

@@ -115,7 +115,8 @@ def dpmm_plans_applied(ctx):
     return n.value
 
 
-TUNING_FIELDS = ("stats_blocks_per_sm", "tile_stages", "tile_scatter", "draw_blocks_per_sm")
+TUNING_FIELDS = ("stats_blocks_per_sm", "tile_stages", "tile_scatter", "draw_blocks_per_sm",
+                 "local_lanes", "local_group_form")
 
 
 def dpmm_set_tuning(ctx, **fields):
@@ -352,6 +353,7 @@ class Sampler:
                  chain_id=0, engine=ENGINE_AUTO, split_q=True, hastings="integrated",
                  open_new_cluster=False, local_iters=1, stream=None):
         self.N, self.D, self.kmax = int(N), int(D), int(kmax)
+        self.local_iters = int(local_iters)
         if hastings not in ("integrated", "instantiated"):
             raise ValueError("hastings must be 'integrated' or 'instantiated'")
         opts = dpmm_default_opts(kmax=kmax, seed=seed, chain_id=chain_id, engine=engine,
@@ -438,6 +440,7 @@ class BatchSampler:
         """datasets: list of (indptr, indices, data, N); alpha / beta scalars or lists."""
         B = len(datasets)
         self.B, self.D, self.kmax = B, int(D), int(kmax)
+        self.local_iters = int(local_iters)
         self.Ns = [int(d[3]) for d in datasets]
         al = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (B,))
         be = np.broadcast_to(np.asarray(beta, dtype=np.float64), (B,))

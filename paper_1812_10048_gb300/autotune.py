@@ -1,8 +1,9 @@
 """Launch autotuning for a chain or a batch of chains.
 
-The step's kernels take four launch settings (dpmm_set_tuning): statistics
+The step's kernels take five launch settings (dpmm_set_tuning): statistics
 blocks per SM, the dense-tile label kernel's stage count and producer scatter
-batch, and the parameter-draw blocks per SM.  None of them changes a result,
+batch, the parameter-draw blocks per SM and the lanes per cell of the local
+Gibbs sub-label kernel (searched only for samplers with local iterations).  None of them changes a result,
 so the fastest can be chosen by timing steps of the live sampler itself: its
 state is saved before the trials and restored after them (a restored chain
 continues bit-identically), and the choice is cached on disk, keyed by the
@@ -32,6 +33,8 @@ SEARCH = (
     ("tile_scatter", (8, 12, 16)),
     ("draw_blocks_per_sm", (1, 2)),
 )
+# searched only for samplers that run local Gibbs iterations
+LOCAL_SEARCH = (("local_group_form", (0, 1)), ("local_lanes", (4, 8, 16, 32)))
 MARGIN = 0.02          # a candidate must beat the incumbent by 2%
 
 
@@ -164,7 +167,9 @@ def autotune(sampler, indptrs, *, trial_steps=20, repeats=3, use_cache=True, pat
         return float(np.median(times))
 
     from . import dpmm_get_tuning
-    best, best_t, n = coordinate_descent(measure, start=dpmm_get_tuning(sampler.ctx))
+    search = SEARCH + (LOCAL_SEARCH if getattr(sampler, "local_iters", 1) > 1 else ())
+    best, best_t, n = coordinate_descent(measure, start=dpmm_get_tuning(sampler.ctx),
+                                         search=search)
     _restore(sampler, saved)
     _lib_tuning(sampler, best)
     rec = {"tuning": best, "ms_per_step": best_t * 1e3, "measurements": n,

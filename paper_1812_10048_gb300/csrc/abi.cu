@@ -443,7 +443,13 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
 
     const size_t K2 = 2 * (size_t)c.kmax;
     if (c.packed) {
-        CKI(dalloc(&c.entries, (size_t)nnz));
+        // padded to a multiple of four entries (zeros) so that 16-byte aligned
+        // bulk copies of rows stay inside the allocation
+        const size_t padded = ((size_t)nnz + 3) & ~(size_t)3;
+        CKI(dalloc(&c.entries, padded > 0 ? padded : 4));
+        if (padded > (size_t)nnz)
+            CKI(cudaMemsetAsync(c.entries + nnz, 0, (padded - (size_t)nnz) * sizeof(uint32_t),
+                                c.stream));
         CKI(launch_pack(d_idx, d_val, nnz, c.entries, c.num_sms, c.stream));
     } else {
         c.cols = d_idx;
@@ -784,12 +790,18 @@ int dpmm_set_tuning(dpmm_ctx* ctx, const dpmm_tuning* t) {
         return fail(DPMM_EINVAL, "tile_scatter %d not in {0, 8, 12, 16}", t->tile_scatter);
     if (!in(t->draw_blocks_per_sm, {0, 1, 2}))
         return fail(DPMM_EINVAL, "draw_blocks_per_sm %d not in {0, 1, 2}", t->draw_blocks_per_sm);
+    if (!in(t->local_lanes, {0, 4, 8, 16, 32}))
+        return fail(DPMM_EINVAL, "local_lanes %d not in {0, 4, 8, 16, 32}", t->local_lanes);
+    if (!in(t->local_group_form, {0, 1}))
+        return fail(DPMM_EINVAL, "local_group_form %d not in {0, 1}", t->local_group_form);
     Ctx& c = ctx->c;
     CK(cudaStreamSynchronize(c.stream));
     c.tune_stats_per_sm = t->stats_blocks_per_sm;
     c.tune_tile_stages = t->tile_stages;
     c.tune_tile_scatter = t->tile_scatter;
     c.tune_draw_per_sm = t->draw_blocks_per_sm;
+    c.tune_local_lanes = t->local_lanes;
+    c.tune_local_group_form = t->local_group_form;
     if (c.step_exec) {
         cudaGraphExecDestroy(c.step_exec);
         c.step_exec = nullptr;
@@ -806,6 +818,8 @@ int dpmm_get_tuning(dpmm_ctx* ctx, dpmm_tuning* t) {
     t->tile_stages = tile_label_stages(c);
     t->tile_scatter = c.tune_tile_scatter ? c.tune_tile_scatter : 12;
     t->draw_blocks_per_sm = c.tune_draw_per_sm ? c.tune_draw_per_sm : 2;
+    t->local_lanes = local_lanes(c);
+    t->local_group_form = c.tune_local_group_form;
     return DPMM_OK;
 }
 

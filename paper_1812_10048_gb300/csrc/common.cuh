@@ -10,6 +10,7 @@
 #include <string>
 
 #include "dpmm.h"
+#include "fixedpoint.h"
 
 namespace dpmm {
 
@@ -182,6 +183,8 @@ struct Ctx {
     int32_t tune_tile_stages = 0;   // label-kernel A/B stages (2 or 4)
     int32_t tune_tile_scatter = 0;  // producer entries per lane and batch (8, 12, 16)
     int32_t tune_draw_per_sm = 0;   // draw-kernel blocks per SM (1 or 2)
+    int32_t tune_local_lanes = 0;   // local sub-label kernel lanes per cell (4 .. 32)
+    int32_t tune_local_group_form = 0;  // 1: local sub-labels in the group form only
 
 
     // chains this context's launches walk: itself (nchains = 1) or, for a
@@ -219,7 +222,9 @@ struct Ctx {
 // ---------------------------------------------------------------------------
 constexpr double kLogqScale = 4294967296.0;
 __device__ __forceinline__ unsigned long long logq_fixed(float logq) {
-    return (unsigned long long)__double2ll_rn((double)logq * kLogqScale);
+    // integer-only (fixedpoint.h): equal to rounding the exact logq * 2^32 to
+    // nearest even, without the FP64 pipe
+    return (unsigned long long)fixed32_from_float(logq);
 }
 __host__ __device__ __forceinline__ double logq_value(unsigned long long acc) {
     return (double)(long long)acc * (1.0 / kLogqScale);
@@ -585,6 +590,7 @@ cudaError_t launch_tile_stats(Ctx& c);
 size_t tile_b_bytes(int32_t C);
 int32_t tile_stat_groups(const Ctx& c);
 int32_t tile_label_stages(const Ctx& c);
+int32_t local_lanes(const Ctx& c);
 cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, int N, float* C,
                                  int* err);
 

@@ -13,7 +13,10 @@
 //   k_stats         recount of reset clusters; bumps the sweep counter t
 #include <math_constants.h>
 
+#include <climits>
+
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace dpmm {
 
@@ -310,144 +313,590 @@ __device__ __forceinline__ uint32_t draw_sublabel(const ChainArgs& a, int64_t ce
 
 // Local Gibbs iteration, second half: labels held, every cell's sub-label
 // drawn from eq. 8 under the new theta-bar (weights n-bar_{r, not i} from the
-// current counts).  The chains of the table are taken in turn.  A chain's
-// cells are dealt round-robin to groups of LANES lanes (LANES chosen from the
-// mean row length); the lanes of a group keep eight row entries each in
-// flight, and the group's first lane draws the cell's sub-label and log q_i.
+// current counts).  Block b takes the cells [b Ntot / G, (b + 1) Ntot / G) of
+// the table's chains in order (Ntot cells in all, G blocks), chain by chain,
+// in one of two forms (below): streamed through a shared-memory ring, or in
+// groups of LANES lanes that read the rows from global memory.  Either way
+// the eq. 8 decisions are batched so that they run on all 32 lanes of a warp.
+//
+// The contraction sum_u x_i^u log theta-bar_{c,r}^u has one fixed FP32 order
+// whatever LANES is: entry i of the row (0-based) belongs to slot i mod 32;
+// a slot sums its entries in row order (FMA); the 32 slot sums are combined
+// by the butterfly over slot distance 16, 8, 4, 2, 1 (at each level both
+// partners form the same sum, addition being commutative).  A lane holds
+// slots sl, sl + LANES, ...; the levels at distance >= LANES combine slots
+// within the lane, the others through shuffles.  A cell's sums thus depend
+// only on its row and the table, so a chain gives the same sub-labels alone
+// or in a batch, with any lane count.
+//
 // The chain's theta-bar pairs of its K clusters are staged in shared memory
-// as a [D][K] table when they fit (by the blocks that hold cells of the
+// as a [D][K | 1] table when they fit (by the blocks that hold cells of the
 // chain), so each gather is a shared-memory load instead of an 8-byte load
-// 2 KB away from its neighbour in the gene-major global table.  A cell's sums
-// depend only on its row, so a chain gives the same sub-labels alone or in a
-// batch.  log q_i is summed per cluster in the block (exact integer units,
-// see logq_fixed), then into the accumulator.  A chain with the blocked copy
-// also has its main S-bar rows cleared here (the tile statistics kernel
-// recounts into them; nothing reads them after the theta-bar draw).
+// 2 KB away from its neighbour in the gene-major global table.  log q_i is
+// summed per cluster in the block (exact integer units, see logq_fixed), then
+// into the accumulator.  A chain with the blocked copy also has its main
+// S-bar rows cleared here (the tile statistics kernel recounts into them;
+// nothing reads them after the theta-bar draw).
 constexpr int kLocalThreads = 1024;
-constexpr int kLocalInFlight = 8;
+constexpr int kLocalInFlight = 8;   // row entries a lane loads before it gathers
 
-template <int LANES>
-__device__ __forceinline__ float2 sub_scores_group(const Csr& csr, int64_t beg, int64_t end,
+// One 32-entry step of a row: entries i0 + sl + LANES m (m < 32 / LANES) of
+// the slots this lane holds; p points at entry i0 + sl.  Past len (checked
+// when kTail) an entry is gene 0 with count 0, which adds exactly nothing
+// (the log theta-bar values are finite).
+template <int LANES, bool kPacked, bool kTail>
+__device__ __forceinline__ void slot_step(const Csr& csr, int64_t p, int rem,
+                                          uint32_t (&u)[32 / LANES], uint32_t (&x)[32 / LANES]) {
+    constexpr int M = 32 / LANES;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        u[m] = 0u;
+        x[m] = 0u;
+        if (!kTail || LANES * m < rem) {
+            if (kPacked) {
+                const uint32_t v = __ldg(csr.entries + p + LANES * m);
+                u[m] = v >> 16;
+                x[m] = v & 0xFFFFu;
+            } else {
+                u[m] = (uint32_t)__ldg(csr.cols + p + LANES * m);
+                x[m] = (uint32_t)__ldg(csr.counts + p + LANES * m);
+            }
+        }
+    }
+}
+
+// Sums of x * theta-bar.x and x * theta-bar.y over the row [beg, beg + len)
+// in the slot order above; every lane of the group returns the full sums.
+// L: the chain's theta-bar pairs, L[u * ld + c] for gene u (shared memory
+// when staged).  Passes of kLocalInFlight / M steps load all their entries
+// before the gathers; the rest of the row goes one checked step at a time.
+template <int LANES, bool kPacked>
+__device__ __forceinline__ float2 sub_scores_slots(const Csr& csr, int64_t beg, int len,
                                                    const float2* __restrict__ L, int ld, int c,
                                                    int sl, unsigned gmask) {
-    float t0 = 0.0f, t1 = 0.0f;
-    for (int64_t e0 = beg + sl; e0 < end; e0 += kLocalInFlight * LANES) {
-        int32_t u[kLocalInFlight], x[kLocalInFlight];
+    constexpr int M = 32 / LANES;                         // slots per lane
+    constexpr int U = kLocalInFlight / M > 0 ? kLocalInFlight / M : 1;   // steps per pass
+    const float2* __restrict__ Lc = L + c;
+    float ax[M], ay[M];
 #pragma unroll
-        for (int q = 0; q < kLocalInFlight; ++q) {
-            u[q] = 0;
-            x[q] = 0;
-            if (e0 + LANES * q < end) csr.get(e0 + LANES * q, u[q], x[q]);
+    for (int m = 0; m < M; ++m) ax[m] = ay[m] = 0.0f;
+    auto add = [&](const uint32_t (&u)[M], const uint32_t (&x)[M]) {
+        float2 l[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) l[m] = Lc[u[m] * (uint32_t)ld];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            ax[m] = fmaf((float)x[m], l[m].x, ax[m]);
+            ay[m] = fmaf((float)x[m], l[m].y, ay[m]);
         }
-        float2 l[kLocalInFlight];
+    };
+    const int64_t p0 = beg + sl;
+    int i0 = 0;
+    for (; i0 + 32 * U <= len; i0 += 32 * U) {
+        uint32_t u[U][M], x[U][M];
 #pragma unroll
-        for (int q = 0; q < kLocalInFlight; ++q)
-            l[q] = x[q] ? L[(int64_t)u[q] * ld + c] : make_float2(0.0f, 0.0f);
+        for (int s = 0; s < U; ++s)
+            slot_step<LANES, kPacked, false>(csr, p0 + i0 + 32 * s, 0, u[s], x[s]);
 #pragma unroll
-        for (int q = 0; q < kLocalInFlight; ++q) {
-            t0 = fmaf((float)x[q], l[q].x, t0);
-            t1 = fmaf((float)x[q], l[q].y, t1);
-        }
+        for (int s = 0; s < U; ++s) add(u[s], x[s]);
+    }
+    for (; i0 < len; i0 += 32) {
+        uint32_t u[M], x[M];
+        slot_step<LANES, kPacked, true>(csr, p0 + i0, len - i0 - sl, u, x);
+        add(u, x);
     }
 #pragma unroll
-    for (int o = LANES / 2; o; o >>= 1) {
-        t0 += __shfl_xor_sync(gmask, t0, o);
-        t1 += __shfl_xor_sync(gmask, t1, o);
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (o >= LANES) {
+            const int k = o / LANES;
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                if (!(m & k)) {
+                    const float sx = ax[m] + ax[m ^ k], sy = ay[m] + ay[m ^ k];
+                    ax[m] = ax[m ^ k] = sx;
+                    ay[m] = ay[m ^ k] = sy;
+                }
+        } else {
+            ax[0] += __shfl_xor_sync(gmask, ax[0], o);
+            ay[0] += __shfl_xor_sync(gmask, ay[0], o);
+        }
     }
-    return make_float2(t0, t1);
+    return make_float2(ax[0], ay[0]);
+}
+
+// Group form (rows without the packed copy, or a table that leaves no room
+// for the ring): batches of one chain's cells below N for the warp.  Lane
+// q = R NG + g of the warp owns group g's cell of round R (group g: lanes
+// LANES g ..; its cells first_g, first_g + G, ...): it loads that cell's
+// state and row bounds at the start of the batch, the group takes them by
+// shuffle in round R, and after the batch's LANES rounds lane q holds the
+// cell's sums and draws it.
+template <int LANES, bool kPacked>
+__device__ __forceinline__ void local_sub_chain(const ChainArgs& ch, const float2* __restrict__ L,
+                                                int ld, int64_t first_l, int64_t G, int64_t N,
+                                                uint32_t tag, uint32_t t,
+                                                unsigned long long* bsq) {
+    constexpr int NG = 32 / LANES;
+    const int lane = threadIdx.x & 31;
+    const int sl = lane % LANES, g = lane / LANES;
+    const unsigned gmask = (LANES == 32 ? 0xFFFFFFFFu : ((1u << LANES) - 1u)) << (lane - sl);
+    const int src = (lane % NG) * LANES;    // a lane of the group whose cell this lane draws
+    for (int64_t r0 = 0;; r0 += LANES) {
+        const int64_t my = first_l + G * (r0 + lane / NG);
+        const bool valid = my < N;
+        if (!__any_sync(0xFFFFFFFFu, valid)) break;
+        uint32_t mst = 0u;
+        long long mbeg = 0;
+        int mlen = 0;
+        if (valid) {
+            mst = ch.state[my];
+            mbeg = ch.csr.indptr[my];
+            mlen = (int)(ch.csr.indptr[my + 1] - mbeg);
+        }
+        float2 mine = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+        for (int rr = 0; rr < LANES; ++rr) {
+            const int q = rr * NG + g;           // the lane that owns this group's cell
+            if (!__any_sync(0xFFFFFFFFu, lane / NG == rr && valid)) break;
+            const uint32_t st = __shfl_sync(0xFFFFFFFFu, mst, q);
+            const long long beg = __shfl_sync(0xFFFFFFFFu, mbeg, q);
+            const int len = __shfl_sync(0xFFFFFFFFu, mlen, q);
+            const float2 lik = sub_scores_slots<LANES, kPacked>(ch.csr, beg, len, L, ld,
+                                                               (int)state_label(st), sl, gmask);
+            const float lx = __shfl_sync(0xFFFFFFFFu, lik.x, src);
+            const float ly = __shfl_sync(0xFFFFFFFFu, lik.y, src);
+            if (lane / NG == rr) mine = make_float2(lx, ly);
+        }
+        local_draw_held(ch, valid ? my : -1, mst, mine, tag, t, bsq);
+    }
+}
+
+// Streamed form (packed rows, staged table): the block's cells in chunks of
+// at most 62 consecutive whole rows (at most kLocalSlotEntries - 6 entries;
+// a longer row is a chunk of its own, read from global memory).  Warp 31
+// produces: per chunk it waits for the ring slot to be released, writes the
+// chunk's cells, row offsets and states to the slot's header and bulk-copies
+// the rows (16-byte aligned span) into the slot; the row bounds and states
+// come from a shared-memory window of kLocalWin cells (the whole block loads
+// the first, the producer the next ones).  Warps 0-30 consume: half g of
+// warp w contracts cell w + 31 g of every chunk (16 lanes, the slot order
+// above), the warp keeps the sums of its last 16 chunks one cell per lane and
+// then draws those 32 cells at once.  A chunk with m < 0 ends the range.
+constexpr int kLocalSlotBytes = 36864;
+constexpr uint32_t kLocalWaitLimit = 1u << 24;   // mbarrier polls before giving up
+constexpr int kLocalSlotEntries = kLocalSlotBytes / 4;
+constexpr int kLocalMaxSlots = 6;
+constexpr int kLocalConsumers = 31;
+constexpr int kLocalChunkCells = 2 * kLocalConsumers;
+constexpr int kLocalWin = 1024;     // cells of row bounds and states the producer holds
+constexpr int kLocalWinOff = 8 * kMaxKmax + 2048 + 4096;
+// bsq, barriers, chunk headers, window (row bounds, states)
+constexpr int kLocalHdr = kLocalWinOff + 4 * (kLocalWin + 64) + 4 * kLocalWin;
+
+struct LocalChunk {
+    long long c0;                   // first cell
+    int32_t m, flags;               // cells (< 0: end); 1: one row read from global memory
+    long long gbeg;                 // that row's first entry
+    int32_t off[kLocalChunkCells + 2];   // row r spans off[r] .. off[r + 1] in the slot
+    uint32_t st[kLocalChunkCells + 2];   // the cells' states
+};
+static_assert(kLocalMaxSlots * sizeof(LocalChunk) <= 4096, "chunk headers exceed their area");
+
+// Row stride (in pairs) of the staged table: K rounded up to odd, so that
+// the pairs of one cluster for 32 random genes spread over 16 bank pairs.
+__host__ __device__ __forceinline__ int staged_ld(int K) { return K | 1; }
+
+// One chain's theta-bar pairs of its K clusters into shared memory as [D][ld]
+// (eight loads in flight per thread).
+__device__ __forceinline__ void stage_table(float2* sL, const float2* __restrict__ Ls2, int D,
+                                            int K, int kmax) {
+    const int tot = D * K, ld = staged_ld(K);
+    for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * (int)blockDim.x) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q * (int)blockDim.x;
+            if (i < tot) {
+                const int u = i / K;
+                v[q] = __ldg(Ls2 + (size_t)u * kmax + (i - u * K));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q * (int)blockDim.x;
+            if (i < tot) {
+                const int u = i / K;
+                sL[u * ld + (i - u * K)] = v[q];
+            }
+        }
+    }
+}
+
+// 16-lane sums of one row in the slot order (p: the row's first entry; kGlobal:
+// p in global memory).  sl: lane within the half warp, gmask: the half's lanes.
+template <bool kGlobal>
+__device__ __forceinline__ float2 row_sums16(const uint32_t* p, int len,
+                                             const float2* __restrict__ Lc, int ld, int sl,
+                                             unsigned gmask) {
+    float ax[2] = {0.0f, 0.0f}, ay[2] = {0.0f, 0.0f};
+    auto ld32 = [&](int i) -> uint32_t { return kGlobal ? __ldg(p + i) : p[i]; };
+    int i0 = 0;
+    for (; i0 + 128 <= len; i0 += 128) {
+        uint32_t v[4][2];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int m = 0; m < 2; ++m) v[s][m] = ld32(i0 + 32 * s + sl + 16 * m);
+        float2 l[4][2];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int m = 0; m < 2; ++m) l[s][m] = Lc[(v[s][m] >> 16) * (uint32_t)ld];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                ax[m] = fmaf((float)(v[s][m] & 0xFFFFu), l[s][m].x, ax[m]);
+                ay[m] = fmaf((float)(v[s][m] & 0xFFFFu), l[s][m].y, ay[m]);
+            }
+    }
+    for (; i0 < len; i0 += 32) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int i = i0 + sl + 16 * m;
+            const uint32_t v = i < len ? ld32(i) : 0u;     // beyond the row: gene 0, count 0
+            const float2 l = Lc[(v >> 16) * (uint32_t)ld];
+            ax[m] = fmaf((float)(v & 0xFFFFu), l.x, ax[m]);
+            ay[m] = fmaf((float)(v & 0xFFFFu), l.y, ay[m]);
+        }
+    }
+    // butterfly: distance 16 within the lane, then 8 .. 1 across the half
+    float sx = ax[0] + ax[1], sy = ay[0] + ay[1];
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+        sx += __shfl_xor_sync(gmask, sx, o);
+        sy += __shfl_xor_sync(gmask, sy, o);
+    }
+    return make_float2(sx, sy);
+}
+
+// Adds each lane's q (exact integer units) into bsq[c] of its cluster c (c < 0:
+// nothing): one shared-memory atomic per distinct cluster of the warp, the
+// lanes of a cluster summed by shuffles first (integer sums: any order).
+// Called by all 32 lanes.
+__device__ __forceinline__ void warp_add_by_cluster(unsigned long long* bsq, int c,
+                                                    unsigned long long q) {
+    const int lane = threadIdx.x & 31;
+    unsigned todo = __ballot_sync(0xFFFFFFFFu, c >= 0);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int cl = __shfl_sync(0xFFFFFFFFu, c, leader);
+        const unsigned same = __ballot_sync(0xFFFFFFFFu, c == cl);
+        unsigned long long v = c == cl ? q : 0ull;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if (lane == leader && v) atomicAdd(&bsq[cl], v);
+        todo &= ~same;
+    }
+}
+
+// eq. 8 draws of the cells a consumer warp holds (one per lane, cell < 0:
+// none).  Called by all 32 lanes.
+__device__ __forceinline__ void local_draw_held(const ChainArgs& ch, long long cell, uint32_t st,
+                                                float2 lik, uint32_t tag, uint32_t t,
+                                                unsigned long long* bsq) {
+    int c = -1;
+    unsigned long long q = 0ull;
+    if (cell >= 0) {
+        c = (int)state_label(st);
+        float logq;
+        const uint32_t s = draw_sublabel_n(ch.st, cell, c, st, ch.nsub[2 * c],
+                                           ch.nsub[2 * c + 1], lik, tag, t, &logq);
+        ch.state[cell] = pack_state((uint32_t)c, s);
+        q = logq_fixed(logq);
+    }
+    warp_add_by_cluster(bsq, c, q);
+}
+
+// One chain's cells [lo, hi) of this block in the streamed form.  full / empty:
+// the slots' barriers; fpar / epar / used: this thread's parity and use bits
+// per slot (they persist across chains; the producer's fpar counts the
+// phases it started); jj: the block's chunk counter; wip / wst: the window.
+// Returns false after a timed-out wait (the error is recorded).
+__device__ __forceinline__ bool local_stream_chain(const ChainArgs& ch, int64_t lo, int64_t hi,
+                                                  const float2* __restrict__ sL, int K,
+                                                  unsigned char* ring, int NS, uint64_t* full,
+                                                  uint64_t* empty, LocalChunk* hdr,
+                                                  uint32_t& fpar, uint32_t& epar, uint32_t& used,
+                                                  uint32_t& jj, uint32_t tag, uint32_t t,
+                                                  unsigned long long* bsq, volatile int* stop,
+                                                  int32_t* wip, uint32_t* wst) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t* __restrict__ indptr = ch.csr.indptr;
+    bool ok = true;
+    if (warp == kLocalConsumers) {
+        // ---------------- producer ----------------
+        int64_t cur = lo;
+        int64_t wb = lo;                                     // window: cells wb .. wb + wn
+        int64_t wn = min((int64_t)kLocalWin, hi - lo);
+        for (;;) {
+            const int s = (int)(jj % (uint32_t)NS);
+            if ((used >> s) & 1u) {
+                int bad = 0;
+                if (lane == 0) {
+                    const bool w = tc::mbar_wait(&empty[s], (epar >> s) & 1u, kLocalWaitLimit);
+                    if (!w) {
+                        *stop = 1;
+                        atomicExch(&ch.sc->error, DPMM_ETIMEOUT);
+                    }
+                    bad = !w || *stop;
+                }
+                epar ^= 1u << s;
+                if (__shfl_sync(0xFFFFFFFFu, bad, 0)) ok = false;
+            }
+            used |= 1u << s;
+            LocalChunk& h = hdr[s];
+            if (!ok || cur >= hi) {
+                if (lane == 0) {
+                    h.m = -1;
+                    tc::mbar_arrive(&full[s]);
+                }
+                fpar ^= 1u << s;
+                ++jj;
+                break;
+            }
+            if (min(cur + kLocalChunkCells, hi) > wb + wn) {
+                // the chunk may reach past the window: the next window starts here
+                wb = cur;
+                wn = min((int64_t)kLocalWin, hi - cur);
+                for (int k = lane; k <= wn; k += 32) wip[k] = indptr[wb + k];
+                for (int k = lane; k < wn; k += 32) wst[k] = ch.state[wb + k];
+                __syncwarp();
+            }
+            // rows cur .. cur + m - 1: the longest run of at most 62 rows that fits a slot
+            const int32_t* w0 = wip + (cur - wb);            // w0[i] = indptr[cur + i]
+            const int lim = (int)min((int64_t)kLocalChunkCells, hi - cur);   // w0[0 .. lim]
+            const int32_t e_s = w0[0];
+            int m = 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i = 32 * q + lane + 1;             // candidate end row
+                const bool fits = i <= lim && w0[i <= lim ? i : 0] - e_s <= kLocalSlotEntries - 6;
+                const int c = __popc(__ballot_sync(0xFFFFFFFFu, fits));
+                if (m == 32 * q) m += c;
+            }
+            const bool global_row = m == 0;
+            if (global_row) m = 1;
+            const int32_t e_e = w0[m];
+            const int32_t a = e_s & ~3;
+            const int32_t b = global_row ? a : ((e_e + 3) & ~3);
+            for (int i = lane; i < m; i += 32) {
+                h.off[i] = global_row ? 0 : w0[i] - a;
+                h.st[i] = wst[cur - wb + i];
+            }
+            if (lane == 0) {
+                h.off[m] = global_row ? e_e - e_s : e_e - a;
+                h.c0 = cur;
+                h.m = m;
+                h.flags = global_row ? 1 : 0;
+                h.gbeg = e_s;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t bytes = (uint32_t)(b - a) * 4u;
+                if (bytes) {
+                    tc::mbar_arrive_expect_tx(&full[s], bytes);
+                    tc::bulk_g2s(ring + (size_t)s * kLocalSlotBytes, ch.csr.entries + a, bytes,
+                                 &full[s]);
+                } else {
+                    tc::mbar_arrive(&full[s]);
+                }
+            }
+            fpar ^= 1u << s;
+            cur += m;
+            ++jj;
+            __syncwarp();      // the window is read before the next chunk may reload it
+        }
+        if (!ok && lane == 0) {
+            // after a timed-out wait: every copy issued has landed before the
+            // block can exit (the latest use of each slot)
+            for (int q = 0; q < NS; ++q)
+                if ((used >> q) & 1u)
+                    tc::mbar_wait(&full[q], ((fpar >> q) & 1u) ^ 1u, kLocalWaitLimit);
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const int g = lane >> 4, sl = lane & 15;
+        const unsigned gmask = 0xFFFFu << (16 * g);
+        long long hcell = -1;           // held cell of this lane
+        uint32_t hst = 0u;
+        float2 hlik = make_float2(0.0f, 0.0f);
+        int held = 0;
+        for (;;) {
+            const int s = (int)(jj % (uint32_t)NS);
+            bool w = true;
+            if (lane == 0) w = tc::mbar_wait(&full[s], (fpar >> s) & 1u, kLocalWaitLimit);
+            w = __shfl_sync(0xFFFFFFFFu, w, 0);
+            fpar ^= 1u << s;
+            ++jj;
+            if (!w) {
+                if (lane == 0) {
+                    *stop = 1;
+                    atomicExch(&ch.sc->error, DPMM_ETIMEOUT);
+                }
+                ok = false;
+                break;
+            }
+            const LocalChunk& h = hdr[s];
+            const int m = h.m;
+            if (m < 0) {
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&empty[s]);
+                break;
+            }
+            const int ci = warp + kLocalConsumers * g;      // this half's cell of the chunk
+            long long cell = -1;
+            uint32_t st = 0u;
+            float2 lik = make_float2(0.0f, 0.0f);
+            if (ci < m) {
+                cell = h.c0 + ci;
+                st = h.st[ci];
+                const int o0 = h.off[ci], len = h.off[ci + 1] - o0;
+                const float2* Lc = sL + state_label(st);
+                if (h.flags & 1)
+                    lik = row_sums16<true>(ch.csr.entries + h.gbeg, len, Lc, staged_ld(K), sl,
+                                           gmask);
+                else
+                    lik = row_sums16<false>(reinterpret_cast<const uint32_t*>(
+                                                ring + (size_t)s * kLocalSlotBytes) + o0,
+                                            len, Lc, staged_ld(K), sl, gmask);
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&empty[s]);
+            // the two halves' cells go to lanes held and held + 1
+            const long long c1 = __shfl_sync(0xFFFFFFFFu, cell, 16);
+            const uint32_t s1 = __shfl_sync(0xFFFFFFFFu, st, 16);
+            const float l1x = __shfl_sync(0xFFFFFFFFu, lik.x, 16);
+            const float l1y = __shfl_sync(0xFFFFFFFFu, lik.y, 16);
+            const long long c0 = __shfl_sync(0xFFFFFFFFu, cell, 0);
+            const uint32_t s0 = __shfl_sync(0xFFFFFFFFu, st, 0);
+            const float l0x = __shfl_sync(0xFFFFFFFFu, lik.x, 0);
+            const float l0y = __shfl_sync(0xFFFFFFFFu, lik.y, 0);
+            if (lane == held) {
+                hcell = c0;
+                hst = s0;
+                hlik = make_float2(l0x, l0y);
+            } else if (lane == held + 1) {
+                hcell = c1;
+                hst = s1;
+                hlik = make_float2(l1x, l1y);
+            }
+            held += 2;
+            if (held == 32) {
+                local_draw_held(ch, hcell, hst, hlik, tag, t, bsq);
+                hcell = -1;
+                held = 0;
+            }
+        }
+        if (ok) local_draw_held(ch, hcell, hst, hlik, tag, t, bsq);
+    }
+    return ok;
 }
 
 template <int LANES, class Tab>
 __global__ void __launch_bounds__(kLocalThreads, 1)
-k_local_sub(const __grid_constant__ Tab tab, int32_t j, int64_t smem_bytes) {
-    extern __shared__ __align__(16) unsigned char smem_local[];
+k_local_sub(const __grid_constant__ Tab tab, int32_t j, int64_t smem_bytes, int32_t group_form) {
+    extern __shared__ __align__(128) unsigned char smem_local[];
     unsigned long long* bsq = reinterpret_cast<unsigned long long*>(smem_local);   // [kMaxKmax]
-    float2* sL = reinterpret_cast<float2*>(smem_local + 8 * kMaxKmax);             // [D][K]
-    if (smem_bytes < (int64_t)8 * kMaxKmax) {
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_local + 8 * kMaxKmax);      // [6]
+    uint64_t* empty = full + kLocalMaxSlots;                                       // [6]
+    volatile int* stop = reinterpret_cast<volatile int*>(empty + kLocalMaxSlots);
+    LocalChunk* hdr = reinterpret_cast<LocalChunk*>(smem_local + 8 * kMaxKmax + 2048);
+    int32_t* wip = reinterpret_cast<int32_t*>(smem_local + kLocalWinOff);           // [kLocalWin + 1]
+    uint32_t* wst = reinterpret_cast<uint32_t*>(wip + kLocalWin + 64);              // [kLocalWin]
+    float2* sL = reinterpret_cast<float2*>(smem_local + kLocalHdr);                 // [D][K]
+    if (smem_bytes < (int64_t)kLocalHdr) {
         // launched without room for the per-cluster sums: report, touch nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&tab[0].sc->error, DPMM_ECAPACITY);
         return;
     }
     const uint32_t tag = kLocalTag0 + 2u * (uint32_t)(j - 1) + 1u;
     const int lane = threadIdx.x & 31;
-    const int sl = lane % LANES;                                // lane within the cell group
-    const unsigned gmask = (LANES == 32 ? 0xFFFFFFFFu : ((1u << LANES) - 1u)) << (lane - sl);
-    const int64_t ngb = blockDim.x / LANES;                     // groups per block
-    const int64_t G = (int64_t)gridDim.x * ngb;
-    const int64_t gid = (int64_t)blockIdx.x * ngb + threadIdx.x / LANES;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    int64_t ntot = 0;
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
+        ntot += ch.N;
         if (ch.tile_enabled)
             for (int64_t i = tid; i < (int64_t)2 * ch.sc->K * ch.D; i += nthr) ch.Ssub[i] = 0u;
     }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kLocalMaxSlots; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], kLocalConsumers);
+        }
+        *stop = 0;
+        tc::fence_mbar_init();
+    }
+    // this block's cells: [A, B) of the chains' cells in table order
+    const int64_t A = ntot * blockIdx.x / gridDim.x, B = ntot * (blockIdx.x + 1) / gridDim.x;
+    uint32_t fpar = 0u, epar = 0u, used = 0u, jj = 0u;
     int64_t base = 0;
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
-        const int K = ch.sc->K, D = ch.D, kmax = ch.kmax;
         const int64_t N = ch.N;
+        const int64_t lo = max(A - base, (int64_t)0), hi = min(B - base, N);
+        base += N;
+        if (lo >= hi) continue;
+        const int K = ch.sc->K, D = ch.D, kmax = ch.kmax;
         const uint32_t t = ch.sc->t - 1u;
-        const int64_t first = base + ((gid - base) % G + G) % G;
-        const bool mine = first < base + N;
-        if (!__syncthreads_or(mine ? 1 : 0)) {
-            base += N;
-            continue;
-        }
-        const bool staged = (int64_t)8 * kMaxKmax + (int64_t)D * K * 8 <= smem_bytes;
+        const int64_t table = (int64_t)D * staged_ld(K) * 8;
+        const bool staged = kLocalHdr + table <= smem_bytes;
+        const int64_t ring_off = (kLocalHdr + table + 127) & ~(int64_t)127;
+        const int NS = (int)min((int64_t)kLocalMaxSlots,
+                                max((int64_t)0, (smem_bytes - ring_off) / kLocalSlotBytes));
+        const bool streamed = !group_form && staged && ch.csr.entries != nullptr && NS >= 2;
         const float2* __restrict__ Ls2 = reinterpret_cast<const float2*>(ch.Ls);
-        for (int i = threadIdx.x; i < K; i += blockDim.x) bsq[i] = 0ull;
-        if (staged)
-            for (int64_t i = threadIdx.x; i < (int64_t)D * K; i += blockDim.x) {
-                const int64_t u = i / K, k = i - u * K;
-                sL[i] = __ldg(Ls2 + u * kmax + k);
-            }
         __syncthreads();
-        const float2* L = staged ? sL : Ls2;
-        const int ld = staged ? K : kmax;
-        int64_t cell = first - base;
-        uint32_t st = 0u;
-        int64_t beg = 0, end = 0;
-        if (cell < N) {
-            st = ch.state[cell];
-            beg = ch.csr.indptr[cell];
-            end = ch.csr.indptr[cell + 1];
+        for (int i = threadIdx.x; i < K; i += blockDim.x) bsq[i] = 0ull;
+        if (staged) stage_table(sL, Ls2, D, K, kmax);
+        if (streamed) {
+            // the producer's first window of row bounds and states
+            const int64_t wn = min((int64_t)kLocalWin, hi - lo);
+            for (int k = threadIdx.x; k <= wn; k += blockDim.x) wip[k] = ch.csr.indptr[lo + k];
+            for (int k = threadIdx.x; k < wn; k += blockDim.x) wst[k] = ch.state[lo + k];
         }
-        while (cell < N) {
-            const int c = (int)state_label(st);
-            uint32_t n0 = 0u, n1 = 0u;
-            if (sl == 0) {
-                n0 = ch.nsub[2 * c];
-                n1 = ch.nsub[2 * c + 1];
+        // the table's generic writes are ordered before the ring's bulk copies
+        // into the same bytes (the ring moves with the table's size)
+        tc::fence_async_smem();
+        __syncthreads();
+        if (streamed) {
+            const bool ok = local_stream_chain(ch, lo, hi, sL, K, smem_local + ring_off, NS, full,
+                                               empty, hdr, fpar, epar, used, jj, tag, t, bsq,
+                                               stop, wip, wst);
+            if (__syncthreads_or(ok ? 0 : 1)) break;
+        } else {
+            // groups of LANES lanes over the block's cells lo + g, lo + g + groups, ...
+            const int64_t ngb = blockDim.x / LANES;
+            const int64_t first_l = lo + (threadIdx.x & ~31) / LANES + lane % (32 / LANES);
+            if (staged) {
+                if (ch.csr.entries)
+                    local_sub_chain<LANES, true>(ch, sL, staged_ld(K), first_l, ngb, hi, tag, t,
+                                                  bsq);
+                else
+                    local_sub_chain<LANES, false>(ch, sL, staged_ld(K), first_l, ngb, hi, tag, t,
+                                                   bsq);
+            } else {
+                if (ch.csr.entries)
+                    local_sub_chain<LANES, true>(ch, Ls2, kmax, first_l, ngb, hi, tag, t, bsq);
+                else
+                    local_sub_chain<LANES, false>(ch, Ls2, kmax, first_l, ngb, hi, tag, t, bsq);
             }
-            // the next cell's state and row bounds load while this one is contracted
-            const int64_t cn = cell + G;
-            uint32_t stn = 0u;
-            int64_t begn = 0, endn = 0;
-            if (cn < N) {
-                stn = ch.state[cn];
-                begn = ch.csr.indptr[cn];
-                endn = ch.csr.indptr[cn + 1];
-            }
-            const float2 lik = sub_scores_group<LANES>(ch.csr, beg, end, L, ld, c, sl, gmask);
-            if (sl == 0) {
-                float logq;
-                const uint32_t s = draw_sublabel_n(ch.st, cell, c, st, n0, n1, lik, tag, t,
-                                                   &logq);
-                ch.state[cell] = pack_state((uint32_t)c, s);
-                const unsigned long long q = logq_fixed(logq);
-                if (q) atomicAdd(&bsq[c], q);
-            }
-            cell = cn;
-            st = stn;
-            beg = begn;
-            end = endn;
         }
         __syncthreads();
         for (int k = threadIdx.x; k < K; k += blockDim.x)
             if (bsq[k]) atomicAdd(&ch.acc_logq[k], bsq[k]);
-        __syncthreads();
-        base += N;
     }
 }
 
@@ -1042,23 +1491,32 @@ cudaError_t launch_open_slot(Ctx& c) {
     });
 }
 
+// Lanes per cell of the local sub-label kernel: tuned, else the power of two
+// nearest below mean row length / kLocalInFlight, within [4, 32].  Any value
+// gives the same sums (fixed slot order).
+int32_t local_lanes(const Ctx& c) {
+    if (c.tune_local_lanes) return c.tune_local_lanes;
+    const int64_t mean = c.mean_row;
+    return mean < 8 * kLocalInFlight ? 4 : mean < 16 * kLocalInFlight ? 8
+                                         : mean < 32 * kLocalInFlight ? 16 : 32;
+}
+
 // One local Gibbs iteration j >= 1 (after the sweep's compaction).
 cudaError_t launch_local_iteration(Ctx& c, int32_t j) {
     cudaError_t e = with_table(c, [&](auto tab) {
         k_draw_local<<<2 * c.num_sms, kDrawThreads, 0, c.stream>>>(tab, j);
-        // lanes per cell: the power of two nearest below mean row length /
-        // kLocalInFlight, within [4, 32] (one or two passes per lane)
-        const int64_t mean = c.mean_row;
+        const int lanes = local_lanes(c);
+        const int32_t gf = c.tune_local_group_form;
         const dim3 grid(c.num_sms);
         const int64_t sm = (int64_t)c.local_smem;
-        if (mean < 8 * kLocalInFlight)
-            k_local_sub<4><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
-        else if (mean < 16 * kLocalInFlight)
-            k_local_sub<8><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
-        else if (mean < 32 * kLocalInFlight)
-            k_local_sub<16><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
+        if (lanes == 4)
+            k_local_sub<4><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm, gf);
+        else if (lanes == 8)
+            k_local_sub<8><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm, gf);
+        else if (lanes == 16)
+            k_local_sub<16><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm, gf);
         else
-            k_local_sub<32><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm);
+            k_local_sub<32><<<grid, kLocalThreads, c.local_smem, c.stream>>>(tab, j, sm, gf);
         if (!c.tile_enabled)
             k_stats<<<c.stats_blocks, kStatsThreads, c.stats_smem, c.stream>>>(
                 tab, (int64_t)(c.stats_smem / sizeof(uint32_t)), 2);

@@ -55,30 +55,33 @@ def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
         _lib.lib()
 
 
-def test_options_struct_layout_matches_the_header(tmp_path):
-    """The ctypes mirror of dpmm_opts has the header's size and field offsets
-    (a C program compiled against include/dpmm.h prints them)."""
+@pytest.mark.parametrize("struct", ["dpmm_opts", "dpmm_tuning"])
+def test_struct_layout_matches_the_header(tmp_path, struct):
+    """The ctypes mirrors of dpmm_opts and dpmm_tuning have the header's size
+    and field offsets (a C program compiled against include/dpmm.h prints
+    them)."""
     import shutil
     import subprocess
-    from paper_1812_10048_gb300._lib import dpmm_opts
+    from paper_1812_10048_gb300 import _lib
+    cls = getattr(_lib, struct)
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    fields = [f[0] for f in dpmm_opts._fields_]
+    fields = [f[0] for f in cls._fields_]
     src = tmp_path / "layout.c"
-    body = "".join(f'    printf("%s %zu\\n", "{f}", offsetof(dpmm_opts, {f}));\n' for f in fields)
+    body = "".join(f'    printf("%s %zu\\n", "{f}", offsetof({struct}, {f}));\n' for f in fields)
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "dpmm.h"\n'
                    'int main(void) {\n'
-                   '    printf("sizeof %zu\\n", sizeof(dpmm_opts));\n' + body +
+                   f'    printf("sizeof %zu\\n", sizeof({struct}));\n' + body +
                    '    return 0;\n}\n')
     exe = tmp_path / "layout"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
     out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
                                                        text=True).stdout.splitlines())
-    assert int(out["sizeof"]) == ctypes.sizeof(dpmm_opts)
+    assert int(out["sizeof"]) == ctypes.sizeof(cls)
     for f in fields:
-        assert int(out[f]) == getattr(dpmm_opts, f).offset, f
+        assert int(out[f]) == getattr(cls, f).offset, f
 
 
 def test_binding_argument_counts_match_the_prototypes():

@@ -73,25 +73,39 @@ def run_single(P, ds, tuning, steps=8):
     return snap, tile
 
 
+def lanes_for(nnz, N):
+    """Default lanes per cell of the local sub-label kernel for a mean row."""
+    mean = nnz // N
+    return 4 if mean < 64 else 8 if mean < 128 else 16 if mean < 256 else 32
+
+
 def test_defaults_reported(P, dense):
     s = P.Sampler(dense.indptr, dense.indices, dense.data, dense.N, dense.D, 1.0, 0.5, kmax=32)
+    lanes = lanes_for(int(dense.indptr[-1]), dense.N)
     assert P.dpmm_get_tuning(s.ctx) == {"stats_blocks_per_sm": 4, "tile_stages": 4,
-                                        "tile_scatter": 12, "draw_blocks_per_sm": 2}
-    P.dpmm_set_tuning(s.ctx, tile_stages=2, tile_scatter=16)
+                                        "tile_scatter": 12, "draw_blocks_per_sm": 2,
+                                        "local_lanes": lanes, "local_group_form": 0}
+    P.dpmm_set_tuning(s.ctx, tile_stages=2, tile_scatter=16, local_lanes=32)
     assert P.dpmm_get_tuning(s.ctx) == {"stats_blocks_per_sm": 4, "tile_stages": 2,
-                                        "tile_scatter": 16, "draw_blocks_per_sm": 2}
+                                        "tile_scatter": 16, "draw_blocks_per_sm": 2,
+                                        "local_lanes": 32, "local_group_form": 0}
     P.dpmm_set_tuning(s.ctx)                     # all zero: back to the defaults
     assert P.dpmm_get_tuning(s.ctx)["tile_stages"] == 4
+    assert P.dpmm_get_tuning(s.ctx)["local_lanes"] == lanes
     s.close()
-    b = P.BatchSampler(batch_data(), 320, kmax=16)
+    data = batch_data()
+    b = P.BatchSampler(data, 320, kmax=16)
+    blanes = lanes_for(sum(int(d[0][-1]) for d in data), sum(d[3] for d in data))
     assert P.dpmm_get_tuning(b.ctx) == {"stats_blocks_per_sm": 2, "tile_stages": 2,
-                                        "tile_scatter": 12, "draw_blocks_per_sm": 2}
+                                        "tile_scatter": 12, "draw_blocks_per_sm": 2,
+                                        "local_lanes": blanes, "local_group_form": 0}
     b.close()
 
 
 @pytest.mark.parametrize("bad", [{"stats_blocks_per_sm": 3}, {"tile_stages": 3},
                                  {"tile_scatter": 10}, {"draw_blocks_per_sm": 4},
-                                 {"tile_stages": -1}])
+                                 {"tile_stages": -1}, {"local_lanes": 2}, {"local_lanes": 64},
+                                 {"local_group_form": 2}])
 def test_invalid_tuning_rejected(P, dense, bad):
     s = P.Sampler(dense.indptr, dense.indices, dense.data, dense.N, dense.D, 1.0, 0.5, kmax=32)
     before = P.dpmm_get_tuning(s.ctx)

@@ -130,6 +130,87 @@ def test_batched_local_iterations_equal_single_chains(P):
         s.close()
 
 
+FORMS = [{"local_group_form": 1, "local_lanes": v} for v in (4, 8, 16, 32)] + [{"local_lanes": 4}]
+
+
+def same_chain(x, y, what):
+    (sx, tx), (sy, ty) = x, y
+    assert sx[2:] == sy[2:], what
+    for a, c in zip(sx[:2] + tuple(tx), sy[:2] + tuple(ty)):
+        np.testing.assert_array_equal(a, c, err_msg=what)
+
+
+@pytest.mark.parametrize("engine", ["auto", "csr"])
+def test_local_forms_give_identical_chains(P, tiny, engine):
+    """The contraction's FP32 order is fixed, so the streamed form and the
+    group form with any lanes per cell give bit-identical chains (single and
+    batched, the batch with one chain lacking the packed rows)."""
+    eng = {"auto": P.ENGINE_AUTO, "csr": P.ENGINE_CSR_FP32}[engine]
+
+    def single(tu):
+        s = P.Sampler(tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5, kmax=32,
+                      seed=21, engine=eng, local_iters=3)
+        if tu:
+            P.dpmm_set_tuning(s.ctx, **tu)
+        s.step(6)
+        out = (s.get_state(), s.stats())
+        s.close()
+        return out
+
+    def batched(tu, big):
+        b = P.BatchSampler(datasets(big_count=big), 300, 1.0, 0.5, kmax=32, seed=9, chain_id=4,
+                           engine=eng, local_iters=3)
+        if tu:
+            P.dpmm_set_tuning(b.ctx, **tu)
+        b.step(4)
+        out = [(b.chain(i).get_state(), b.chain(i).stats()) for i in range(b.B)]
+        b.close()
+        return out
+
+    ref = single(None)
+    brefs = {big: batched(None, big) for big in (False, True)}
+    for tu in FORMS:
+        same_chain(single(tu), ref, str(tu))
+        for big in (False, True):
+            for i, (x, y) in enumerate(zip(batched(tu, big), brefs[big])):
+                same_chain(x, y, f"{tu} big={big} chain {i}")
+
+
+def test_local_streamed_form_rows_longer_than_a_slot(P):
+    """Rows of more than 10,234 entries (a ring slot less the alignment
+    margin) go around the ring (read from global memory) and give the same
+    sub-labels as the group form; so does a block range longer than the
+    producer's 1,024-cell window."""
+    rng = np.random.default_rng(77)
+    N, D = 160_000, 12_000
+    lens = rng.integers(1, 60, size=N)
+    lens[[3, 250, 251, 252, 700, 159_999]] = [8700, 10234, 10235, 12_000, 11_000, 7200]
+    indptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    # distinct columns per row: (7 row + 131 j) mod D, j < n (131 is prime to D), sorted
+    row = np.repeat(np.arange(N), lens)
+    j = np.arange(indptr[-1]) - np.repeat(indptr[:-1], lens)
+    cols = (7 * row + 131 * j) % D
+    order = np.lexsort((cols, row))
+    indices = cols[order]
+    data = rng.integers(1, 30, size=indptr[-1])
+
+    def run(tu):
+        s = P.Sampler(indptr, indices.astype(np.int32), data.astype(np.int32), N, D, 1.0, 0.5,
+                      kmax=8, seed=4, engine=P.ENGINE_CSR_FP32, local_iters=2)
+        if tu:
+            P.dpmm_set_tuning(s.ctx, **tu)
+        s.sweep(1)                        # K = 1: the table (96 KB) leaves room for two ring slots
+        P.dpmm_local_gibbs(s.ctx, 1)
+        out = (s.get_state(), s.stats())
+        s.close()
+        return out
+
+    ref = run(None)
+    assert ref[0][2] == 1
+    for tu in FORMS:
+        same_chain(run(tu), ref, str(tu))
+
+
 def test_local_iteration_arguments(P, tiny):
     args = (tiny.indptr, tiny.indices, tiny.data, tiny.N, tiny.D, 1.0, 0.5)
     with pytest.raises(P.DpmmError):
