@@ -500,13 +500,21 @@ __device__ __forceinline__ void stats_cells(const Csr& csr, const uint32_t* __re
 // and K + 1 the two eq. 8 sub-label Gumbels (words 0, 1 of (cell, t, ., 0));
 // cluster-major, N floats a row.  The values are the ones the label kernel
 // would draw itself; it reads them before its accumulators are ready.
-__device__ __forceinline__ void noise_cells(const ChainArgs& ch, int64_t first, int64_t stride) {
+// Whether the label kernel of this sweep reads drawn-ahead noise for the
+// chain (the dense-tile engine labels it).
+__device__ __forceinline__ bool noise_wanted(const ChainArgs& ch, int K) {
+    return ch.tile_enabled && K >= ch.tile_kmin && K <= kTileMaxK;
+}
+
+// The noise of cells first, first + stride, ... below end of one chain.
+__device__ __forceinline__ void noise_cells(const ChainArgs& ch, int64_t first, int64_t end,
+                                            int64_t stride) {
     const int K = ch.sc->K;
-    if (!ch.tile_enabled || K < ch.tile_kmin || K > kTileMaxK) return;
+    if (!noise_wanted(ch, K)) return;
     const uint32_t t = ch.sc->t;
     const int64_t N = ch.N;
     float* __restrict__ out = ch.noise;
-    for (int64_t cell = first; cell < N; cell += stride) {
+    for (int64_t cell = first; cell < end; cell += stride) {
         for (int k0 = 0; k0 < K; k0 += 4) {
             const uint4 w = ch.st.words(TAG_LABEL, (uint32_t)cell, t, (uint32_t)(k0 >> 2));
             out[(size_t)k0 * N + cell] = gumbel(w.x);
@@ -519,19 +527,67 @@ __device__ __forceinline__ void noise_cells(const ChainArgs& ch, int64_t first, 
         out[(size_t)(K + 1) * N + cell] = gumbel(h.y);
     }
 }
-// Blocks blk of nblocks take the noise: with at least as many blocks as
-// chains, chain c gets the blocks blk = c mod n and splits its cells over
-// them; else block blk takes chains blk, blk + nblocks, ... alone.
+// Blocks blk of nblocks take the noise (called by whole blocks).  One chain:
+// its cells dealt over every thread.  Several chains (at most blockDim.x):
+// the work of chain b is N_b (K_b + 2) draws; block blk takes the draws
+// [blk U / nblocks, (blk + 1) U / nblocks) of the U in all (a cell goes to the
+// block that holds its first draw), so chains of very different sizes share
+// the blocks evenly.  scratch: 2 n + 1 + 32 int64 of shared memory.  More
+// chains than threads: block blk takes chains blk, blk + nblocks, ... alone.
 template <class Tab>
-__device__ __forceinline__ void fill_noise(const Tab& tab, int64_t nblocks, int64_t blk) {
-    const int64_t n = tab.n();
-    if (nblocks >= n) {
-        const int64_t c = blk % n, rank = blk / n, nb = (nblocks - c + n - 1) / n;
-        noise_cells(tab[(int)c], rank * blockDim.x + threadIdx.x, nb * blockDim.x);
-    } else {
-        for (int64_t c = blk; c < n; c += nblocks)
-            noise_cells(tab[(int)c], threadIdx.x, blockDim.x);
+__device__ __forceinline__ void fill_noise(const Tab& tab, int64_t nblocks, int64_t blk,
+                                           long long* scratch) {
+    const int n = tab.n();
+    if (n == 1) {
+        noise_cells(tab[0], blk * blockDim.x + threadIdx.x, tab[0].N, nblocks * blockDim.x);
+        return;
     }
+    if (n > (int)blockDim.x) {
+        for (int64_t c = blk; c < n; c += nblocks)
+            noise_cells(tab[(int)c], threadIdx.x, tab[(int)c].N, blockDim.x);
+        return;
+    }
+    long long* off = scratch;              // [n + 1]: draws before chain b
+    long long* per = scratch + n + 1;      // [n]: draws per cell (0: no noise)
+    long long* wsum = per + n;             // [32]: per-warp totals
+    const int b = threadIdx.x, lane = b & 31, w = b >> 5;
+    long long pc = 0, u = 0;
+    if (b < n) {
+        const ChainArgs& ch = tab[b];
+        const int K = ch.sc->K;
+        if (noise_wanted(ch, K)) {
+            pc = K + 2;
+            u = ch.N * pc;
+        }
+    }
+    long long x = u;                       // inclusive scan in the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    long long before = 0;
+    for (int i = 0; i < w; ++i) before += wsum[i];
+    if (b < n) {
+        off[b] = before + x - u;
+        per[b] = pc;
+        if (b == n - 1) off[n] = before + x;
+    }
+    __syncthreads();
+    const long long U = off[n];
+    const long long U0 = U / nblocks * blk + U % nblocks * blk / nblocks;
+    const long long U1 = U / nblocks * (blk + 1) + U % nblocks * (blk + 1) / nblocks;
+    for (int c = 0; c < n; ++c) {
+        const long long pcc = per[c], ob = off[c], oe = off[c + 1];
+        if (!pcc || oe <= U0 || ob >= U1) continue;
+        const int64_t N = tab[c].N;
+        const int64_t c0 = U0 > ob ? (int64_t)((U0 - ob + pcc - 1) / pcc) : 0;
+        const int64_t c1 = U1 >= oe ? N : min(N, (int64_t)((U1 - ob + pcc - 1) / pcc));
+        noise_cells(tab[c], c0 + threadIdx.x, c1, blockDim.x);
+    }
+    __syncthreads();                       // the scratch may be reused after this
 }
 
 template <class F>

@@ -440,6 +440,8 @@ struct PlanSmem {
     int32_t partner[kMaxKmax];
     int32_t into[kMaxKmax];
     int32_t newidx[kMaxKmax];
+    int32_t applying[kMaxKmax];   // k_plan_apply: the chains whose plan is applied
+    int32_t napplying;
 };
 
 __device__ void plan_block(DevScalars* sc, int32_t kind, uint32_t* __restrict__ nsub,
@@ -675,12 +677,39 @@ k_plan_apply(const __grid_constant__ Tab tab, int32_t kind, GridBar* bar, int64_
         if (threadIdx.x == 0) atomicExch(&tab[0].sc->error, DPMM_ETIMEOUT);
         return;
     }
+    // the chains whose plan is applied, read side by side (one round trip
+    // instead of one per chain and phase); in table order when they fit the
+    // list, else every chain is checked in each phase
+    if (threadIdx.x == 0) sm.napplying = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < tab.n(); b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const int a = b < tab.n() && reinterpret_cast<volatile DevScalars*>(tab[b].sc)->apply;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, a);
+        int* wcount = sm.tmp;
+        if ((threadIdx.x & 31) == 0) wcount[threadIdx.x >> 5] = __popc(m);
+        __syncthreads();
+        int before = sm.napplying;
+        for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) before += wcount[w];
+        const int pos = before + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+        if (a && pos < kMaxKmax) sm.applying[pos] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wcount[w];
+            sm.napplying += tot;
+        }
+        __syncthreads();
+    }
+    const bool listed = sm.napplying <= kMaxKmax;
+    const int nloop = listed ? sm.napplying : tab.n();
+    auto chain_at = [&](int i) -> int { return listed ? sm.applying[i] : i; };
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // (1) rows of each changed chain's new main statistics, from the old main
     //     into the accumulators
-    for (int b = 0; b < tab.n(); ++b) {
-        const ChainArgs& ch = tab[b];
+    for (int i = 0; i < nloop; ++i) {
+        const ChainArgs& ch = tab[chain_at(i)];
         volatile DevScalars* vs = ch.sc;
         if (!vs->apply) continue;
         const int D = ch.D;
@@ -705,8 +734,8 @@ k_plan_apply(const __grid_constant__ Tab tab, int32_t kind, GridBar* bar, int64_
     //     (SUB_COIN sub-labels: fair coins on the tag-7 stream, step t for a
     //     sweep's resets, m after splits)
     const uint32_t sub_kind = compact ? SUBINIT_RESET : SUBINIT_SPLIT;
-    for (int b = 0; b < tab.n(); ++b) {
-        const ChainArgs& ch = tab[b];
+    for (int i = 0; i < nloop; ++i) {
+        const ChainArgs& ch = tab[chain_at(i)];
         volatile DevScalars* vs = ch.sc;
         if (!vs->apply) continue;
         const int64_t total = (int64_t)2 * vs->K_new * ch.D;
@@ -737,8 +766,8 @@ k_plan_apply(const __grid_constant__ Tab tab, int32_t kind, GridBar* bar, int64_
     }
     // (3) re-initialised clusters recounted (their rows were gathered as zeros);
     //     then block 0 commits K = K_new and counts the phase
-    for (int b = 0; b < tab.n(); ++b) {
-        const ChainArgs& ch = tab[b];
+    for (int i = 0; i < nloop; ++i) {
+        const ChainArgs& ch = tab[chain_at(i)];
         volatile DevScalars* vs = ch.sc;
         if (!vs->apply) continue;
         const int Kn = vs->K_new;
@@ -765,7 +794,12 @@ cudaError_t launch_lg_table(Ctx& c) {
 
 cudaError_t launch_move_score(Ctx& c, int32_t mode) {
     return with_table(c, [&](auto tab) {
-        k_move_partial<<<kMaxPartials, kPartialThreads, 0, c.stream>>>(tab, mode);
+        // one chain: kMaxPartials blocks (one per item); a batch: eight blocks
+        // per SM, so that each chain's group has several blocks for its items
+        // (which block takes an item changes nothing: partial slots are per
+        // item and summed in a fixed order)
+        const int grid = c.nchains > 1 ? std::max(kMaxPartials, 8 * c.num_sms) : kMaxPartials;
+        k_move_partial<<<grid, kPartialThreads, 0, c.stream>>>(tab, mode);
         return cudaGetLastError();
     });
 }

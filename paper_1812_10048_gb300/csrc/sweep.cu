@@ -70,6 +70,7 @@ __device__ __forceinline__ void clear_accumulators(int K, uint32_t* acc_nsub,
 
 template <class Tab>
 __global__ void k_select_engine(const __grid_constant__ Tab tab) {
+    __shared__ long long scratch[2 * 256 + 1 + 32];
     for (int b = blockIdx.x; b < tab.n(); b += gridDim.x) {
         const ChainArgs& ch = tab[b];
         const int K = ch.sc->K;
@@ -77,7 +78,7 @@ __global__ void k_select_engine(const __grid_constant__ Tab tab) {
         if (threadIdx.x == 0) select_engine(ch.sc, K, ch);
         clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
     }
-    fill_noise(tab, (int64_t)gridDim.x, (int64_t)blockIdx.x);
+    fill_noise(tab, (int64_t)gridDim.x, (int64_t)blockIdx.x, scratch);
 }
 
 // The K+1 candidate of eq. 4 (chains with open_new): appended as cluster K
@@ -168,12 +169,69 @@ __device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, int open, u
 
 // The 3K + 1 rows of every chain form one list dealt round-robin to the
 // blocks.  The block that draws row 0 of a chain also selects the chain's
-// labelling engine and clears its n-bar / sum log q accumulators.
+// labelling engine and clears its n-bar / sum log q accumulators.  With
+// several chains (at most kDrawTable) the threads first read every chain's
+// K, open slot and counter side by side, so a block finds its rows without a
+// round trip per chain.
+constexpr int kDrawTable = 512;
+
 template <class Tab>
 __global__ void __launch_bounds__(kDrawThreads)
 k_draw_params(const __grid_constant__ Tab tab) {
     __shared__ float red[32];
-    __shared__ float lgc[kDrawCache];
+    __shared__ __align__(16) float lgc[kDrawCache];   // also the noise split's scratch
+    __shared__ int32_t srow[kDrawTable + 1];           // rows before chain b
+    __shared__ int32_t sK[kDrawTable], sopen[kDrawTable];
+    __shared__ uint32_t st_[kDrawTable];
+    const int n = tab.n();
+    if (n > 1 && n <= kDrawTable) {
+        const int b = threadIdx.x;
+        int rows = 0;
+        if (b < n) {
+            const ChainArgs& ch = tab[b];
+            const int K = ch.sc->K;
+            sK[b] = K;
+            sopen[b] = ch.open_new ? ch.sc->open_slot : 0;
+            st_[b] = ch.sc->t;
+            rows = 3 * K + 1;
+        }
+        // exclusive scan of the row counts (n <= kDrawTable <= blockDim.x)
+        const int lane = b & 31, w = b >> 5;
+        int x = rows;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        int* wsum = reinterpret_cast<int*>(red);
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        int before = 0;
+        for (int i = 0; i < w; ++i) before += wsum[i];
+        if (b < n) {
+            srow[b] = before + x - rows;
+            if (b == n - 1) srow[n] = before + x;
+        }
+        __syncthreads();
+        const int total = srow[n];
+        int c = 0;
+        for (int id = blockIdx.x; id < total; id += gridDim.x) {
+            while (srow[c + 1] <= id) ++c;
+            const ChainArgs& ch = tab[c];
+            const int row = id - srow[c], K = sK[c];
+            if (row == 0) {
+                if (threadIdx.x == 0) select_engine(ch.sc, K, ch);
+                clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
+            }
+            draw_row(ch, K, sopen[c], TAG_THETA, st_[c], row, red, lgc);
+            __syncthreads();
+        }
+        const int64_t free0 = total < (int)gridDim.x ? total : 0;
+        if ((int64_t)blockIdx.x >= free0)
+            fill_noise(tab, (int64_t)gridDim.x - free0, (int64_t)blockIdx.x - free0,
+                       reinterpret_cast<long long*>(lgc));
+        return;
+    }
     int64_t base = 0;
     for (int b = 0; b < tab.n(); ++b) {
         const ChainArgs& ch = tab[b];
@@ -194,10 +252,14 @@ k_draw_params(const __grid_constant__ Tab tab) {
         base += rows;
     }
     // the label noise: blocks without a row take it (all blocks when every
-    // block has rows)
+    // block has rows); 2 n + 33 int64 of scratch fit the 32 KB cache for
+    // n <= 1,024 chains
+    static_assert(sizeof(float) * kDrawCache >= sizeof(long long) * (2 * kDrawThreads + 33),
+                  "noise scratch");
     const int64_t free0 = base < gridDim.x ? base : 0;
     if ((int64_t)blockIdx.x >= free0)
-        fill_noise(tab, (int64_t)gridDim.x - free0, (int64_t)blockIdx.x - free0);
+        fill_noise(tab, (int64_t)gridDim.x - free0, (int64_t)blockIdx.x - free0,
+                   reinterpret_cast<long long*>(lgc));
 }
 
 // Local Gibbs iteration j >= 1 after a sweep (Section 2.3), first half: the
@@ -1320,10 +1382,15 @@ __device__ __forceinline__ void assign_chain(const ChainArgs& a, int64_t smem_by
 
 
 // Every chain of the table in turn (a chain labelled by the dense-tile engine
-// returns at once), each with all blocks.
+// returns at once), each with all blocks.  The threads first read every
+// chain's engine flag side by side, so a launch in which the dense-tile
+// engine labels all chains ends after one round trip.
 template <class Tab>
 __global__ void __launch_bounds__(kAssignThreads, 1)
 k_assign(const __grid_constant__ Tab tab, int64_t smem_bytes) {
+    int csr = 0;
+    for (int b = threadIdx.x; b < tab.n() && !csr; b += blockDim.x) csr = !tab[b].sc->tile_used;
+    if (!__syncthreads_or(csr)) return;
     for (int b = 0; b < tab.n(); ++b) {
         assign_chain(tab[b], smem_bytes);
         __syncthreads();

@@ -132,13 +132,14 @@ __device__ __forceinline__ float bf16_value(uint16_t b) {
     return __uint_as_float((uint32_t)b << 16);
 }
 
-// B operand of one sweep: block (c, q, b) fills rows 16q .. 16q + 15 of chunk
-// c (genes 64c .. 64c + 63) of chain b; every block of chunk c forms the same
-// m_u.  In a step (force = 0) the blocks of chain b first clear its main
-// S-bar rows.
+// B operand of one sweep: block (c, q, b) fills rows rb q .. rb q + rb - 1 of
+// chunk c (genes 64c .. 64c + 63) of chain b; every block of chunk c forms the
+// same m_u (rb = 16 rows for one chain, 64 for a batch: fewer blocks, less
+// repeated m_u).  In a step (force = 0) the blocks of chain b first clear its
+// main S-bar rows.
 template <class Tab>
 __global__ void __launch_bounds__(256)
-k_build_b(const __grid_constant__ Tab tab, int32_t force) {
+k_build_b(const __grid_constant__ Tab tab, int32_t force, int32_t rb) {
     __shared__ float part[4][64];
     __shared__ float m[64];
     const ChainArgs& ch = tab[blockIdx.z];
@@ -162,7 +163,7 @@ k_build_b(const __grid_constant__ Tab tab, int32_t force) {
     const int c = blockIdx.x;
     if (c >= ch.tile_C) return;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
-    if ((int)blockIdx.y * 16 >= Ntot) return;
+    if ((int)blockIdx.y * rb >= Ntot) return;
     {
         // m_u: 4 threads per gene, each a quarter of the 3K rows, fixed order
         const int g = threadIdx.x & 63, qq = threadIdx.x >> 6;
@@ -179,7 +180,7 @@ k_build_b(const __grid_constant__ Tab tab, int32_t force) {
         __syncthreads();
     }
     unsigned char* dst = B + (size_t)c * kBChunkBytes;
-    for (int i = blockIdx.y * 1024 + threadIdx.x; i < min(Ntot, (int)blockIdx.y * 16 + 16) * 64;
+    for (int i = blockIdx.y * rb * 64 + threadIdx.x; i < min(Ntot, (int)(blockIdx.y + 1) * rb) * 64;
          i += blockDim.x) {
         const int row = i >> 6, g = i & 63, u = c * 64 + g;
         float L = 0.0f;
@@ -900,8 +901,9 @@ cudaError_t configure_tile(Ctx& c) {
 
 cudaError_t launch_build_b(Ctx& c, bool force) {
     return with_table(c, [&](auto tab) {
-        k_build_b<<<dim3(c.tile_C, kNtotMax / 16, c.nchains), 256, 0, c.stream>>>(tab,
-                                                                                  force ? 1 : 0);
+        const int rb = c.nchains > 1 ? 64 : 16;
+        k_build_b<<<dim3(c.tile_C, kNtotMax / rb, c.nchains), 256, 0, c.stream>>>(
+            tab, force ? 1 : 0, rb);
         return cudaGetLastError();
     });
 }
