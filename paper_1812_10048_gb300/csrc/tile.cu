@@ -771,7 +771,8 @@ k_assign_tc(const __grid_constant__ Tab tab, float* dbg_out, int64_t smem_bytes,
 // groups), so its private counters cover only 64 genes ([2K][64] words in
 // shared memory; K > kTileMaxK counts straight into global memory) and its
 // flush adds at most 2K x 64 words.  One warp per (tile, chunk) segment at a
-// time, with the tile's 128 cell states cached.  Integer sums, exact.
+// time, with the counter row (2 k + r) ld of each of the tile's 128 cells
+// cached (0xFFFFFFFF past the last cell).  Integer sums, exact.
 constexpr int kStatsTileThreads = 512;
 
 template <typename T_>
@@ -785,26 +786,39 @@ __device__ __forceinline__ void count_segments(T_* priv, int ld, uint32_t* pn, u
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t cell = (int64_t)tile * 128 + lane + 32 * j;
-            const uint32_t st = cell < N ? state[cell] : 0xFFFFFFFFu;
-            my[lane + 32 * j] = st;
-            if (c == 0 && st != 0xFFFFFFFFu) atomicAdd(&pn[2 * state_label(st) + state_sub(st)], 1u);
+            uint32_t row = 0xFFFFFFFFu;
+            if (cell < N) {
+                const uint32_t st = state[cell];
+                const uint32_t kr = 2 * state_label(st) + state_sub(st);
+                row = kr * (uint32_t)ld;
+                if (c == 0) atomicAdd(&pn[kr], 1u);
+            }
+            my[lane + 32 * j] = row;
         }
         __syncwarp();
         const int64_t seg = (int64_t)tile * C + c;
         const int p0 = ptr[4 * seg], p1 = ptr[4 * seg + 4];
-        for (int e = p0 + lane; e < p1; e += 32 * 16) {
-            uint32_t v[16];   // 16 independent loads in flight per lane
+        // an entry of count 0 (segment padding) adds nothing; its cell may lie
+        // past the last one, so it is skipped before its row is read
+        auto add = [&](uint32_t v) {
+            const uint32_t x = v & 0xFFFFu;
+            if (x) atomicAdd(&priv[my[v >> 22] + ((v >> 16) & 63u)], x);
+        };
+        int e = p0 + lane;
+        for (; e + 32 * 15 < p1; e += 32 * 16) {      // whole batches: 16 loads in flight
+            const uint32_t* pe = ent + e;
+            uint32_t v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __ldg(pe + 32 * j);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) add(v[j]);
+        }
+        if (e < p1) {                                  // the rest, bounds-checked
+            uint32_t v[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = e + 32 * j < p1 ? __ldg(ent + e + 32 * j) : 0u;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const uint32_t x = v[j] & 0xFFFFu;
-                if (!x) continue;
-                const uint32_t st = my[v[j] >> 22];
-                atomicAdd(&priv[(size_t)(2 * state_label(st) + state_sub(st)) * ld +
-                                ((v[j] >> 16) & 63u)],
-                          x);
-            }
+            for (int j = 0; j < 16; ++j) add(v[j]);
         }
         __syncwarp();
     }
