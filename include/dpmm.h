@@ -431,8 +431,8 @@ int dpmm_eb_step(dpmm_ctx* ctx, double eta_alpha, double eta_beta, double max_st
  * routine is called.  All calls on a device share that array and it keeps the
  * last call's contents (each call clears what must start at zero): calls whose
  * GPU work overlaps race and must be serialised by the caller.  The first call
- * on a device looks up the array's device address (once per device); make that
- * first call before any stream capture.  Malformed CSR rows, columns or labels
+ * on a device looks up the array's device address (once per device).
+ * Malformed CSR rows, columns or labels
  * are skipped on the device and reported as DPMM_EINVAL; a cluster whose
  * count of one gene reaches 2^32 gives DPMM_EOVERFLOW.  Runs on `stream`
  * (NULL: the legacy default stream) and synchronises it before returning.
