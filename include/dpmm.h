@@ -209,10 +209,10 @@ int dpmm_debug_engine(dpmm_ctx* ctx, int32_t* tile_used);
  *                        group form: 4, 8, 16 or 32 (default: the power of
  *                        two nearest below the mean row length / 8, within
  *                        [4, 32])
- *   local_group_form     1: that kernel always takes the group form; 0
- *                        (default): the streamed form wherever the chain has
- *                        the packed rows and its theta-bar table leaves room
- *                        for the ring in shared memory
+ *   local_stream         1: that kernel streams the rows through a shared-memory
+ *                        ring (bulk copies) wherever the chain has the packed
+ *                        rows and its theta-bar table leaves room; 0 (default):
+ *                        lane groups read the rows from global memory
  * Other values: DPMM_EINVAL.  dpmm_set_tuning drops the captured step graph
  * (the next dpmm_step captures a new one).  dpmm_get_tuning returns the values
  * in force (defaults resolved).
@@ -223,7 +223,7 @@ typedef struct dpmm_tuning {
     int32_t tile_scatter;
     int32_t draw_blocks_per_sm;
     int32_t local_lanes;
-    int32_t local_group_form;
+    int32_t local_stream;
     int32_t reserved[2];
 } dpmm_tuning;
 

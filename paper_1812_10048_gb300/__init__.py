@@ -116,7 +116,7 @@ def dpmm_plans_applied(ctx):
 
 
 TUNING_FIELDS = ("stats_blocks_per_sm", "tile_stages", "tile_scatter", "draw_blocks_per_sm",
-                 "local_lanes", "local_group_form")
+                 "local_lanes", "local_stream")
 
 
 def dpmm_set_tuning(ctx, **fields):

@@ -36,7 +36,7 @@ class dpmm_opts(ctypes.Structure):
 class dpmm_tuning(ctypes.Structure):
     _fields_ = [("stats_blocks_per_sm", ctypes.c_int32), ("tile_stages", ctypes.c_int32),
                 ("tile_scatter", ctypes.c_int32), ("draw_blocks_per_sm", ctypes.c_int32),
-                ("local_lanes", ctypes.c_int32), ("local_group_form", ctypes.c_int32),
+                ("local_lanes", ctypes.c_int32), ("local_stream", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 2)]
 
 

@@ -34,7 +34,7 @@ SEARCH = (
     ("draw_blocks_per_sm", (1, 2)),
 )
 # searched only for samplers that run local Gibbs iterations
-LOCAL_SEARCH = (("local_group_form", (0, 1)), ("local_lanes", (4, 8, 16, 32)))
+LOCAL_SEARCH = (("local_stream", (0, 1)), ("local_lanes", (4, 8, 16, 32)))
 MARGIN = 0.02          # a candidate must beat the incumbent by 2%
 
 

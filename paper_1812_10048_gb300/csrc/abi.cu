@@ -106,7 +106,7 @@ void free_ctx(Ctx& c) {
         if (e) cudaEventDestroy(e);
     void* ptrs[] = {c.indptr, c.entries, c.cols, c.counts, c.state, c.sc, c.nsub, c.Ssub,
                     c.sumlogq, c.acc_nsub, c.acc_Ssub, c.acc_logq, c.logpi, c.Lc, c.Ls,
-                    c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
+                    c.local_tab, c.lmap, c.desc, c.reinit, c.decide, c.log_h, c.pair_ab, c.lg_table,
                     c.move_part, c.move_ticket, c.tile_ent, c.tile_ptr, c.tile_B, c.noise,
                     c.gbar, c.d_chains};
     for (void* p : ptrs)
@@ -145,6 +145,7 @@ ChainArgs dpmm::chain_args(const Ctx& c) {
     a.logpi = c.logpi;
     a.Lc = c.Lc;
     a.Ls = c.Ls;
+    a.local_tab = c.local_tab;
     a.lmap = c.lmap;
     a.desc = c.desc;
     a.reinit = c.reinit;
@@ -468,6 +469,8 @@ int dpmm_init(dpmm_ctx** out, const int32_t* indptr, const int32_t* indices, con
     CKI(dalloc(&c.logpi, (size_t)c.kmax + 1));
     CKI(dalloc(&c.Lc, (size_t)c.kmax * D));
     CKI(dalloc(&c.Ls, K2 * D));
+    if (c.opts.local_iters > 1)
+        CKI(dalloc(&c.local_tab, (size_t)D * (size_t)(c.kmax | 1) * 2 + 4));
     CKI(dalloc(&c.lmap, K2));
     CKI(dalloc(&c.desc, K2));
     CKI(dalloc(&c.reinit, (size_t)c.kmax));
@@ -792,8 +795,8 @@ int dpmm_set_tuning(dpmm_ctx* ctx, const dpmm_tuning* t) {
         return fail(DPMM_EINVAL, "draw_blocks_per_sm %d not in {0, 1, 2}", t->draw_blocks_per_sm);
     if (!in(t->local_lanes, {0, 4, 8, 16, 32}))
         return fail(DPMM_EINVAL, "local_lanes %d not in {0, 4, 8, 16, 32}", t->local_lanes);
-    if (!in(t->local_group_form, {0, 1}))
-        return fail(DPMM_EINVAL, "local_group_form %d not in {0, 1}", t->local_group_form);
+    if (!in(t->local_stream, {0, 1}))
+        return fail(DPMM_EINVAL, "local_stream %d not in {0, 1}", t->local_stream);
     Ctx& c = ctx->c;
     CK(cudaStreamSynchronize(c.stream));
     c.tune_stats_per_sm = t->stats_blocks_per_sm;
@@ -801,7 +804,7 @@ int dpmm_set_tuning(dpmm_ctx* ctx, const dpmm_tuning* t) {
     c.tune_tile_scatter = t->tile_scatter;
     c.tune_draw_per_sm = t->draw_blocks_per_sm;
     c.tune_local_lanes = t->local_lanes;
-    c.tune_local_group_form = t->local_group_form;
+    c.tune_local_stream = t->local_stream;
     if (c.step_exec) {
         cudaGraphExecDestroy(c.step_exec);
         c.step_exec = nullptr;
@@ -819,7 +822,7 @@ int dpmm_get_tuning(dpmm_ctx* ctx, dpmm_tuning* t) {
     t->tile_scatter = c.tune_tile_scatter ? c.tune_tile_scatter : 12;
     t->draw_blocks_per_sm = c.tune_draw_per_sm ? c.tune_draw_per_sm : 2;
     t->local_lanes = local_lanes(c);
-    t->local_group_form = c.tune_local_group_form;
+    t->local_stream = c.tune_local_stream;
     return DPMM_OK;
 }
 

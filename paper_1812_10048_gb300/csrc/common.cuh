@@ -147,6 +147,7 @@ struct Ctx {
     float* logpi = nullptr;       // [kmax + 1]
     float* Lc = nullptr;          // [D][kmax] cluster log theta, gene-major
     float* Ls = nullptr;          // [D][kmax][2] sub-cluster log theta, gene-major
+    float* local_tab = nullptr;   // [D][K | 1][2] theta-bar of a local iteration (local_iters > 1)
 
     // move plan
     uint32_t* lmap = nullptr;     // [2 kmax] old (k, r) -> new label | sub mode
@@ -184,7 +185,7 @@ struct Ctx {
     int32_t tune_tile_scatter = 0;  // producer entries per lane and batch (8, 12, 16)
     int32_t tune_draw_per_sm = 0;   // draw-kernel blocks per SM (1 or 2)
     int32_t tune_local_lanes = 0;   // local sub-label kernel lanes per cell (4 .. 32)
-    int32_t tune_local_group_form = 0;  // 1: local sub-labels in the group form only
+    int32_t tune_local_stream = 0;  // 1: local sub-labels streamed through the ring where it fits
 
 
     // chains this context's launches walk: itself (nchains = 1) or, for a
@@ -369,6 +370,7 @@ struct ChainArgs {
     float* logpi;
     float* Lc;
     float* Ls;
+    float* local_tab;
     uint32_t* lmap;
     int32_t* desc;
     uint8_t* reinit;

@@ -114,8 +114,15 @@ __global__ void k_open_slot(const __grid_constant__ Tab tab) {
 // candidate (open = 1) the alpha entry of pi is the candidate's weight and
 // there is no remainder entry (log pi_K = -inf).
 constexpr int kDrawCache = 8192;
+// Row stride (in pairs) of the staged table: K rounded up to odd, so that
+// the pairs of one cluster for 32 random genes spread over 16 bank pairs.
+__host__ __device__ __forceinline__ int staged_ld(int K) { return K | 1; }
+
+// compact: when not null (local iterations), the sub-cluster rows are also
+// written to it as [D][K | 1] pairs, the local kernel's shared-memory layout.
 __device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, int open, uint32_t theta_tag,
-                                         uint32_t t, int row, float* red, float* lgc) {
+                                         uint32_t t, int row, float* red, float* lgc,
+                                         float* compact = nullptr) {
     const int D = ch.D, kmax = ch.kmax;
     const float beta = (float)ch.beta, alpha = (float)ch.alpha;
     const Stream& st = ch.st;
@@ -144,8 +151,11 @@ __device__ __forceinline__ void draw_row(const ChainArgs& ch, int K, int open, u
             s += expf((cached ? lgc[u] : *slot(u)) - mx);
         s = block_reduce_sum(s, red);
         const float lse = mx + logf(s);
-        for (int u = threadIdx.x; u < D; u += blockDim.x)
-            *slot(u) = (cached ? lgc[u] : *slot(u)) - lse;
+        for (int u = threadIdx.x; u < D; u += blockDim.x) {
+            const float v = (cached ? lgc[u] : *slot(u)) - lse;
+            *slot(u) = v;
+            if (compact && p != 0) compact[((size_t)u * staged_ld(K) + k) * 2 + (p - 1)] = v;
+        }
     } else {
         const uint32_t* nsub = ch.nsub;
         float* logpi = ch.logpi;
@@ -283,7 +293,7 @@ k_draw_local(const __grid_constant__ Tab tab, int32_t j) {
         for (int64_t id = first; id < base + rows; id += gridDim.x) {
             const int i = (int)(id - base);
             if (i == 0) clear_accumulators(K, ch.acc_nsub, ch.acc_logq);
-            draw_row(ch, K, 0, tag, t, 3 * (i >> 1) + 1 + (i & 1), red, lgc);
+            draw_row(ch, K, 0, tag, t, 3 * (i >> 1) + 1 + (i & 1), red, lgc, ch.local_tab);
             __syncthreads();
         }
         base += rows;
@@ -377,9 +387,10 @@ __device__ __forceinline__ uint32_t draw_sublabel(const ChainArgs& a, int64_t ce
 // drawn from eq. 8 under the new theta-bar (weights n-bar_{r, not i} from the
 // current counts).  Block b takes the cells [b Ntot / G, (b + 1) Ntot / G) of
 // the table's chains in order (Ntot cells in all, G blocks), chain by chain,
-// in one of two forms (below): streamed through a shared-memory ring, or in
-// groups of LANES lanes that read the rows from global memory.  Either way
-// the eq. 8 decisions are batched so that they run on all 32 lanes of a warp.
+// in one of two forms (below): in groups of LANES lanes that read the rows
+// from global memory (the default), or streamed through a shared-memory ring.
+// Either way the eq. 8 decisions are batched so that they run on all 32
+// lanes of a warp.
 //
 // The contraction sum_u x_i^u log theta-bar_{c,r}^u has one fixed FP32 order
 // whatever LANES is: entry i of the row (0-based) belongs to slot i mod 32;
@@ -394,7 +405,9 @@ __device__ __forceinline__ uint32_t draw_sublabel(const ChainArgs& a, int64_t ce
 // The chain's theta-bar pairs of its K clusters are staged in shared memory
 // as a [D][K | 1] table when they fit (by the blocks that hold cells of the
 // chain), so each gather is a shared-memory load instead of an 8-byte load
-// 2 KB away from its neighbour in the gene-major global table.  log q_i is
+// 2 KB away from its neighbour in the gene-major global table; the local
+// draws also write the table in that layout, so a block stages it with
+// contiguous 16-byte loads.  log q_i is
 // summed per cluster in the block (exact integer units, see logq_fixed), then
 // into the accumulator.  A chain with the blocked copy also has its main
 // S-bar rows cleared here (the tile statistics kernel recounts into them;
@@ -486,8 +499,9 @@ __device__ __forceinline__ float2 sub_scores_slots(const Csr& csr, int64_t beg, 
     return make_float2(ax[0], ay[0]);
 }
 
-// Group form (rows without the packed copy, or a table that leaves no room
-// for the ring): batches of one chain's cells below N for the warp.  Lane
+// Group form (the default; also for rows without the packed copy or a table
+// that leaves no room for the ring): batches of one chain's cells below N
+// for the warp.  Lane
 // q = R NG + g of the warp owns group g's cell of round R (group g: lanes
 // LANES g ..; its cells first_g, first_g + G, ...): it loads that cell's
 // state and row bounds at the start of the batch, the group takes them by
@@ -533,7 +547,8 @@ __device__ __forceinline__ void local_sub_chain(const ChainArgs& ch, const float
     }
 }
 
-// Streamed form (packed rows, staged table): the block's cells in chunks of
+// Streamed form (with local_stream tuning, packed rows and a staged table):
+// the block's cells in chunks of
 // at most 62 consecutive whole rows (at most kLocalSlotEntries - 6 entries;
 // a longer row is a chunk of its own, read from global memory).  Warp 31
 // produces: per chunk it waits for the ring slot to be released, writes the
@@ -550,6 +565,7 @@ constexpr int kLocalSlotEntries = kLocalSlotBytes / 4;
 constexpr int kLocalMaxSlots = 6;
 constexpr int kLocalConsumers = 31;
 constexpr int kLocalChunkCells = 2 * kLocalConsumers;
+constexpr int kLocalBarConsumers = 1;   // named barrier of the consumer warps
 constexpr int kLocalWin = 1024;     // cells of row bounds and states the producer holds
 constexpr int kLocalWinOff = 8 * kMaxKmax + 2048 + 4096;
 // bsq, barriers, chunk headers, window (row bounds, states)
@@ -564,20 +580,17 @@ struct LocalChunk {
 };
 static_assert(kLocalMaxSlots * sizeof(LocalChunk) <= 4096, "chunk headers exceed their area");
 
-// Row stride (in pairs) of the staged table: K rounded up to odd, so that
-// the pairs of one cluster for 32 random genes spread over 16 bank pairs.
-__host__ __device__ __forceinline__ int staged_ld(int K) { return K | 1; }
 
-// One chain's theta-bar pairs of its K clusters into shared memory as [D][ld]
-// (eight loads in flight per thread).
+// One chain's theta-bar pairs of its K clusters into shared memory as [D][ld],
+// by threads tid of nthr (eight loads in flight per thread).
 __device__ __forceinline__ void stage_table(float2* sL, const float2* __restrict__ Ls2, int D,
-                                            int K, int kmax) {
+                                            int K, int kmax, int tid, int nthr) {
     const int tot = D * K, ld = staged_ld(K);
-    for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * (int)blockDim.x) {
+    for (int i0 = tid; i0 < tot; i0 += 8 * nthr) {
         float2 v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int i = i0 + q * (int)blockDim.x;
+            const int i = i0 + q * nthr;
             if (i < tot) {
                 const int u = i / K;
                 v[q] = __ldg(Ls2 + (size_t)u * kmax + (i - u * K));
@@ -585,13 +598,34 @@ __device__ __forceinline__ void stage_table(float2* sL, const float2* __restrict
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int i = i0 + q * (int)blockDim.x;
+            const int i = i0 + q * nthr;
             if (i < tot) {
                 const int u = i / K;
                 sL[u * ld + (i - u * K)] = v[q];
             }
         }
     }
+}
+
+// The same table from the compact copy the local draws wrote ([D][ld] pairs,
+// contiguous): 16-byte loads, eight in flight per thread.
+__device__ __forceinline__ void copy_table(float2* sL, const float* __restrict__ tab, int D,
+                                           int K, int tid, int nthr) {
+    const int pairs = D * staged_ld(K);
+    const int vec = pairs / 2;                       // 16-byte units (two pairs)
+    const uint4* __restrict__ src = reinterpret_cast<const uint4*>(tab);
+    uint4* dst = reinterpret_cast<uint4*>(sL);
+    for (int i0 = tid; i0 < vec; i0 += 8 * nthr) {
+        uint4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (i0 + q * nthr < vec) v[q] = __ldg(src + i0 + q * nthr);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (i0 + q * nthr < vec) dst[i0 + q * nthr] = v[q];
+    }
+    if ((pairs & 1) && tid == 0)
+        sL[pairs - 1] = reinterpret_cast<const float2*>(tab)[pairs - 1];
 }
 
 // 16-lane sums of one row in the slot order (p: the row's first entry; kGlobal:
@@ -867,7 +901,7 @@ __device__ __forceinline__ bool local_stream_chain(const ChainArgs& ch, int64_t 
 
 template <int LANES, class Tab>
 __global__ void __launch_bounds__(kLocalThreads, 1)
-k_local_sub(const __grid_constant__ Tab tab, int32_t j, int64_t smem_bytes, int32_t group_form) {
+k_local_sub(const __grid_constant__ Tab tab, int32_t j, int64_t smem_bytes, int32_t stream) {
     extern __shared__ __align__(128) unsigned char smem_local[];
     unsigned long long* bsq = reinterpret_cast<unsigned long long*>(smem_local);   // [kMaxKmax]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_local + 8 * kMaxKmax);      // [6]
@@ -918,27 +952,41 @@ k_local_sub(const __grid_constant__ Tab tab, int32_t j, int64_t smem_bytes, int3
         const int64_t ring_off = (kLocalHdr + table + 127) & ~(int64_t)127;
         const int NS = (int)min((int64_t)kLocalMaxSlots,
                                 max((int64_t)0, (smem_bytes - ring_off) / kLocalSlotBytes));
-        const bool streamed = !group_form && staged && ch.csr.entries != nullptr && NS >= 2;
+        const bool streamed = stream && staged && ch.csr.entries != nullptr && NS >= 2;
         const float2* __restrict__ Ls2 = reinterpret_cast<const float2*>(ch.Ls);
         __syncthreads();
         for (int i = threadIdx.x; i < K; i += blockDim.x) bsq[i] = 0ull;
-        if (staged) stage_table(sL, Ls2, D, K, kmax);
         if (streamed) {
-            // the producer's first window of row bounds and states
+            // the producer's first window of row bounds and states (the whole
+            // block, one round trip); then the producer starts its copies
+            // while the consumer warps stage the table
             const int64_t wn = min((int64_t)kLocalWin, hi - lo);
             for (int k = threadIdx.x; k <= wn; k += blockDim.x) wip[k] = ch.csr.indptr[lo + k];
             for (int k = threadIdx.x; k < wn; k += blockDim.x) wst[k] = ch.state[lo + k];
-        }
-        // the table's generic writes are ordered before the ring's bulk copies
-        // into the same bytes (the ring moves with the table's size)
-        tc::fence_async_smem();
-        __syncthreads();
-        if (streamed) {
+            // this segment's ring and table do not overlap; an earlier
+            // segment's table under this ring was fenced after its staging
+            __syncthreads();
+            if ((int)(threadIdx.x >> 5) != kLocalConsumers) {
+                if (ch.local_tab)
+                    copy_table(sL, ch.local_tab, D, K, threadIdx.x, 32 * kLocalConsumers);
+                else
+                    stage_table(sL, Ls2, D, K, kmax, threadIdx.x, 32 * kLocalConsumers);
+                tc::fence_async_smem();   // before a later segment's ring may cover it
+                tc::named_bar(kLocalBarConsumers, 32 * kLocalConsumers);
+            }
             const bool ok = local_stream_chain(ch, lo, hi, sL, K, smem_local + ring_off, NS, full,
                                                empty, hdr, fpar, epar, used, jj, tag, t, bsq,
                                                stop, wip, wst);
             if (__syncthreads_or(ok ? 0 : 1)) break;
         } else {
+            if (staged) {
+                if (ch.local_tab)
+                    copy_table(sL, ch.local_tab, D, K, threadIdx.x, blockDim.x);
+                else
+                    stage_table(sL, Ls2, D, K, kmax, threadIdx.x, blockDim.x);
+            }
+            tc::fence_async_smem();       // before a later segment's ring may cover it
+            __syncthreads();
             // groups of LANES lanes over the block's cells lo + g, lo + g + groups, ...
             const int64_t ngb = blockDim.x / LANES;
             const int64_t first_l = lo + (threadIdx.x & ~31) / LANES + lane % (32 / LANES);
@@ -1573,7 +1621,7 @@ cudaError_t launch_local_iteration(Ctx& c, int32_t j) {
     cudaError_t e = with_table(c, [&](auto tab) {
         k_draw_local<<<2 * c.num_sms, kDrawThreads, 0, c.stream>>>(tab, j);
         const int lanes = local_lanes(c);
-        const int32_t gf = c.tune_local_group_form;
+        const int32_t gf = c.tune_local_stream;
         const dim3 grid(c.num_sms);
         const int64_t sm = (int64_t)c.local_smem;
         if (lanes == 4)

@@ -84,11 +84,11 @@ def test_defaults_reported(P, dense):
     lanes = lanes_for(int(dense.indptr[-1]), dense.N)
     assert P.dpmm_get_tuning(s.ctx) == {"stats_blocks_per_sm": 4, "tile_stages": 4,
                                         "tile_scatter": 12, "draw_blocks_per_sm": 2,
-                                        "local_lanes": lanes, "local_group_form": 0}
+                                        "local_lanes": lanes, "local_stream": 0}
     P.dpmm_set_tuning(s.ctx, tile_stages=2, tile_scatter=16, local_lanes=32)
     assert P.dpmm_get_tuning(s.ctx) == {"stats_blocks_per_sm": 4, "tile_stages": 2,
                                         "tile_scatter": 16, "draw_blocks_per_sm": 2,
-                                        "local_lanes": 32, "local_group_form": 0}
+                                        "local_lanes": 32, "local_stream": 0}
     P.dpmm_set_tuning(s.ctx)                     # all zero: back to the defaults
     assert P.dpmm_get_tuning(s.ctx)["tile_stages"] == 4
     assert P.dpmm_get_tuning(s.ctx)["local_lanes"] == lanes
@@ -98,14 +98,14 @@ def test_defaults_reported(P, dense):
     blanes = lanes_for(sum(int(d[0][-1]) for d in data), sum(d[3] for d in data))
     assert P.dpmm_get_tuning(b.ctx) == {"stats_blocks_per_sm": 2, "tile_stages": 2,
                                         "tile_scatter": 12, "draw_blocks_per_sm": 2,
-                                        "local_lanes": blanes, "local_group_form": 0}
+                                        "local_lanes": blanes, "local_stream": 0}
     b.close()
 
 
 @pytest.mark.parametrize("bad", [{"stats_blocks_per_sm": 3}, {"tile_stages": 3},
                                  {"tile_scatter": 10}, {"draw_blocks_per_sm": 4},
                                  {"tile_stages": -1}, {"local_lanes": 2}, {"local_lanes": 64},
-                                 {"local_group_form": 2}])
+                                 {"local_stream": 2}])
 def test_invalid_tuning_rejected(P, dense, bad):
     s = P.Sampler(dense.indptr, dense.indices, dense.data, dense.N, dense.D, 1.0, 0.5, kmax=32)
     before = P.dpmm_get_tuning(s.ctx)

@@ -130,7 +130,7 @@ def test_batched_local_iterations_equal_single_chains(P):
         s.close()
 
 
-FORMS = [{"local_group_form": 1, "local_lanes": v} for v in (4, 8, 16, 32)] + [{"local_lanes": 4}]
+FORMS = [{"local_lanes": v} for v in (4, 8, 16, 32)] + [{"local_stream": 1}]
 
 
 def same_chain(x, y, what):
