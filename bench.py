@@ -56,7 +56,7 @@ def parse():
                     help="skip the oracle run on all host cores (one chain per core)")
     ap.add_argument("--config", default="main",
                     choices=["main", "batched", "large", "grad", "eb", "study", "local", "ari",
-                             "bf16err", "engines"],
+                             "bf16err", "engines", "tiny"],
                     help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
                          "as one batch; large: 1.3M x 2k")
     ap.add_argument("--autotune", action="store_true",
@@ -555,7 +555,22 @@ def run_large(args):
         forms[name] = {"sweeps_per_s": round(steps / (ms.sum() / 1e3), 2),
                        "ms_per_step": round(float(ms.mean()), 4), "K_final": int(K),
                        "ari_vs_truth": round(adjusted_rand_index(lab, ds.labels), 4)}
+        if name == "bf16":
+            st_ = s.get_state()
+            state = (st_[0], st_[1], st_[2], st_[3], st_[4], s.stats()[2])
         s.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on the first 50,000 cells from the BF16 chain's state,
+        # scaled by cells / N (at least three steps; extrapolated)
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        rate, n_steps, el, cells = oracle_steps_per_sec(ds, state, args.cpu_seconds,
+                                                        cells=min(ds.N, 50_000))
+        cpu = {"value": round(rate, 6), "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_steps} oracle steps (sweep + split/merge, FP64) on the first "
+                         f"{cells} of {ds.N} cells from the GPU chain's state, {el:.1f} s, "
+                         f"scaled by {cells}/{ds.N} to the full workload (extrapolated)",
+               "cpu_model": cpu_model()}
     line = {
         "metric": "Gibbs sweeps/sec at 1.3M cells x 2k genes (BF16 hi/lo form)",
         "value": forms["bf16"]["sweeps_per_s"], "unit": "sweeps/s", "n_gpus": 1,
@@ -567,8 +582,56 @@ def run_large(args):
                    "counts_over_255": int((ds.data > 255).sum()), "alpha": 1.0, "beta": 0.1,
                    "kmax": 256, "generation_s": round(gen_s, 1),
                    "l2": "inputs (> 1 GB) larger than L2"},
-        "forms": forms, "clocks": clk,
+        "forms": forms, "clocks": clk, "cpu_baseline": cpu,
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_tiny(args):
+    """The 2,000 x 500 workload (5 equal clusters, Dir(0.1), LogNormal(log 1500,
+    0.5), alpha 1, beta 0.5): 200 GPU steps after 3 untimed ones from K = 1
+    (launch-bound at this size) and the FP64 oracle chain from K = 1 on the
+    same data and seed (up to 200 steps within --cpu-seconds), with ARI
+    against the generating labels."""
+    import torch
+    from paper_1812_10048_gb300 import build as _build
+    _build.build()
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    from oracle.ari import adjusted_rand_index
+    from oracle.sampler import Sampler as OracleSampler
+    ds = synth.tiny()
+    steps = 200
+    s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, kmax=64, seed=42)
+    st = torch.cuda.ExternalStream(s.stream)
+    ms = time_steps(lambda: s.step(1), st, steps, 3, torch)   # the first steps capture the graph
+    lab, K = s.labels()
+    gpu = {"sweeps_per_s": round(steps / (ms.sum() / 1e3), 1), "K_final": int(K),
+           "ari_vs_truth": round(adjusted_rand_index(lab, ds.labels), 4)}
+    s.close()
+    line = {"metric": "Gibbs sweeps/sec at 2k cells x 500 genes", "value": gpu["sweeps_per_s"],
+            "unit": "sweeps/s", "n_gpus": 1, "steps": steps, "higher_is_better": True,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "2,000 cells x 500 genes, 5 equal clusters, Dir(0.1), "
+                                   "LogNormal(log 1500, 0.5)", "alpha": 1.0, "beta": 0.5,
+                       "kmax": 64, "timing": "launch-bound; steps from K = 1, no L2 flush"},
+            "gpu": gpu}
+    if not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        o = OracleSampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, seed=42)
+        n, t0 = 0, time.perf_counter()
+        while n < steps and time.perf_counter() - t0 < args.cpu_seconds:
+            o.sweep()
+            o.split_merge(0)
+            n += 1
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": round(n / el, 3), "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle steps (sweep + split/merge, FP64) from K = 1 on the full "
+                      f"2,000-cell workload, {el:.1f} s", "K_final": int(o.K),
+            "ari_vs_truth": round(adjusted_rand_index(o.labels, ds.labels), 4),
+            "cpu_model": cpu_model()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1121,6 +1184,8 @@ def main():
         return run_local(args)
     if args.config == "batched":
         return run_batched(args)
+    if args.config == "tiny":
+        return run_tiny(args)
     if args.config == "large":
         return run_large(args)
     rank, world, local = dist_env()
