@@ -59,6 +59,8 @@ def parse():
                              "bf16err", "engines", "tiny"],
                     help="main: the 68k x 1k metric (default); batched: 64 datasets stepped "
                          "as one batch; large: 1.3M x 2k")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="main: skip the short batched and local-iteration measurements")
     ap.add_argument("--autotune", action="store_true",
                     help="main / batched: choose the launch tuning by timing the live sampler "
                          "before the warm-up (not cached); default: the built-in tuning")
@@ -1262,6 +1264,8 @@ def main():
         "clocks": prim["clocks"],
         "wall_s_timed_loop": round(prim["wall_s"], 3),
     }
+    if not args.no_secondary and world == 1:
+        line["secondary"] = secondary_runs(ds)
     if not args.no_cpu_baseline and world == 1:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         rate, n_steps, el, cells = oracle_steps_per_sec(ds, prim["state"], args.cpu_seconds)
@@ -1278,6 +1282,42 @@ def main():
             line["cpu_baseline_all_cores"] = allc
     print(json.dumps(line))
     return 0
+
+
+def secondary_runs(ds):
+    """Two short measurements beside the metric (not part of it): one local
+    Gibbs iteration on the metric's workload (CUDA events, 100 iterations after
+    20 steps of a local_iters = 2 chain) and the 64-dataset BF16 batch (CUDA
+    events, 300 batched steps after 100 untimed ones; its 1.4 GB of inputs
+    exceed L2).  A failure is reported in the line instead of the figure."""
+    import torch
+    import paper_1812_10048_gb300 as P
+    from paper_1812_10048_gb300 import synth
+    out = {}
+    try:
+        s = P.Sampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.1, kmax=256, seed=42,
+                      local_iters=2)
+        s.step(20)
+        s.sync()
+        st = torch.cuda.ExternalStream(s.stream)
+        ms = time_steps(lambda: P.dpmm_local_gibbs(s.ctx, 1), st, 100, 5, torch)
+        out["local_iteration_us"] = round(float(ms.mean()) * 1e3, 2)
+        s.close()
+    except Exception as e:   # reported, the metric stands
+        out["local_iteration_error"] = str(e)[:200]
+    try:
+        t0 = time.time()
+        dss = synth.batched(64, workers=min(16, os.cpu_count() or 1))
+        data = [(d.indptr, d.indices, d.data, d.N) for d in dss]
+        bs = P.BatchSampler(data, 1000, 1.0, 0.5, kmax=64, seed=42)
+        st = torch.cuda.ExternalStream(bs.stream)
+        ms = time_steps(lambda: bs.step(1), st, 300, 100, torch)
+        out["batched_64_datasets_chain_sweeps_per_s"] = round(64 * 300 / (ms.sum() / 1e3), 1)
+        out["batched_generation_s"] = round(time.time() - t0, 1)
+        bs.close()
+    except Exception as e:   # reported, the metric stands
+        out["batched_error"] = str(e)[:200]
+    return out
 
 
 def run_reference(args, rank, world):
