@@ -93,6 +93,35 @@ def test_batch_mixing_tile_and_csr_chains(P):
         s.close()
 
 
+def test_large_batch_of_small_chains(P):
+    """600 chains (more than the draw kernel reads side by side, so its
+    per-chain loop and the engine-selection kernel's per-chain noise split
+    run): three of them against their single-chain runs, bit for bit."""
+    from paper_1812_10048_gb300 import synth
+    ds = []
+    for b in range(600):
+        d = synth.make_dataset(40 + (b * 7) % 160, 64, 2 + b % 3, gamma=0.2,
+                               lib_mu=np.log(300.0), lib_sigma=0.4, seed=7000 + b)
+        ds.append((d.indptr, d.indices, d.data, d.N))
+    batch = P.BatchSampler(ds, 64, 1.0, 0.5, kmax=8, seed=13, chain_id=0)
+    picks = [0, 311, 599]
+    singles = [P.Sampler(ds[b][0], ds[b][1], ds[b][2], ds[b][3], 64, 1.0, 0.5, kmax=8, seed=13,
+                         chain_id=b) for b in picks]
+    batch.step(4)
+    for s in singles:
+        s.step(4)
+    for b, s in zip(picks, singles):
+        v = batch.chain(b)
+        got, ref = v.get_state(), s.get_state()
+        assert got[2:] == ref[2:], b
+        np.testing.assert_array_equal(got[0], ref[0])
+        np.testing.assert_array_equal(got[1], ref[1])
+        for x, y in zip(v.stats(), s.stats()):
+            np.testing.assert_array_equal(x, y)
+        s.close()
+    batch.close()
+
+
 def test_batch_context_rejects_per_chain_calls(P):
     ds = datasets()[:2]
     batch = P.BatchSampler(ds, 300, kmax=16)
