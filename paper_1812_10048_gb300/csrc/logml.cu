@@ -2,7 +2,10 @@
 // respect to log alpha and a gene-wise log beta (theta integrated out of
 // eq. 12 against eq. 28 with lambda generalised to beta_u, pi out of eq. 10).
 //
-//   k_lml_stats     n_k, S_ku of the labelled cells (integer, exact)
+//   k_lml_stats     n_k, S_ku of the labelled cells (integer, exact); for a
+//                   sampler's chain (dpmm_logml_grad) k_lml_from_chain sums
+//                   its sub-cluster statistics and k_lml_csr_stats counts
+//                   given labels from its packed CSR
 //   k_lml_forward   FP64, blocks (cluster, 256 genes): lgamma(n_k) + lgamma(B) - lgamma(B + T_k)
 //                   + sum_{u: S_ku > 0} [lgamma(beta_u + S_ku) - lgamma(beta_u)];
 //                   one extra block adds K log alpha + lgamma(alpha) - lgamma(alpha + N)

@@ -1,16 +1,20 @@
-// Split/merge moves (Sections 2.3-2.4) and the move plans shared with the
-// sweep's empty-cluster removal.
+// Split/merge moves (Sections 2.3-2.4) and the plans shared with the sweep's
+// empty-cluster removal.
 //
-//   k_move_prep / k_move_partial
-//                 pick the chain (fair coin on the tag-4 stream unless the
-//                 caller fixes it) and score every proposal in FP64:
-//                 split of cluster k into its sub-clusters (eq. 7, with the
-//                 likelihood ratio of eq. 9 / 14 / 16 taken with theta and
-//                 pi integrated out, and q(S*|S) from eq. 8), or merge of a
-//                 random disjoint pair (eq. 7 with the eq. 23 proposal ratio)
-//   k_plan        one block: turns decisions (or the sweep's empty clusters)
-//                 into a label map, a statistics-gather descriptor and the
-//                 new n-bar / sum log q of every surviving cluster
+//   k_lg_table      the FP64 lgamma and logarithm tables (at init and when
+//                   dpmm_set_hyper changes beta)
+//   k_move_partial  picks the chain (fair coin unless the caller fixes it)
+//                   and scores every proposal in FP64: the split of cluster k
+//                   into its sub-clusters (eq. 7, with the likelihood ratio of
+//                   eq. 9 / 14 / 16 taken with theta and pi integrated out and
+//                   q(S*|S) from eq. 8; eq. 18 instantiated as an option), or
+//                   the merge of a random disjoint pair (eq. 7 with the eq. 23
+//                   proposal ratio); per-item partial sums, the last block of
+//                   each proposal decides it
+//   k_plan_apply    one cooperative launch: the plan (label map, statistics
+//                   gather descriptors, new n-bar / sum log q of every
+//                   surviving cluster) of a move or of the sweep's compaction,
+//                   then, only when it changes something, its application
 #include <math_constants.h>
 
 #include <cmath>

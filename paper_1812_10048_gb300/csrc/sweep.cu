@@ -1,16 +1,28 @@
-// Kernels of one Gibbs sweep (eq. 4 with the eq. 8 sub-cluster step) and the
-// generic plan-application kernels shared with the split/merge moves.
+// Kernels of one Gibbs sweep (eq. 4 with the eq. 8 sub-cluster step), the
+// CSR label engine and the local Gibbs iterations.
 //
-// Sweep pipeline (all on the context stream, K read on the device):
+// Sweep (one launch per kernel over every chain of the context's table):
+//   k_open_slot     (open_new_cluster) eq. 4's K+1 candidate appended as a
+//                   cluster without cells
 //   k_draw_params   pi ~ Dir(n_1..n_K, alpha); theta_k ~ Dir(beta + S_k);
-//                   theta-bar_{k,r} ~ Dir(beta + S-bar_{k,r})  (eq. 4, eq. 19)
-//   k_assign        c_i = argmax_k log pi_k + sum_u x_i^u log theta_k^u + g_ik
-//                   (eq. 4 third line, Gumbel-max) and the eq. 8 sub-label
-//   k_stats         n-bar, S-bar of the new labels (integer, exact)
-//   k_plan          removal of empty clusters, sub-cluster resets (moves.cu)
-//   k_gather_stats  compacted statistics
-//   k_relabel       labels renumbered, reset sub-labels redrawn
-//   k_stats         recount of reset clusters; bumps the sweep counter t
+//                   theta-bar_{k,r} ~ Dir(beta + S-bar_{k,r}) (eq. 4, eq. 19),
+//                   in log space; selects each chain's label engine, clears
+//                   the sweep's accumulators and fills the dense-tile engine's
+//                   label noise
+//   k_assign        CSR label engine: c_i = argmax_k log pi_k + sum_u x_iu
+//                   log theta_ku + g_ik (eq. 4 third line, Gumbel-max) and the
+//                   eq. 8 sub-label, statistics fused when they fit; returns
+//                   at once for a chain the dense-tile engine (tile.cu) labels
+//   k_stats         n-bar, S-bar of the new labels (integer, exact) unless fused
+//   k_csr_commit    a CSR-labelled sweep's S-bar into the main statistics
+// The compaction and the split/merge move that follow are in moves.cu.
+// Local Gibbs iterations (local_iters > 1, Section 2.3), labels held:
+//   k_draw_local    theta-bar from eq. 19 given the current sub-labels
+//   k_local_sub     eq. 8 sub-labels and log q
+//   k_local_commit  the recounted statistics become the main ones
+// Also k_select_engine (the engine choice of a label call outside a sweep),
+// k_init_state (every cell in cluster 0, fair-coin sub-labels) and
+// k_debug_scores (scores of selected cells, a test hook).
 #include <math_constants.h>
 
 #include <climits>

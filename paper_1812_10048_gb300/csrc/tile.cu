@@ -109,10 +109,11 @@ cudaError_t launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int Kd, i
 // (K <= 40).  Centring subtracts m_u, the mean of the 3K log theta values of
 // gene u, from every row; it shifts all of a cell's scores by the same
 // sum_u x_u m_u, which leaves the Gumbel argmax, the eq. 8 draw and log q_i
-// unchanged.  The epilogue gives each of the 128 cells a thread: Gumbel-max
-// over its K scores, the eq. 8 sub-label from the two sub-cluster scores of the
-// chosen cluster, the cell state, and then the whole CTA adds the tile's
-// counts into shared-memory statistics.
+// unchanged.  The epilogue (two groups of four warps, a thread of each per
+// cell) takes the Gumbel-max over the cell's K scores and the eq. 8 sub-label
+// from the two sub-cluster scores of the chosen cluster, writes the cell state
+// and adds log q_i to its cluster's accumulator; the statistics are counted
+// afterwards from the blocked copy (k_stats_tile).
 // ===========================================================================
 
 constexpr int kNtotMax = 256;
