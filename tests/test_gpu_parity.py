@@ -334,6 +334,61 @@ def test_edge_cases_empty_rows_wide_counts_single_cell(P):
     assert K == 1 and labels[0] == 0
 
 
+def test_no_cells_or_no_genes_are_rejected(P):
+    empty = np.zeros(0, np.int32)
+    with pytest.raises(P.DpmmError, match="EINVAL"):
+        P.Sampler(np.zeros(1, np.int32), empty, empty, 0, 5, 1.0, 1.0)
+    with pytest.raises(P.DpmmError, match="EINVAL"):
+        P.Sampler(np.zeros(3, np.int32), empty, empty, 2, 0, 1.0, 1.0)
+
+
+@pytest.mark.parametrize("engine", ["csr_fp32", "tile_bf16"])
+def test_matrix_without_counts(P, engine):
+    """No cell has a count: eq. 4 labels come from log pi and the Gumbels
+    alone and eq. 8 sub-labels from the n-bar weights.  One label step from an
+    injected K = 4 state agrees with the FP64 decisions on the same Philox
+    words; a chain keeps valid labels and exact (all-zero) S-bar."""
+    from types import SimpleNamespace
+    from oracle.sampler import Sampler as OracleSampler, sufficient_stats
+    from .parity import bf16_bound, check_assign, decisions_from_oracle, fp32_bound
+    N, D = 700, 40
+    empty = np.zeros(0, np.int32)
+    ds = SimpleNamespace(indptr=np.zeros(N + 1, np.int32), indices=empty, data=empty, N=N, D=D)
+    eng = P.ENGINE_CSR_FP32 if engine == "csr_fp32" else P.ENGINE_TILE_BF16
+    rng = np.random.default_rng(17)
+    labels0 = rng.permutation(np.arange(N) % 4)
+    sub0 = rng.integers(0, 2, size=N)
+    o = OracleSampler(ds.indptr, ds.indices, ds.data, N, D, 1.0, 0.5, seed=7)
+    n0 = np.bincount(labels0, minlength=4)
+    o.set_state(labels0, sub0, 4, t=3, m=3, sumlogq=n0 * np.log(0.5))
+    g, _ = make_pair(P, ds, seed=7, engine=eng)
+    inject(P, g, o)
+    P.dpmm_draw_params(g.ctx)
+    logpi32, logtheta32 = P.dpmm_get_params(g.ctx, o.K, D)
+    P.dpmm_set_params(g.ctx, logpi32, logtheta32)
+    logpi, logtheta = logpi32.astype(np.float64), logtheta32.astype(np.float64)
+    bound = (fp32_bound if engine == "csr_fp32" else bf16_bound)(o.X.astype(np.float64), logtheta)
+    ref = decisions_from_oracle(o, logpi, logtheta, bound)
+    K0, t0 = o.K, o.t
+    o.assign_and_update(logpi, logtheta)
+    P.dpmm_assign(g.ctx)
+    assert P.dpmm_debug_engine(g.ctx) == (1 if engine == "tile_bf16" else 0)
+    labels, sub, K, t, m = g.get_state()
+    assert t == o.t and K == o.K
+    nsub, Ssub, sq = g.stats()
+    checked, _ = check_assign(ref, K0, K, labels, sub, sq, o.seed, o.chain_id, t0)
+    assert checked >= 1
+    # a chain of sweeps and moves on the empty matrix
+    g.step(20)
+    labels, sub, K, _, _ = g.get_state()
+    assert 1 <= K and labels.min() >= 0 and labels.max() < K
+    nsub, Ssub, _ = g.stats()
+    on, oS = sufficient_stats(o.X, labels, sub, K)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    assert not np.any(Ssub)
+
+
 def test_invalid_inputs_raise(P):
     ok_ptr = np.array([0, 1, 2], np.int32)
     with pytest.raises(P.DpmmError, match="EINVAL"):
