@@ -41,7 +41,10 @@ extern "C" {
 
 #define DPMM_ENGINE_AUTO 0      /* pick per sweep from K and the count density (measured) */
 #define DPMM_ENGINE_CSR_FP32 1  /* warp-per-cell CSR contraction, FP32 */
-#define DPMM_ENGINE_TILE_BF16 2 /* dense 128-cell tiles on tcgen05, BF16 hi/lo */
+#define DPMM_ENGINE_TILE_BF16 2 /* dense 128-cell tiles on tcgen05, BF16 hi/lo; needs
+                                   the packed entries (D <= 65,536 genes, every count
+                                   <= 65,535) and 1 <= K <= 40: a sweep outside that
+                                   runs the CSR engine (dpmm_debug_engine tells) */
 
 typedef struct dpmm_ctx dpmm_ctx;
 

@@ -389,6 +389,94 @@ def test_matrix_without_counts(P, engine):
     assert not np.any(Ssub)
 
 
+def _wide_matrix(D, big, seed=23):
+    """260 cells (two full 128-cell tiles and a ragged one) over D genes, about
+    30 genes a cell, the last gene used, counts of 255, 256-999 and `big`."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    N = 260
+    cols_l, x_l = [], []
+    for i in range(N):
+        cols = np.unique(rng.integers(0, D, size=30))
+        if i % 7 == 0:
+            cols = np.unique(np.append(cols, D - 1))
+        x = rng.integers(1, 6, size=cols.size)
+        if i % 11 == 0:
+            x[0] = big
+        if i % 5 == 0:
+            x[-1] = rng.integers(256, 1000)
+        if i % 13 == 0:
+            x[rng.integers(0, cols.size)] = 255
+        cols_l.append(cols.astype(np.int32))
+        x_l.append(x.astype(np.int32))
+    indptr = np.concatenate([[0], np.cumsum([c.size for c in cols_l])]).astype(np.int32)
+    return SimpleNamespace(indptr=indptr, indices=np.concatenate(cols_l),
+                           data=np.concatenate(x_l), N=N, D=D)
+
+
+def _one_label_step_against_fp64(P, ds, engine, bound_fn):
+    """One label step of a GPU chain from an injected K = 3 state, checked
+    against the FP64 decisions from the parameters the GPU drew; statistics
+    exact.  Returns the GPU chain."""
+    from oracle.sampler import Sampler as OracleSampler, sufficient_stats
+    from .parity import check_assign, decisions_from_oracle
+    rng = np.random.default_rng(29)
+    labels0 = rng.permutation(np.arange(ds.N) % 3)
+    sub0 = rng.integers(0, 2, size=ds.N)
+    o = OracleSampler(ds.indptr, ds.indices, ds.data, ds.N, ds.D, 1.0, 0.5, seed=5)
+    o.set_state(labels0, sub0, 3, t=2, m=2,
+                sumlogq=np.bincount(labels0, minlength=3) * np.log(0.5))
+    g, _ = make_pair(P, ds, seed=5, engine=engine)
+    inject(P, g, o)
+    P.dpmm_draw_params(g.ctx)
+    logpi32, logtheta32 = P.dpmm_get_params(g.ctx, o.K, ds.D)
+    P.dpmm_set_params(g.ctx, logpi32, logtheta32)
+    logpi, logtheta = logpi32.astype(np.float64), logtheta32.astype(np.float64)
+    ref = decisions_from_oracle(o, logpi, logtheta, bound_fn(o.X.astype(np.float64), logtheta))
+    K0, t0 = o.K, o.t
+    o.assign_and_update(logpi, logtheta)
+    P.dpmm_assign(g.ctx)
+    labels, sub, K, t, m = g.get_state()
+    assert t == o.t and K == o.K
+    nsub, Ssub, sq = g.stats()
+    checked, _ = check_assign(ref, K0, K, labels, sub, sq, o.seed, o.chain_id, t0)
+    assert checked >= 1
+    on, oS = sufficient_stats(o.X, labels, sub, K)
+    np.testing.assert_array_equal(nsub, on)
+    np.testing.assert_array_equal(Ssub, oS)
+    return g
+
+
+@pytest.mark.parametrize("engine", ["csr_fp32", "tile_bf16"])
+def test_widest_packed_matrix(P, engine):
+    """The packed form's limits: 65,536 genes (the last one used) and counts
+    up to 65,535, with high bytes for the tensor-core form's second plane."""
+    from .parity import bf16_bound, fp32_bound
+    from .test_gpu_tile import blocked_reference
+    ds = _wide_matrix(65536, 65535)
+    tile = engine == "tile_bf16"
+    g = _one_label_step_against_fp64(P, ds, P.ENGINE_TILE_BF16 if tile else P.ENGINE_CSR_FP32,
+                                     bf16_bound if tile else fp32_bound)
+    assert P.dpmm_debug_engine(g.ctx) == (1 if tile else 0)
+    if tile:
+        T, C, tptr, tent = P.dpmm_debug_tile_layout(g.ctx)
+        rT, rC, rptr, rent = blocked_reference(ds.indptr, ds.indices, ds.data, ds.N, ds.D)
+        assert (T, C) == (rT, rC) == (3, 1024)
+        np.testing.assert_array_equal(tptr, rptr)
+        np.testing.assert_array_equal(tent, rent)
+
+
+@pytest.mark.parametrize("D, big", [(65537, 65535), (1000, 65536)])
+def test_tile_engine_on_unpackable_counts_runs_the_csr_engine(P, D, big):
+    """One gene too many or one count too large for the packed entries: a
+    chain that asks for the tensor-core engine is labelled by the FP32 CSR
+    engine, with the FP32 decisions."""
+    from .parity import fp32_bound
+    ds = _wide_matrix(D, big)
+    g = _one_label_step_against_fp64(P, ds, P.ENGINE_TILE_BF16, fp32_bound)
+    assert P.dpmm_debug_engine(g.ctx) == 0
+
+
 def test_invalid_inputs_raise(P):
     ok_ptr = np.array([0, 1, 2], np.int32)
     with pytest.raises(P.DpmmError, match="EINVAL"):
