@@ -122,6 +122,41 @@ def test_large_batch_of_small_chains(P):
     batch.close()
 
 
+@pytest.mark.parametrize("engine", ["auto", "tile"])
+def test_batch_of_degenerate_and_tile_boundary_chains(P, engine):
+    """A batch holding a one-cell chain, chains of 127, 128 and 129 cells (the
+    128-cell tile boundary), a chain without any count and a larger one: every
+    chain equals its single-chain run bit for bit, and its statistics equal a
+    recount of its own labels."""
+    from paper_1812_10048_gb300 import synth
+    from oracle.sampler import csr_matrix, sufficient_stats
+    D = 64
+    ds = []
+    for b, N in enumerate((1, 127, 128, 129, 500)):
+        d = synth.make_dataset(N, D, min(3, N), gamma=0.2, lib_mu=np.log(300.0), lib_sigma=0.4,
+                               seed=7700 + b)
+        ds.append((d.indptr, d.indices, d.data, d.N))
+    empty = np.zeros(0, np.int32)
+    ds.insert(3, (np.zeros(301, np.int32), empty, empty, 300))
+    eng = {"auto": P.ENGINE_AUTO, "tile": P.ENGINE_TILE_BF16}[engine]
+    batch = P.BatchSampler(ds, D, 1.0, 0.5, kmax=16, seed=21, chain_id=0, engine=eng)
+    singles = [P.Sampler(d[0], d[1], d[2], d[3], D, 1.0, 0.5, kmax=16, seed=21, chain_id=b,
+                         engine=eng) for b, d in enumerate(ds)]
+    batch.step(6)
+    for s in singles:
+        s.step(6)
+    compare(P, batch, singles, D)
+    for b, (ip, ix, dt, N) in enumerate(ds):
+        labels, sub, K, _, _ = batch.chain(b).get_state()
+        nsub, Ssub, _ = batch.chain(b).stats()
+        on, oS = sufficient_stats(csr_matrix(ip, ix, dt, N, D), labels, sub, K)
+        np.testing.assert_array_equal(nsub, on)
+        np.testing.assert_array_equal(Ssub, oS)
+    for s in singles:
+        s.close()
+    batch.close()
+
+
 def test_batch_context_rejects_per_chain_calls(P):
     ds = datasets()[:2]
     batch = P.BatchSampler(ds, 300, kmax=16)

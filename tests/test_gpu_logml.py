@@ -100,3 +100,31 @@ def test_chain_bound_logml_grad_matches_oracle(P):
     labels2, K2 = s.labels()
     assert K2 == K and np.array_equal(labels2, labels)
     s.close()
+
+
+def test_without_counts_only_the_partition_term_remains(P):
+    """No cell has a count (T_k = 0, S = 0): the collapsed log ML is the CRP
+    partition term K log alpha + lgamma(alpha) - lgamma(alpha + N) + sum_k
+    lgamma(n_k) alone, its log-beta gradient vanishes and d/d log alpha =
+    K + alpha (psi(alpha) - psi(alpha + N)), in closed form."""
+    import torch
+    from scipy.special import digamma, gammaln
+    N, D, K = 500, 80, 5
+    rng = np.random.default_rng(4)
+    labels = rng.permutation(np.arange(N) % K).astype(np.int32)
+    empty = np.zeros(0, np.int32)
+    h = P.LogML(np.zeros(N + 1, np.int32), empty, empty, N, D, labels, K)
+    la = 0.4
+    a = np.exp(la)
+    n = np.bincount(labels, minlength=K)
+    ref = K * la + gammaln(a) - gammaln(a + N) + gammaln(n).sum()
+    lb = (np.log(0.1) + 0.1 * rng.standard_normal(D)).astype(np.float32)
+    got = h.forward(la, torch.from_numpy(lb).cuda())
+    assert abs(got - ref) <= 1e-10 * abs(ref)
+    gb = torch.empty(D, dtype=torch.float32, device="cuda")
+    ga = h.backward(la, torch.from_numpy(lb).cuda(), gb)
+    torch.cuda.synchronize()
+    ga_ref = K + a * (digamma(a) - digamma(a + N))
+    assert abs(ga - ga_ref) <= 1e-9 * max(1.0, abs(ga_ref))
+    np.testing.assert_allclose(gb.cpu().numpy(), 0.0, rtol=0, atol=1e-6)
+    h.close()
