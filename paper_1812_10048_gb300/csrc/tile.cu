@@ -134,13 +134,18 @@ __device__ __forceinline__ float bf16_value(uint16_t b) {
 }
 
 // B operand of one sweep: block (c, q, b) fills rows rb q .. rb q + rb - 1 of
-// chunk c (genes 64c .. 64c + 63) of chain b; every block of chunk c forms the
-// same m_u (rb = 16 rows for one chain, 64 for a batch: fewer blocks, less
-// repeated m_u).  In a step (force = 0) the blocks of chain b first clear its
-// main S-bar rows.
+// chunk c (genes 64c .. 64c + 63) of chain b (rb = 16 rows for one chain, 64
+// for a batch).  Each block reads the chunk's 3K log theta values per gene
+// into shared memory with all of a thread's loads in flight at once, then
+// forms m_u and its rows from there.  In a step (force = 0) the blocks of
+// chain b first clear its main S-bar rows.
+constexpr int kBuildThreads = 256;
+constexpr int kBuildStage = 3 * kTileMaxK * 64 / kBuildThreads;   // values per thread
+
 template <class Tab>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kBuildThreads)
 k_build_b(const __grid_constant__ Tab tab, int32_t force, int32_t rb) {
+    __shared__ float sv[3 * kTileMaxK * 64];   // [3K][64]: row j of gene 64c + g
     __shared__ float part[4][64];
     __shared__ float m[64];
     const ChainArgs& ch = tab[blockIdx.z];
@@ -165,15 +170,30 @@ k_build_b(const __grid_constant__ Tab tab, int32_t force, int32_t rb) {
     if (c >= ch.tile_C) return;
     const int S0 = tile_s0(K), Ntot = tile_ntot(K);
     if ((int)blockIdx.y * rb >= Ntot) return;
+    // rows j < K: cluster j (log theta); K <= j < 3K: sub-cluster (j - K) / 2,
+    // r = (j - K) % 2 (log theta-bar).  Every load first, then the stores.
+    const int n3 = 3 * K * 64;
+    float v[kBuildStage];
+#pragma unroll
+    for (int r = 0; r < kBuildStage; ++r) {
+        const int i = threadIdx.x + kBuildThreads * r;
+        const int j = i >> 6, u = c * 64 + (i & 63);
+        v[r] = 0.0f;
+        if (i < n3 && u < D)
+            v[r] = j < K ? __ldg(Lc + (size_t)u * kmax + j) : __ldg(Ls + (size_t)u * kmax * 2 + (j - K));
+    }
+#pragma unroll
+    for (int r = 0; r < kBuildStage; ++r) {
+        const int i = threadIdx.x + kBuildThreads * r;
+        if (i < n3) sv[i] = v[r];
+    }
+    __syncthreads();
     {
         // m_u: 4 threads per gene, each a quarter of the 3K rows, fixed order
         const int g = threadIdx.x & 63, qq = threadIdx.x >> 6;
-        const int u = c * 64 + g;
         float s = 0.0f;
-        if (u < D) {
-            for (int j = qq; j < 3 * K; j += 4)
-                s += j < K ? Lc[(size_t)u * kmax + j] : Ls[(size_t)u * kmax * 2 + (j - K)];
-        }
+        if (c * 64 + g < D)
+            for (int j = qq; j < 3 * K; j += 4) s += sv[j * 64 + g];
         part[qq][g] = s;
         __syncthreads();
         if (threadIdx.x < 64)
@@ -189,11 +209,11 @@ k_build_b(const __grid_constant__ Tab tab, int32_t force, int32_t rb) {
         bool live = u < D;
         if (row < 2 * K) {
             part = row & 1;
-            if (live) L = Lc[(size_t)u * kmax + (row >> 1)];
+            L = sv[(row >> 1) * 64 + g];
         } else if (row >= S0 && row < S0 + 4 * K) {
             const int q = row - S0;
             part = q & 1;
-            if (live) L = Ls[((size_t)u * kmax + (q >> 2)) * 2 + ((q >> 1) & 1)];
+            L = sv[(K + (q >> 1)) * 64 + g];
         } else {
             live = false;
         }
@@ -917,7 +937,7 @@ cudaError_t configure_tile(Ctx& c) {
 cudaError_t launch_build_b(Ctx& c, bool force) {
     return with_table(c, [&](auto tab) {
         const int rb = c.nchains > 1 ? 64 : 16;
-        k_build_b<<<dim3(c.tile_C, kNtotMax / rb, c.nchains), 256, 0, c.stream>>>(
+        k_build_b<<<dim3(c.tile_C, kNtotMax / rb, c.nchains), kBuildThreads, 0, c.stream>>>(
             tab, force ? 1 : 0, rb);
         return cudaGetLastError();
     });
